@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: FGMRES time to a 1e-8 relative residual and V-cycle HBM GB/s.
+
+Workload (default): the one-group 3-component system on a 1024x1024 grid with
+a 10^4 coefficient jump across a circular inclusion (3.1M unknowns, 15.7M
+nonzeros, seeded synthetic coefficients), preconditioned by Schur1 with one
+classical-AMG V(1,1) cycle per subsystem inverse, FP64.  One step = the whole
+hot path on that system: device setup (block extraction, strength, PMIS,
+interpolation, Galerkin products, smoother diagonals, coarsest inverse) plus
+the FGMRES(30) solve to ||b - A x|| <= 1e-8 ||b||.  Inputs are resident in HBM
+before the timed region; the operator (201 MB) is larger than L2, so no flush
+is needed between steps.
+
+--impl reference times the FP64 CPU oracle on the same workload (host cores),
+the deliberately slow program the GPU path is checked against.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = 1
+KIND = "schur1"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.idx = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2002_04958_gb300 import inputs
+    from paper_2002_04958_gb300 import mgdamg
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2002_04958_gb300.build import build
+    build()
+
+    sysm = inputs.preset(args.config)
+    dev = torch.device("cuda", local)
+    rp = torch.from_numpy(sysm.rowptr).to(dev)
+    ci = torch.from_numpy(sysm.col).to(dev)
+    va = torch.from_numpy(sysm.val).to(dev)
+    b = torch.from_numpy(sysm.b).to(dev)
+    opts = dict(precision=args.precision, batched=args.batched, use_graph=args.graph, autotune=1)
+    slv = mgdamg.Solver(**opts)
+
+    def step():
+        slv.setup(sysm.G, sysm.N, rp, ci, va, args.kind)
+        x, it, rr, rc = slv.solve(b, tol=args.tol)
+        return x, it, rr
+
+    for _ in range(args.warmup):
+        x, it, rr = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    slv.profile(True)
+    l0 = mgdamg.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    setup_ms, solve_ms, iters = [], [], []
+    for _ in range(args.steps):
+        x, it, rr = step()
+        st = slv.stats()
+        setup_ms.append(st["setup_ms"])
+        solve_ms.append(st["solve_ms"])
+        iters.append(it)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = mgdamg.kernel_launches() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    n0, t0, by0 = slv.profile_read(0)    # level-0 smoothing + residual kernels (dominant)
+    n1, t1, by1 = slv.profile_read(1)    # every V-cycle kernel
+    slv.profile(False)
+    st = slv.stats()
+    xg = x
+    relres = rr
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    h_rp = torch.from_numpy(sysm.rowptr).pin_memory()
+    h_ci = torch.from_numpy(sysm.col).pin_memory()
+    h_va = torch.from_numpy(sysm.val).pin_memory()
+    h_b = torch.from_numpy(sysm.b).pin_memory()
+    h_x = torch.zeros(sysm.n, dtype=torch.float64).pin_memory()
+    d_rp, d_ci, d_va = torch.empty_like(rp), torch.empty_like(ci), torch.empty_like(va)
+    e2e_ms = []
+    for k in range(max(2, args.steps // 2) + 1):
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        d_rp.copy_(h_rp, non_blocking=True)
+        d_ci.copy_(h_ci, non_blocking=True)
+        d_va.copy_(h_va, non_blocking=True)
+        slv.setup(sysm.G, sysm.N, d_rp, d_ci, d_va, args.kind)
+        h_x.zero_()
+        slv.solve_host_ptr(h_b.data_ptr(), h_x.data_ptr(), tol=args.tol)
+        torch.cuda.synchronize()
+        if k > 0:
+            e2e_ms.append((time.perf_counter() - t_a) * 1e3)
+    h2d = sysm.rowptr.nbytes + sysm.col.nbytes + sysm.val.nbytes + sysm.b.nbytes + sysm.n * 8
+    d2h = sysm.n * 8
+
+    # variants for context (one solve each, outside the timed region)
+    variants = {}
+    if not args.no_variants:
+        for name, kind, o in [("monolithic_amg_fp64", "amg", dict()),
+                              (f"{args.kind}_fp32_vcycle", args.kind, dict(precision=1)),
+                              (f"{args.kind}_fp32_vcycle_batched_graph", args.kind,
+                               dict(precision=1, batched=1, use_graph=1))]:
+            try:
+                v = mgdamg.Solver(autotune=1, **o)
+                v.setup(sysm.G, sysm.N, rp, ci, va, kind)
+                torch.cuda.synchronize()
+                t_a = time.perf_counter()
+                v.setup(sysm.G, sysm.N, rp, ci, va, kind)
+                xv, itv, rrv, rc = v.solve(b, tol=args.tol, allow_noconv=True)
+                torch.cuda.synchronize()
+                tt = time.perf_counter() - t_a
+                sv = v.stats()
+                err = (torch.linalg.vector_norm(xv - xg) / torch.linalg.vector_norm(xg)).item()
+                variants[name] = {"iters": itv, "relres": rrv, "status": rc, "time_s": round(tt, 5),
+                                  "setup_ms": round(sv["setup_ms"], 3), "solve_ms": round(sv["solve_ms"], 3),
+                                  "rel_diff_vs_fp64_x": err}
+                v.close()
+            except Exception as ex:  # report, do not hide
+                variants[name] = {"error": str(ex)}
+
+    peak, peak_kind = _peaks()
+    ach = by0 / (t0 * 1e-3) / 1e9 if t0 > 0 else None
+    vgbs = by1 / (t1 * 1e-3) / 1e9 if t1 > 0 else None
+    traffic = _traffic_from_profiles()
+    out = {
+        "metric": "FGMRES time-to-1e-8 residual (s) and V-cycle HBM GB/s, mixed/batched vs FP64",
+        "value": round(ms / 1e3, 6),
+        "unit": "s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.precision == 0 else "f64-krylov/f32-vcycle",
+        "data": "synthetic",
+        "config": {"workload": inputs.PRESET_NAMES[args.config] if args.kind == KIND else
+                   f"{inputs.PRESET_NAMES[args.config]}[{args.kind}]",
+                   "G": sysm.G, "grid": list(sysm.dims), "n": sysm.n, "nnz": sysm.nnz,
+                   "precond": args.kind, "krylov": "FGMRES(30), right preconditioned", "tol": args.tol,
+                   "step": "device setup + solve", "parallelism": f"replicas{ws}",
+                   "l2": "inputs larger than L2 (operator 201 MB), no flush"},
+        "iters": iters[-1],
+        "final_relres": relres,
+        "setup_ms": round(statistics.median(setup_ms), 3),
+        "solve_ms": round(statistics.median(solve_ms), 3),
+        "vcycle_gbs": round(vgbs, 1) if vgbs else None,
+        "roofline": {"bound": "hbm", "kernel": "level-0 l1-Jacobi smoothing + residual (k_pre/k_post)",
+                     "achieved": round(ach, 1) if ach else None, "peak": peak, "unit": "GB/s",
+                     "frac": round(ach / peak, 4) if ach else None, "traffic": traffic,
+                     "peak_source": peak_kind, "launches": n0, "ms": round(t0, 4)},
+        "e2e": {"value": round(statistics.median(e2e_ms) / 1e3, 6), "unit": "s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "stats": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()},
+        "variants": variants,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, sysm, iters[-1])
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _traffic_from_profiles():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, when it was taken from the current kernel source."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    src = os.path.join(ROOT, "paper_2002_04958_gb300", "csrc", "solve_kernels.cu")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()
+    if d.get("solve_kernels_sha256") != h:
+        return None
+    return d.get("traffic_bytes_per_launch")
+
+
+def cpu_baseline(args, sysm, gpu_iters):
+    """The FP64 oracle on the same workload, single-threaded C on one host core."""
+    from oracle import oracle as orc
+    orc.build()
+    A = orc.csr_of_system(sysm)
+    t0 = time.perf_counter()
+    M = orc.Block(A, sysm.G, sysm.N, args.kind)
+    t1 = time.perf_counter()
+    budget_its = args.cpu_iters
+    x, it, rr, st, _ = orc.fgmres(A, sysm.b, M, tol=args.tol, maxit=budget_its)
+    t2 = time.perf_counter()
+    full = st == 0
+    solve = t2 - t1
+    if not full:   # scale the sampled iterations to the iteration count of the solve
+        solve = solve * max(gpu_iters, it) / max(it, 1)
+    return {"value": round((t1 - t0) + solve, 4), "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"full oracle setup + FGMRES solve of the same system ({it} iterations)" if full else
+                       f"full oracle setup + {it} FGMRES iterations scaled to {gpu_iters}"),
+            "setup_s": round(t1 - t0, 4), "iters": it, "converged": full}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    from paper_2002_04958_gb300 import inputs
+    orc.build()
+    sysm = inputs.preset(args.config)
+    A = orc.csr_of_system(sysm)
+    times, iters = [], []
+
+    def step():
+        t0 = time.perf_counter()
+        M = orc.Block(A, sysm.G, sysm.N, args.kind)
+        t1 = time.perf_counter()
+        x, it, rr, st, _ = orc.fgmres(A, sysm.b, M, tol=args.tol, maxit=args.ref_iters)
+        t2 = time.perf_counter()
+        return t1 - t0, t2 - t1, it, st
+
+    for _ in range(args.warmup):
+        step()
+    samples = []
+    for _ in range(args.steps):
+        samples.append(step())
+    # the iteration count of the full solve (one oracle solve, outside the samples)
+    full_its = args.full_iters
+    if full_its is None:
+        M = orc.Block(A, sysm.G, sysm.N, args.kind)
+        _, full_its, _, _, _ = orc.fgmres(A, sysm.b, M, tol=args.tol, maxit=1000)
+    vals = [su + so * full_its / max(it, 1) for su, so, it, st in samples]
+    v = statistics.median(vals)
+    out = {
+        "metric": "FGMRES time-to-1e-8 residual (s) and V-cycle HBM GB/s, mixed/batched vs FP64",
+        "value": round(v, 4), "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(v * 1e3, 2), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": inputs.PRESET_NAMES[args.config], "n": sysm.n, "nnz": sysm.nnz,
+                   "precond": args.kind},
+        "cpu_baseline": {"value": round(v, 4), "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: full oracle setup + {args.ref_iters} FGMRES iterations, "
+                                   f"scaled to the {full_its} iterations of the full solve"},
+        "e2e": {"value": round(v, 4), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=WORKLOAD)
+    ap.add_argument("--kind", default=KIND)
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--batched", type=int, default=0)
+    ap.add_argument("--graph", type=int, default=0)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--cpu-iters", type=int, default=30)
+    ap.add_argument("--ref-iters", type=int, default=4)
+    ap.add_argument("--full-iters", type=int, default=None)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * mgdamg.h -- C ABI of the GB300 (sm_103a) solver for the (G+2)x(G+2)-block
+ * linear systems of multi-group radiation diffusion (Eq. 2.2): classical-AMG
+ * block preconditioners (monolithic AMG, Section 3.1; PCTL, Section 3.3;
+ * Schur1 and Schur2, Section 3.4; block-diagonal and block lower-triangular,
+ * the Remarks of Section 3.6) inside right-preconditioned FGMRES(m).
+ *
+ * Conventions for every entry point:
+ *   - "d_" pointers are device pointers (CUDA global memory on the device that
+ *     was current at mgd_create), "h_" pointers are host pointers.
+ *   - Input arrays stay owned by the caller and are only read during the call;
+ *     the library copies what it keeps.  Output arrays are caller-owned and
+ *     must hold the stated number of elements.
+ *   - All device work is issued on the CUDA stream given to mgd_create.  A
+ *     call returns after its results are complete on that stream, unless its
+ *     comment says otherwise.
+ *   - Return value 0 is success; otherwise one of the MGD_E* codes below, with
+ *     a message from mgd_last_error.  No C++ exception crosses this boundary.
+ *   - Indices are 0-based int32.  The matrix is CSR with strictly increasing
+ *     column indices inside each row, in block-major order: unknown (a, k) of
+ *     component a in cell k is row/column a*N + k, components 0..G-1 are the
+ *     radiation groups, G is the electron and G+1 the ion temperature.
+ *     Off-block entries must couple the same cell (the D_ab are diagonal).
+ */
+#ifndef MGDAMG_H
+#define MGDAMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mgd_ctx mgd_ctx; /* opaque, library-owned */
+
+/* preconditioner kinds */
+enum {
+  MGD_AMG = 0,    /* one classical-AMG V(1,1) cycle on the whole system (Section 3.1) */
+  MGD_PCTL = 1,   /* physical-variable-based two-level scheme (Section 3.3, Eq. 3.3) */
+  MGD_SCHUR1 = 2, /* five-stage block Schur complement, Eq. 3.1 with C_R ~ diag(C_g) (Section 3.4) */
+  MGD_SCHUR2 = 3, /* three-stage approximate block factorisation, Eq. 3.2 (Section 3.4) */
+  MGD_BD = 4,     /* block diagonal (Remark, Section 3.6) */
+  MGD_BLT = 5     /* block lower triangular (Remark, Section 3.6) */
+};
+
+/* status codes */
+enum {
+  MGD_OK = 0,
+  MGD_EINVAL = 1,      /* bad argument, size, layout, unsorted/duplicate columns, non-positive diagonal */
+  MGD_ENOCONV = 2,     /* iteration cap reached; x holds the last iterate */
+  MGD_EBREAKDOWN = 3,  /* Arnoldi breakdown before the tolerance was met */
+  MGD_ESINGULAR = 4,   /* zero pivot in the coarsest-level elimination */
+  MGD_ENAN = 5,        /* non-finite residual */
+  MGD_ETIMEOUT = 6,    /* a device-side bounded wait ran out */
+  MGD_ECUDA = 7,       /* CUDA runtime error */
+  MGD_ENOMEM = 8,      /* device allocation failed */
+  MGD_ESTATE = 9       /* call out of order (e.g. solve before setup) */
+};
+
+typedef struct mgd_opts {
+  double theta_str;       /* strength threshold, Section 3.1: 0.25 */
+  int max_coarse;         /* coarsest level solved by elimination when it has <= this many rows: 100 */
+  int max_levels;         /* 25 */
+  double theta_wd;        /* Definition 2 threshold: 0.9 */
+  double theta_wc;        /* Definition 1 threshold: 1e-2 */
+  double sigma_wc;        /* Section 3.6 switch criterion: 0.5 */
+  double inner_tol;       /* option #3 accuracy for the PCTL p_a: 1e-2 (Section 4) */
+  int inner_maxit;        /* option #3 cycle cap: 100 */
+  int nvcyc_group;        /* option #2 V-cycles per inverse of a group operator: 1 */
+  int nvcyc_E;            /* ... of an E operator: 1 */
+  int nvcyc_I;            /* ... of an I operator: 1 */
+  int nvcyc_other;        /* ... of the monolithic or PCTL coarse operator: 1 */
+  int jacobi_sweeps;      /* option #1 sweeps: 1 */
+  int adaptive;           /* 1: Section 3.6 coupling drops and the Section 3.5 option #1/#2 choice */
+  unsigned long long seed;/* PMIS weight seed */
+  int restart;            /* FGMRES restart length m: 30 */
+  int max_it;             /* cap on preconditioner applications per solve: 1000 */
+  int precision;          /* 0: FP64 V-cycles; 1: FP32 V-cycles (storage and arithmetic) inside FP64 FGMRES */
+  int batched;            /* 1: independent V-cycles of a stage run as one launch per level and phase */
+  int use_graph;          /* 1: the preconditioner apply is replayed from a captured CUDA graph */
+  int autotune;           /* 1: time sparse-kernel variants per level at setup and keep the fastest */
+  int keep_transpose;     /* 1: keep A_l^T per level so that mgd_solve_transpose can run */
+} mgd_opts;
+
+/* Fill *o with the defaults listed above.  Returns MGD_EINVAL if o is NULL. */
+int mgd_opts_default(mgd_opts *o);
+
+/* Create a context bound to the current CUDA device and to `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * handle; destroy it with mgd_destroy. */
+int mgd_create(mgd_ctx **out, const mgd_opts *o, void *stream);
+
+/* Setup phase (Section 3.1 setup; Sections 3.3-3.6 block operators):
+ * G groups, N cells, n = (G+2)*N unknowns, nnz entries; d_rowptr[n+1],
+ * d_colidx[nnz], d_vals[nnz] on the device.  Validates the layout (MGD_EINVAL
+ * on failure), extracts the blocks and couplings, applies the adaptive rules
+ * when opts.adaptive, builds every AMG hierarchy on the device (strength,
+ * PMIS, classical modified interpolation, Galerkin RAP, l1 diagonals, dense
+ * coarsest inverse) and prepares the solve.  Replaces any previous setup. */
+int mgd_setup(mgd_ctx *c, int G, int N, int n, int nnz, const int *d_rowptr, const int *d_colidx,
+              const double *d_vals, int kind);
+
+/* Same sparsity pattern, new values d_vals[nnz]: re-runs the whole numeric
+ * setup (the coarse patterns may change with the values). */
+int mgd_update_values(mgd_ctx *c, const double *d_vals);
+
+/* Solve A x = b by FGMRES(restart) preconditioned on the right, stopping when
+ * ||b - A x||_2 <= tol ||b||_2 (Section 4).  d_b[n] in, d_x[n] in: initial
+ * guess, out: solution.  *iters = preconditioner applications, *relres = final
+ * true relative residual.  Returns MGD_ENOCONV if max_it is reached. */
+int mgd_solve(mgd_ctx *c, const double *d_b, double tol, double *d_x, int *iters, double *relres);
+
+/* As mgd_solve with host buffers h_b[n], h_x[n] (x: initial guess in,
+ * solution out); copies in and out on the context's stream. */
+int mgd_solve_host(mgd_ctx *c, const double *h_b, double tol, double *h_x, int *iters, double *relres);
+
+/* Adjoint solve A^T lambda = g with the transposed preconditioner (the V-cycle
+ * run with A_l^T, the same P, R and smoother, and the transposed coarsest
+ * solve).  Needs opts.keep_transpose and kind MGD_AMG or MGD_BD. */
+int mgd_solve_transpose(mgd_ctx *c, const double *d_g, double tol, double *d_lambda, int *iters,
+                        double *relres);
+
+/* Gradient of a loss with respect to the stored values of A, given x = A^{-1} b
+ * and lambda = A^{-T} dL/dx: d_grad[k] = -lambda[row(k)] * x[col(k)], k < nnz. */
+int mgd_grad_values(mgd_ctx *c, const double *d_x, const double *d_lambda, double *d_grad);
+
+/* One application z = M^{-1} v of the preconditioner (d_v[n], d_z[n]). */
+int mgd_precond_apply(mgd_ctx *c, const double *d_v, double *d_z);
+
+/* Statistics of the current setup. */
+typedef struct mgd_stats {
+  int kind, G, N, n, nnz;
+  int n_ops;                  /* number of scalar operators inverted by the preconditioner */
+  int max_levels_used;        /* deepest hierarchy */
+  double grid_complexity;     /* sum over operators and levels of n_l / sum of n_0 */
+  double op_complexity;       /* sum of nnz(A_l) / sum of nnz(A_0) */
+  double setup_ms;            /* wall time of the last mgd_setup */
+  double solve_ms;            /* wall time of the last solve */
+  int last_iters;
+  double last_relres;
+  double vcycle_bytes;        /* algorithmic HBM bytes of one preconditioner apply (V-cycles only) */
+  double precond_bytes;       /* algorithmic bytes of one preconditioner apply including block updates */
+  double iter_bytes_base;     /* bytes of one FGMRES iteration outside the preconditioner, for j = 0 */
+  int n_dropped;              /* couplings dropped by the Section 3.6 rule */
+  int n_jacobi_ops;           /* operators approximated by option #1 */
+} mgd_stats;
+int mgd_get_stats(mgd_ctx *c, mgd_stats *s);
+
+/* Residual history of the last solve: h_hist[k] = Arnoldi estimate of the
+ * relative residual after preconditioner application k+1 (k < *count). */
+int mgd_get_history(mgd_ctx *c, double *h_hist, int cap, int *count);
+
+/* Introspection of operator `op` (index into the preconditioner's operator
+ * list, see mgd_op_info) for the parity tests. */
+int mgd_op_info(mgd_ctx *c, int op, int *kind, int *comp, int *nlevels, int *use_jacobi, int *coarse_lu);
+int mgd_level_info(mgd_ctx *c, int op, int level, int *n, int *nnz, int *nnzP, int *ncoarse);
+/* Copy level `level` of operator `op` to host buffers (any may be NULL):
+ * A_l as h_rp[n+1], h_ci[nnz], h_v[nnz]; C/F splitting h_cf[n] (1 = C,
+ * -1 = F; absent on the coarsest level); P_l as h_prp[n+1], h_pci[nnzP],
+ * h_pv[nnzP]. */
+int mgd_level_export(mgd_ctx *c, int op, int level, int *h_rp, int *h_ci, double *h_v, signed char *h_cf,
+                     int *h_prp, int *h_pci, double *h_pv);
+/* Block-level vectors (host copies, N entries): which = 0: PCTL p_a of
+ * component comp; 1: diagonal of A_comp; 2: coupling D_{comp,comp2}. Returns
+ * MGD_EINVAL when absent. */
+int mgd_block_vector(mgd_ctx *c, int which, int comp, int comp2, double *h_out);
+/* 1 if coupling D_{a,b} was dropped by the Section 3.6 rule. */
+int mgd_coupling_dropped(mgd_ctx *c, int a, int b);
+
+/* Kernel timing for the roofline: when enabled, CUDA events bracket every
+ * launch of the tracked kernel classes on the context's stream.  The read
+ * call synchronises the stream and returns, per class, the launch count, the
+ * summed device time and the summed algorithmic bytes (classes: 0 = level-0
+ * smoothing+residual kernels of the V-cycle, 1 = all V-cycle kernels, 2 = the
+ * FGMRES operator SpMV, 3 = Arnoldi vector kernels).  Enabling also turns
+ * off graph replay so that each launch is bracketed. */
+int mgd_profile_enable(mgd_ctx *c, int on);
+int mgd_profile_read(mgd_ctx *c, int cls, long long *launches, double *ms, double *bytes);
+
+/* Kernels this library has launched in the calling process so far (a graph
+ * replay counts each of its kernel nodes); a monotone counter for checking
+ * that work ran on the device. */
+long long mgd_kernel_launches(void);
+
+const char *mgd_last_error(mgd_ctx *c);
+void mgd_destroy(mgd_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1968 @@
+// mgd_host.cu -- host orchestration of the solver: AMG hierarchy setup on the
+// device (Section 3.1), batched V-cycle plans and their autotuner, the block
+// preconditioners (Sections 3.1, 3.3-3.6), right-preconditioned FGMRES(m)
+// (Section 2 and the stopping rule of Section 4) and the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mgdamg.h"
+#include "mgd_internal.cuh"
+
+namespace mgd {
+
+long long g_kernel_launches = 0;
+
+enum OpKind { OP_A = 0, OP_CE = 1, OP_CG = 2, OP_SG = 3, OP_SI = 4, OP_AC = 5, OP_MONO = 6 };
+
+// ------------------------------------------------------------------ profiler
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  cudaEvent_t get() {
+    if (used < pool.size()) return pool[used++];
+    cudaEvent_t e;
+    MGD_CUDA(cudaEventCreate(&e));
+    pool.push_back(e);
+    ++used;
+    return e;
+  }
+  void reset() {
+    recs.clear();
+    used = 0;
+  }
+  int begin(cudaStream_t s) {
+    if (!on) return -1;
+    cudaEvent_t a = get();
+    MGD_CUDA(cudaEventRecord(a, s));
+    recs.push_back({-1, a, nullptr, 0.0});
+    return (int)recs.size() - 1;
+  }
+  void end(int id, int cls, double bytes, cudaStream_t s) {
+    if (id < 0) return;
+    cudaEvent_t b = get();
+    MGD_CUDA(cudaEventRecord(b, s));
+    recs[id].cls = cls;
+    recs[id].b = b;
+    recs[id].bytes = bytes;
+  }
+  ~Profiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+// ------------------------------------------------------------------ options
+struct Opts {
+  mgd_opts o;
+};
+
+// ------------------------------------------------------------------ hierarchy
+struct Level {
+  Csr A;
+  float* v32 = nullptr;
+  Sell sell;
+  double* dinv = nullptr;
+  float* dinv32 = nullptr;
+  Csr P, R;
+  float *pv32 = nullptr, *rv32 = nullptr;
+  Csr AT;
+  float* atv32 = nullptr;
+  Sell sellT;
+  signed char* CF = nullptr;
+  int nc = 0;
+  void *b = nullptr, *x = nullptr, *xt = nullptr, *r = nullptr;
+};
+
+struct Hier {
+  std::vector<Level> L;
+  bool coarse_lu = false;
+  double* cinv = nullptr;
+  double* cinvT = nullptr;
+  int cn = 0;
+  int nlev() const { return (int)L.size(); }
+};
+
+struct SetupCtx {
+  Arena* arena;
+  cudaStream_t s;
+  const mgd_opts* o;
+  bool mixed;
+  bool keepT;
+};
+
+static Csr csr_alloc(Arena& a, int n, int m, int nnz) {
+  Csr c;
+  c.n = n;
+  c.m = m;
+  c.nnz = nnz;
+  c.rp = a.alloc<int>(n + 1);
+  c.ci = a.alloc<int>(nnz);
+  c.v = a.alloc<double>(nnz);
+  return c;
+}
+
+static Csr csr_copy(Arena& a, const Csr& x, cudaStream_t s) {
+  Csr c = csr_alloc(a, x.n, x.m, x.nnz);
+  MGD_CUDA(cudaMemcpyAsync(c.rp, x.rp, sizeof(int) * (x.n + 1), cudaMemcpyDeviceToDevice, s));
+  MGD_CUDA(cudaMemcpyAsync(c.ci, x.ci, sizeof(int) * x.nnz, cudaMemcpyDeviceToDevice, s));
+  MGD_CUDA(cudaMemcpyAsync(c.v, x.v, sizeof(double) * x.nnz, cudaMemcpyDeviceToDevice, s));
+  return c;
+}
+
+// C = X Y with the accumulation order of the Galerkin products (see setup_kernels.cu)
+static Csr spgemm(Arena& a, const Csr& X, const Csr& Y, cudaStream_t s) {
+  Scratch sc(s);
+  int n = X.n;
+  int* ub = sc.alloc<int>(n);
+  launch_spgemm_ub(n, X.rp, X.ci, Y.rp, ub, s);
+  long long* off = sc.alloc<long long>(n + 1);
+  launch_offsets64(ub, off, n, s);
+  long long total = 0;
+  MGD_CUDA(cudaMemcpyAsync(&total, off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  MGD_CUDA(cudaStreamSynchronize(s));
+  int* tc = sc.alloc<int>(total);
+  double* tv = sc.alloc<double>(total);
+  int* cnt = sc.alloc<int>(n);
+  launch_spgemm_expand(n, X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off, tc, tv, cnt, s);
+  Csr C;
+  C.n = n;
+  C.m = Y.m;
+  C.rp = a.alloc<int>(n + 1);
+  exclusive_scan(cnt, C.rp, n, s);
+  C.nnz = read_int(C.rp + n, s);
+  C.ci = a.alloc<int>(C.nnz);
+  C.v = a.alloc<double>(C.nnz);
+  launch_spgemm_compact(n, off, tc, tv, C.rp, C.ci, C.v, s);
+  return C;
+}
+
+static Csr transpose(Arena& a, const Csr& X, cudaStream_t s) {
+  Scratch sc(s);
+  Csr T;
+  T.n = X.m;
+  T.m = X.n;
+  T.nnz = X.nnz;
+  int* cnt = sc.alloc<int>(X.m);
+  MGD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * std::max(X.m, 1), s));
+  launch_transpose_count(X.nnz, X.ci, cnt, s);
+  T.rp = a.alloc<int>(T.n + 1);
+  exclusive_scan(cnt, T.rp, T.n, s);
+  T.ci = a.alloc<int>(T.nnz);
+  T.v = a.alloc<double>(T.nnz);
+  int* cur = sc.alloc<int>(X.m);
+  MGD_CUDA(cudaMemsetAsync(cur, 0, sizeof(int) * std::max(X.m, 1), s));
+  launch_transpose_fill(X.n, X.rp, X.ci, X.v, T.rp, cur, T.ci, T.v, s);
+  launch_sort_rows(T.n, T.rp, T.ci, T.v, s);
+  return T;
+}
+
+static Sell build_sell(Arena& a, const Csr& A, bool mixed, cudaStream_t s) {
+  Scratch sc(s);
+  Sell S;
+  S.n = A.n;
+  S.nslices = (A.n + 31) / 32;
+  int* w = sc.alloc<int>(S.nslices);
+  launch_sell_widths(A.n, A.rp, w, s);
+  S.sptr = a.alloc<int>(S.nslices + 1);
+  exclusive_scan(w, S.sptr, S.nslices, s);
+  S.nstored = read_int(S.sptr + S.nslices, s);
+  S.ci = a.alloc<int>(S.nstored);
+  S.v = a.alloc<double>(S.nstored);
+  launch_sell_fill(A.n, A.rp, A.ci, A.v, S.sptr, S.ci, S.v, s);
+  if (mixed) {
+    S.v32 = a.alloc<float>(S.nstored);
+    launch_cast_f64_f32((int)S.nstored, S.v, S.v32, s);
+  }
+  return S;
+}
+
+static float* cast32(Arena& a, const double* x, int n, cudaStream_t s) {
+  float* y = a.alloc<float>(n);
+  launch_cast_f64_f32(n, x, y, s);
+  return y;
+}
+
+// Section 3.1 setup: strength -> PMIS -> interpolation -> R = P^T -> A_c = R (A P),
+// level by level until the coarsest criterion; then smoother diagonals,
+// kernel layouts, FP32 copies and the coarsest dense inverse.
+static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
+  Arena& ar = *sc.arena;
+  cudaStream_t s = sc.s;
+  const mgd_opts& o = *sc.o;
+  h.L.clear();
+  h.L.emplace_back();
+  h.L[0].A = A0;
+  for (int l = 0;; ++l) {
+    Level& lv = h.L[l];
+    int n = lv.A.n;
+    if (n <= o.max_coarse || l == o.max_levels - 1) break;
+    Scratch tmp(s);
+    uint8_t* S = tmp.alloc<uint8_t>(lv.A.nnz);
+    launch_strength(n, lv.A.rp, lv.A.ci, lv.A.v, o.theta_str, S, s);
+    int* cnt = tmp.alloc<int>(n);
+    MGD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * n, s));
+    launch_count_st(n, lv.A.rp, lv.A.ci, S, cnt, s);
+    int* strp = tmp.alloc<int>(n + 1);
+    exclusive_scan(cnt, strp, n, s);
+    int nst = read_int(strp + n, s);
+    int* stci = tmp.alloc<int>(nst);
+    int* cur = tmp.alloc<int>(n);
+    MGD_CUDA(cudaMemsetAsync(cur, 0, sizeof(int) * n, s));
+    launch_fill_st(n, lv.A.rp, lv.A.ci, S, strp, cur, stci, s);
+    double* w = tmp.alloc<double>(n);
+    signed char* CF = ar.alloc<signed char>(n);
+    launch_pmis_init(n, lv.A.rp, S, cnt, o.seed, l, w, CF, s);
+    uint8_t* newc = tmp.alloc<uint8_t>(n);
+    int* und = tmp.alloc<int>(1);
+    for (int round = 0; round < n + 1; ++round) {
+      launch_pmis_round(n, lv.A.rp, lv.A.ci, S, strp, stci, w, CF, newc, und, s);
+      if (read_int(und, s) == 0) break;
+    }
+    int* pcnt = tmp.alloc<int>(n);
+    int* isc = tmp.alloc<int>(n);
+    launch_interp_count(n, lv.A.rp, lv.A.ci, S, CF, pcnt, isc, s);
+    int* cidx = tmp.alloc<int>(n + 1);
+    exclusive_scan(isc, cidx, n, s);
+    int nc = read_int(cidx + n, s);
+    if (nc == 0 || nc == n) break;  // coarsening stalled: this level is the coarsest
+    lv.CF = CF;
+    lv.nc = nc;
+    Csr P;
+    P.n = n;
+    P.m = nc;
+    P.rp = ar.alloc<int>(n + 1);
+    exclusive_scan(pcnt, P.rp, n, s);
+    P.nnz = read_int(P.rp + n, s);
+    P.ci = ar.alloc<int>(P.nnz);
+    P.v = ar.alloc<double>(P.nnz);
+    launch_interp_fill(n, lv.A.rp, lv.A.ci, lv.A.v, S, CF, cidx, P.rp, P.ci, P.v, s);
+    lv.P = P;
+    lv.R = transpose(ar, P, s);
+    Arena apa;
+    apa.stream = s;
+    Csr AP = spgemm(apa, lv.A, P, s);
+    Csr Ac = spgemm(ar, lv.R, AP, s);
+    MGD_CUDA(cudaStreamSynchronize(s));
+    apa.release();
+    h.L.emplace_back();
+    h.L.back().A = Ac;
+  }
+  // finalize levels
+  for (int l = 0; l < h.nlev(); ++l) {
+    Level& lv = h.L[l];
+    int n = lv.A.n;
+    lv.dinv = ar.alloc<double>(n);
+    launch_l1_dinv(n, lv.A.rp, lv.A.v, lv.dinv, s);
+    lv.sell = build_sell(ar, lv.A, sc.mixed, s);
+    if (sc.mixed) {
+      lv.v32 = cast32(ar, lv.A.v, lv.A.nnz, s);
+      lv.dinv32 = cast32(ar, lv.dinv, n, s);
+      if (l < h.nlev() - 1) {
+        lv.pv32 = cast32(ar, lv.P.v, lv.P.nnz, s);
+        lv.rv32 = cast32(ar, lv.R.v, lv.R.nnz, s);
+      }
+    }
+    if (sc.keepT) {
+      lv.AT = transpose(ar, lv.A, s);
+      lv.sellT = build_sell(ar, lv.AT, sc.mixed, s);
+      if (sc.mixed) lv.atv32 = cast32(ar, lv.AT.v, lv.AT.nnz, s);
+    }
+    size_t es = sc.mixed ? sizeof(float) : sizeof(double);
+    lv.b = ar.alloc<char>(es * n);
+    lv.x = ar.alloc<char>(es * n);
+    lv.xt = ar.alloc<char>(es * n);
+    lv.r = ar.alloc<char>(es * n);
+    MGD_CUDA(cudaMemsetAsync(lv.b, 0, es * n, s));
+    MGD_CUDA(cudaMemsetAsync(lv.x, 0, es * n, s));
+    MGD_CUDA(cudaMemsetAsync(lv.xt, 0, es * n, s));
+    MGD_CUDA(cudaMemsetAsync(lv.r, 0, es * n, s));
+  }
+  Level& last = h.L.back();
+  if (last.A.n <= o.max_coarse) {
+    int n = last.A.n;
+    Scratch tmp(s);
+    double* a = tmp.alloc<double>((size_t)n * n);
+    int* piv = tmp.alloc<int>(n);
+    int* st = tmp.alloc<int>(1);
+    MGD_CUDA(cudaMemsetAsync(st, 0, sizeof(int), s));
+    h.cinv = ar.alloc<double>((size_t)n * n);
+    h.cinvT = ar.alloc<double>((size_t)n * n);
+    launch_densify(n, last.A.rp, last.A.ci, last.A.v, a, s);
+    launch_dense_inverse(n, a, piv, h.cinv, h.cinvT, st, s);
+    if (read_int(st, s) != 0) throw Error{MGD_ESINGULAR, "zero pivot in the coarsest-level elimination"};
+    h.coarse_lu = true;
+    h.cn = n;
+  }
+}
+
+// ------------------------------------------------------------------ batched V-cycle plans
+template <typename T>
+struct VBatch {
+  std::vector<Hier*> hs;
+  int depth = 0;
+  struct LP {
+    LDesc<T>* d_down = nullptr;
+    int ndown = 0, maxn = 0, maxnc = 0;
+    LDesc<T>* d_clu = nullptr;
+    int nclu = 0, maxcn = 0;
+    LDesc<T>* d_cjac = nullptr;
+    int ncjac = 0, maxcj = 0;
+    int fmtA = FMT_SELL, fmtR = FMT_CSR4, fmtP = FMT_CSR1;
+    double bytes_pre = 0, bytes_post = 0, bytes_restrict = 0, bytes_prolong = 0, bytes_coarse = 0, bytes_jac = 0;
+  };
+  std::vector<LP> plan, planT;
+  double bytes_total = 0;
+};
+
+template <typename T>
+static const T* pick(const double* d, const float* f);
+template <>
+const double* pick<double>(const double* d, const float*) {
+  return d;
+}
+template <>
+const float* pick<float>(const double*, const float* f) {
+  return f;
+}
+
+template <typename T>
+static LDesc<T> make_desc(Hier& h, int l, bool trans) {
+  Level& lv = h.L[l];
+  LDesc<T> d;
+  memset(&d, 0, sizeof(d));
+  d.n = lv.A.n;
+  d.nc = lv.nc;
+  const Csr& A = trans ? lv.AT : lv.A;
+  const Sell& S = trans ? lv.sellT : lv.sell;
+  d.rp = A.rp;
+  d.ci = A.ci;
+  d.v = pick<T>(A.v, trans ? lv.atv32 : lv.v32);
+  d.sptr = S.sptr;
+  d.sci = S.ci;
+  d.sv = pick<T>(S.v, S.v32);
+  d.dinv = pick<T>(lv.dinv, lv.dinv32);
+  if (l < h.nlev() - 1) {
+    d.prp = lv.P.rp;
+    d.pci = lv.P.ci;
+    d.pv = pick<T>(lv.P.v, lv.pv32);
+    d.rrp = lv.R.rp;
+    d.rci = lv.R.ci;
+    d.rv = pick<T>(lv.R.v, lv.rv32);
+    d.bc = (T*)h.L[l + 1].b;
+    d.xc = (T*)h.L[l + 1].x;
+  }
+  d.b = (T*)lv.b;
+  d.x = (T*)lv.x;
+  d.xt = (T*)lv.xt;
+  d.r = (T*)lv.r;
+  d.cinv = trans ? h.cinvT : h.cinv;
+  d.cn = h.cn;
+  return d;
+}
+
+static double sp_bytes(long long nnz, long long rows, int sv) { return (double)nnz * (sv + 4) + 4.0 * (rows + 1); }
+
+template <typename T>
+static void build_plan(Arena& ar, VBatch<T>& vb, bool trans, cudaStream_t s) {
+  auto& plan = trans ? vb.planT : vb.plan;
+  vb.depth = 0;
+  for (Hier* h : vb.hs) vb.depth = std::max(vb.depth, h->nlev());
+  plan.assign(vb.depth, typename VBatch<T>::LP());
+  const int sv = sizeof(T);
+  double total = 0;
+  for (int l = 0; l < vb.depth; ++l) {
+    auto& lp = plan[l];
+    std::vector<LDesc<T>> down, clu, cjac;
+    for (Hier* h : vb.hs) {
+      if (l >= h->nlev()) continue;
+      Level& lv = h->L[l];
+      LDesc<T> d = make_desc<T>(*h, l, trans);
+      long long n = lv.A.n, nnz = lv.A.nnz;
+      if (l < h->nlev() - 1) {
+        down.push_back(d);
+        lp.maxn = std::max<int>(lp.maxn, (int)n);
+        lp.maxnc = std::max(lp.maxnc, lv.nc);
+        lp.bytes_pre += sp_bytes(nnz, n, sv) + 4.0 * sv * n;
+        lp.bytes_post += sp_bytes(nnz, n, sv) + 4.0 * sv * n;
+        lp.bytes_restrict += sp_bytes(lv.R.nnz, lv.nc, sv) + (double)sv * (n + lv.nc);
+        lp.bytes_prolong += sp_bytes(lv.P.nnz, n, sv) + (double)sv * (lv.nc + 2 * n);
+      } else if (h->coarse_lu) {
+        clu.push_back(d);
+        lp.maxcn = std::max(lp.maxcn, h->cn);
+        lp.bytes_coarse += 8.0 * h->cn * h->cn + 2.0 * sv * h->cn;
+      } else {
+        cjac.push_back(d);
+        lp.maxcj = std::max<int>(lp.maxcj, (int)n);
+        lp.bytes_jac += 3.0 * sv * n;
+        lp.bytes_post += sp_bytes(nnz, n, sv) + 4.0 * sv * n;
+      }
+    }
+    auto upload = [&](std::vector<LDesc<T>>& v, LDesc<T>*& dst) {
+      if (v.empty()) return;
+      dst = ar.alloc<LDesc<T>>(v.size());
+      MGD_CUDA(cudaMemcpyAsync(dst, v.data(), sizeof(LDesc<T>) * v.size(), cudaMemcpyHostToDevice, s));
+    };
+    upload(down, lp.d_down);
+    upload(clu, lp.d_clu);
+    upload(cjac, lp.d_cjac);
+    lp.ndown = (int)down.size();
+    lp.nclu = (int)clu.size();
+    lp.ncjac = (int)cjac.size();
+    total += lp.bytes_pre + lp.bytes_post + lp.bytes_restrict + lp.bytes_prolong + lp.bytes_coarse + lp.bytes_jac;
+  }
+  if (!trans) vb.bytes_total = total;
+  MGD_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope
+}
+
+template <typename T>
+static void run_vbatch(VBatch<T>& vb, bool trans, cudaStream_t s, Profiler& prof) {
+  auto& plan = trans ? vb.planT : vb.plan;
+  for (int l = 0; l < vb.depth; ++l) {
+    auto& lp = plan[l];
+    if (lp.ndown) {
+      int id = prof.begin(s);
+      launch_phase<T>(PH_PRE, lp.fmtA, lp.fmtR, lp.d_down, lp.ndown, lp.maxn, s);
+      prof.end(id, l == 0 ? 0 : 1, lp.bytes_pre, s);
+      id = prof.begin(s);
+      launch_phase<T>(PH_RESTRICT, lp.fmtA, lp.fmtR, lp.d_down, lp.ndown, lp.maxnc, s);
+      prof.end(id, 1, lp.bytes_restrict, s);
+    }
+    if (lp.nclu) {
+      int id = prof.begin(s);
+      launch_phase<T>(PH_COARSE, lp.fmtA, lp.fmtR, lp.d_clu, lp.nclu, lp.maxcn, s);
+      prof.end(id, 1, lp.bytes_coarse, s);
+    }
+    if (lp.ncjac) {
+      int id = prof.begin(s);
+      launch_phase<T>(PH_JAC1, lp.fmtA, lp.fmtR, lp.d_cjac, lp.ncjac, lp.maxcj, s);
+      launch_phase<T>(PH_POST, lp.fmtA, lp.fmtR, lp.d_cjac, lp.ncjac, lp.maxcj, s);
+      prof.end(id, l == 0 ? 0 : 1, lp.bytes_jac, s);
+    }
+  }
+  for (int l = vb.depth - 2; l >= 0; --l) {
+    auto& lp = plan[l];
+    if (!lp.ndown) continue;
+    int id = prof.begin(s);
+    launch_phase<T>(PH_PROLONG, lp.fmtA, lp.fmtP, lp.d_down, lp.ndown, lp.maxn, s);
+    prof.end(id, 1, lp.bytes_prolong, s);
+    id = prof.begin(s);
+    launch_phase<T>(PH_POST, lp.fmtA, lp.fmtP, lp.d_down, lp.ndown, lp.maxn, s);
+    prof.end(id, l == 0 ? 0 : 1, lp.bytes_post, s);
+  }
+}
+
+// Autotuner: per level of a batch, time the operator phase (PRE) under each
+// sparse layout and the transfer phases under each threads-per-row choice;
+// keep the fastest.  Inputs are the level buffers (zero at setup).
+template <typename T>
+static void autotune(VBatch<T>& vb, bool trans, cudaStream_t s) {
+  auto& plan = trans ? vb.planT : vb.plan;
+  cudaEvent_t e0, e1;
+  MGD_CUDA(cudaEventCreate(&e0));
+  MGD_CUDA(cudaEventCreate(&e1));
+  auto time_it = [&](auto fn) {
+    fn();
+    MGD_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) fn();
+    MGD_CUDA(cudaEventRecord(e1, s));
+    MGD_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    MGD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return ms;
+  };
+  const int candA[] = {FMT_SELL, FMT_CSR1, FMT_CSR2, FMT_CSR4, FMT_CSR8};
+  const int candRP[] = {FMT_CSR1, FMT_CSR2, FMT_CSR4, FMT_CSR8};
+  for (int l = 0; l < vb.depth; ++l) {
+    auto& lp = plan[l];
+    if (!lp.ndown) continue;
+    float best = 1e30f;
+    for (int f : candA) {
+      float ms = time_it([&] { launch_phase<T>(PH_PRE, f, lp.fmtR, lp.d_down, lp.ndown, lp.maxn, s); });
+      if (ms < best) {
+        best = ms;
+        lp.fmtA = f;
+      }
+    }
+    best = 1e30f;
+    for (int f : candRP) {
+      float ms = time_it([&] { launch_phase<T>(PH_RESTRICT, lp.fmtA, f, lp.d_down, lp.ndown, lp.maxnc, s); });
+      if (ms < best) {
+        best = ms;
+        lp.fmtR = f;
+      }
+    }
+    best = 1e30f;
+    for (int f : candRP) {
+      float ms = time_it([&] { launch_phase<T>(PH_PROLONG, lp.fmtA, f, lp.d_down, lp.ndown, lp.maxn, s); });
+      if (ms < best) {
+        best = ms;
+        lp.fmtP = f;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
+// ------------------------------------------------------------------ block preconditioner
+struct InvOp {
+  int kind, comp;
+  Csr A;               // operator (FP64)
+  bool jacobi = false; // option #1
+  int count = 1;       // sweeps (#1) or V-cycles (#2)
+  Hier h;
+  double* jd = nullptr;  // 1/diag(A)
+  float* jd32 = nullptr;
+  void* b = nullptr;     // rhs (type T): level-0 b of the hierarchy, or own buffer for #1
+  void* x = nullptr;     // output (type T)
+  void* bsave = nullptr; // extra buffers for several cycles / sweeps
+  void* xacc = nullptr;
+  int n = 0;
+  float* v32 = nullptr;
+  void* d_jac = nullptr;   // JacDesc<T>: x = D^-1 b
+  void* d_jac2 = nullptr;  // JacDesc<T>: xacc = D^-1 bsave (further sweeps)
+};
+
+struct Step {
+  enum { PRODUCE, INVERT, CONSUME, BLOCKRESID } type;
+  void* descs = nullptr;  // device descriptors
+  int nd = 0;
+  int len = 0;            // vector length of produce/consume
+  std::vector<int> ops;   // INVERT
+  int batch = -1;         // index into batches when batched
+  double bytes = 0;
+};
+
+struct BlockData {
+  int G = 0, N = 0, nc = 0;
+  std::vector<Csr> Ab;              // diagonal blocks
+  std::vector<double*> d;           // nc*nc coupling vectors (nullptr: absent/dropped)
+  std::vector<int> dropped;
+  std::vector<double*> diag;        // diag(A_a)
+  std::vector<double*> p;           // PCTL p_a
+  Csr Ac;
+  double** d_dtab = nullptr;        // device copy of d
+  int** d_brp = nullptr;
+  int** d_bci = nullptr;
+  double** d_bv = nullptr;
+};
+
+}  // namespace mgd
+
+// ------------------------------------------------------------------ context
+struct mgd_ctx {
+  mgd_opts o;
+  cudaStream_t s = nullptr;
+  int device = 0;
+  std::string err;
+  mgd::Arena ar;
+  bool ready = false;
+  int kind = 0, G = 0, N = 0, n = 0, nnz = 0;
+  mgd::Csr A;      // monolithic operator (FP64)
+  mgd::Sell Asell;
+  int fmtMono = mgd::FMT_SELL;
+  mgd::Csr AT;
+  mgd::Sell ATsell;
+  mgd::BlockData bd;
+  std::vector<mgd::InvOp> ops;
+  std::vector<mgd::Step> steps, stepsT;
+  std::vector<mgd::VBatch<double>> vb64;
+  std::vector<mgd::VBatch<float>> vb32;
+  mgd::IOSlots* io = nullptr;
+  double *wEs = nullptr, *wIs = nullptr, *rfull = nullptr;
+  // FGMRES storage
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *hbuf = nullptr, *partial = nullptr,
+         *ybuf = nullptr, *xtmp = nullptr, *btmp = nullptr;
+  double* hpin = nullptr;  // pinned host
+  int m = 30;
+  std::vector<double> hist;
+  mgd::Profiler prof;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_ok = false;
+  long long graph_nodes = 0;
+  mgd_stats st;
+  int n_jacobi = 0;
+};
+
+namespace mgd {
+
+static bool mixed(const mgd_ctx* c) { return c->o.precision == 1; }
+
+static PRef ABS(double* p) { return PRef{0, 0, p}; }
+static PRef VIN(long long off) { return PRef{1, off, nullptr}; }
+static PRef ZOUT(long long off) { return PRef{2, off, nullptr}; }
+static PRef NUL() { return PRef{0, 0, nullptr}; }
+
+template <typename T>
+static void add_produce(mgd_ctx* c, std::vector<ProduceDesc<T>>& v, int op, PRef a,
+                        std::vector<std::tuple<const double*, PRef, double>> terms) {
+  ProduceDesc<T> d;
+  memset(&d, 0, sizeof(d));
+  d.dst = (T*)c->ops[op].b;
+  d.a = a;
+  d.nt = 0;
+  for (auto& t : terms) {
+    if (d.nt >= kMaxTerms) throw Error{MGD_EINVAL, "too many coupling terms"};
+    d.d[d.nt] = std::get<0>(t);
+    d.w[d.nt] = std::get<1>(t);
+    d.s[d.nt] = std::get<2>(t);
+    d.nt++;
+  }
+  v.push_back(d);
+}
+
+template <typename T>
+static void add_consume(std::vector<ConsumeDesc<T>>& v, PRef dst, PRef base, double s, const void* x,
+                        const double* dvec = nullptr) {
+  ConsumeDesc<T> d;
+  memset(&d, 0, sizeof(d));
+  d.dst = dst;
+  d.base = base;
+  d.s = s;
+  d.x = (const T*)x;
+  (void)dvec;
+  v.push_back(d);
+}
+
+template <typename D>
+static void* upload_vec(mgd_ctx* c, const std::vector<D>& v) {
+  if (v.empty()) return nullptr;
+  D* d = c->ar.alloc<D>(v.size());
+  MGD_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(D) * v.size(), cudaMemcpyHostToDevice, c->s));
+  MGD_CUDA(cudaStreamSynchronize(c->s));
+  return d;
+}
+
+template <typename T>
+static void push_produce(mgd_ctx* c, std::vector<Step>& steps, std::vector<ProduceDesc<T>> v, int len) {
+  Step st;
+  st.type = Step::PRODUCE;
+  st.nd = (int)v.size();
+  st.len = len;
+  st.descs = upload_vec(c, v);
+  for (auto& d : v) st.bytes += (double)len * (sizeof(T) + (d.a.slot || d.a.abs ? 8 : 0) + 16.0 * d.nt);
+  steps.push_back(st);
+}
+template <typename T>
+static void push_consume(mgd_ctx* c, std::vector<Step>& steps, std::vector<ConsumeDesc<T>> v, int len) {
+  Step st;
+  st.type = Step::CONSUME;
+  st.nd = (int)v.size();
+  st.len = len;
+  st.descs = upload_vec(c, v);
+  for (auto& d : v) st.bytes += (double)len * (sizeof(T) + 8 + (d.base.slot || d.base.abs ? 8 : 0));
+  steps.push_back(st);
+}
+static void push_invert(std::vector<Step>& steps, std::vector<int> ops) {
+  Step st;
+  st.type = Step::INVERT;
+  st.ops = ops;
+  steps.push_back(st);
+}
+
+// ------------------------------------------------------------------ inverse operators
+template <typename T>
+static void finalize_op(mgd_ctx* c, InvOp& op) {
+  const size_t es = sizeof(T);
+  op.n = op.A.n;
+  if (op.jacobi) {
+    op.jd = c->ar.alloc<double>(op.n);
+    launch_diag_inv(op.n, op.A.rp, op.A.ci, op.A.v, op.jd, c->s);
+    if (mixed(c)) {
+      op.jd32 = cast32(c->ar, op.jd, op.n, c->s);
+      op.v32 = cast32(c->ar, op.A.v, op.A.nnz, c->s);
+    }
+    op.b = c->ar.alloc<char>(es * op.n, true);
+    op.x = c->ar.alloc<char>(es * op.n, true);
+  } else {
+    SetupCtx sc{&c->ar, c->s, &c->o, mixed(c), c->o.keep_transpose != 0};
+    build_hierarchy(sc, op.h, op.A);
+    op.b = op.h.L[0].b;
+    op.x = op.h.L[0].x;
+  }
+  if (op.count > 1) {
+    op.bsave = c->ar.alloc<char>(es * op.n, true);
+    op.xacc = c->ar.alloc<char>(es * op.n, true);
+  }
+  if (op.jacobi) {
+    JacDesc<T> j1{(T*)op.x, (const T*)op.b, pick<T>(op.jd, op.jd32)};
+    JacDesc<T> j2{(T*)op.xacc, (const T*)op.bsave, pick<T>(op.jd, op.jd32)};
+    JacDesc<T>* d = c->ar.alloc<JacDesc<T>>(2);
+    MGD_CUDA(cudaMemcpyAsync(d, &j1, sizeof(j1), cudaMemcpyHostToDevice, c->s));
+    MGD_CUDA(cudaMemcpyAsync(d + 1, &j2, sizeof(j2), cudaMemcpyHostToDevice, c->s));
+    MGD_CUDA(cudaStreamSynchronize(c->s));
+    op.d_jac = d;
+    op.d_jac2 = d + 1;
+  }
+}
+
+static int cycles_for(const mgd_opts& o, int kind, int comp, int G) {
+  if (kind == OP_AC || kind == OP_MONO) return o.nvcyc_other;
+  if (comp < G) return o.nvcyc_group;
+  if (comp == G) return o.nvcyc_E;
+  return o.nvcyc_I;
+}
+
+static double gamma_wd(mgd_ctx* c, const Csr& A) {
+  Scratch sc(c->s);
+  int* cnt = sc.alloc<int>(1);
+  MGD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), c->s));
+  launch_gamma_wd(A.n, A.rp, A.ci, A.v, c->o.theta_wd, cnt, c->s);
+  return A.n ? (double)read_int(cnt, c->s) / A.n : 0.0;
+}
+
+static int add_op(mgd_ctx* c, int kind, int comp, Csr A) {
+  InvOp op;
+  op.kind = kind;
+  op.comp = comp;
+  op.A = A;
+  op.jacobi = c->o.adaptive && kind != OP_MONO && gamma_wd(c, A) == 0.0;
+  op.count = op.jacobi ? c->o.jacobi_sweeps : cycles_for(c->o, kind, comp, c->G);
+  if (op.count < 1) op.count = 1;
+  c->ops.push_back(op);
+  return (int)c->ops.size() - 1;
+}
+
+static Csr diag_modified(mgd_ctx* c, const Csr& A, const double* x, const double* y, const double* z) {
+  Csr M = csr_copy(c->ar, A, c->s);
+  if (x && y) launch_diag_modify(M.n, M.rp, M.ci, M.v, x, y, z, c->s);
+  return M;
+}
+
+// run option #1 / #2 for a list of operators (one batch when batched)
+template <typename T>
+static void run_invert(mgd_ctx* c, const Step& st, bool trans);
+
+template <typename T>
+std::vector<VBatch<T>>& batches(mgd_ctx* c);
+template <>
+std::vector<VBatch<double>>& batches<double>(mgd_ctx* c) {
+  return c->vb64;
+}
+template <>
+std::vector<VBatch<float>>& batches<float>(mgd_ctx* c) {
+  return c->vb32;
+}
+
+template <typename T>
+static void apply_jacobi_ops(mgd_ctx* c, const std::vector<int>& ids, bool trans) {
+  // option #1: x = D^-1 b, then further sweeps x += D^-1 (b - A x).  D is
+  // diagonal, so the transposed operator uses the same D; the residual of
+  // further sweeps uses A^T in the transposed apply.
+  for (int id : ids) {
+    InvOp& op = c->ops[id];
+    launch_jacobi<T>((const JacDesc<T>*)op.d_jac, 1, op.n, c->s);
+    for (int k = 1; k < op.count; ++k) {
+      const Csr& A = op.A;
+      launch_residual<T>(FMT_CSR4, op.n, A.rp, A.ci, pick<T>(A.v, op.v32), nullptr, nullptr, nullptr,
+                         (const T*)op.b, (const T*)op.x, (T*)op.bsave, c->s);
+      launch_jacobi<T>((const JacDesc<T>*)op.d_jac2, 1, op.n, c->s);
+      launch_axpy<T>(op.n, (T*)op.x, (const T*)op.xacc, c->s);
+    }
+    (void)trans;
+  }
+}
+
+template <typename T>
+static void run_invert(mgd_ctx* c, const Step& st, bool trans) {
+  std::vector<int> jac, vc;
+  for (int id : st.ops) (c->ops[id].jacobi ? jac : vc).push_back(id);
+  apply_jacobi_ops<T>(c, jac, trans);
+  if (vc.empty()) return;
+  auto& B = batches<T>(c)[st.batch];
+  int maxcount = 1;
+  for (int id : vc) maxcount = std::max(maxcount, c->ops[id].count);
+  if (maxcount == 1) {
+    run_vbatch<T>(B, trans, c->s, c->prof);
+    return;
+  }
+  // several V-cycles: x = V b; repeat: x += V (b - A x)   (per operator)
+  for (int id : vc) {
+    InvOp& op = c->ops[id];
+    MGD_CUDA(cudaMemcpyAsync(op.bsave, op.b, sizeof(T) * op.n, cudaMemcpyDeviceToDevice, c->s));
+  }
+  run_vbatch<T>(B, trans, c->s, c->prof);
+  for (int id : vc) {
+    InvOp& op = c->ops[id];
+    MGD_CUDA(cudaMemcpyAsync(op.xacc, op.x, sizeof(T) * op.n, cudaMemcpyDeviceToDevice, c->s));
+  }
+  for (int k = 1; k < maxcount; ++k) {
+    for (int id : vc) {
+      InvOp& op = c->ops[id];
+      Level& l0 = op.h.L[0];
+      const Csr& A = trans ? l0.AT : l0.A;
+      const T* av = pick<T>(A.v, trans ? l0.atv32 : l0.v32);
+      if (k < op.count)
+        launch_residual<T>(FMT_CSR4, op.n, A.rp, A.ci, av, nullptr, nullptr, nullptr, (const T*)op.bsave,
+                           (const T*)op.xacc, (T*)op.b, c->s);
+      else
+        MGD_CUDA(cudaMemsetAsync(op.b, 0, sizeof(T) * op.n, c->s));
+    }
+    run_vbatch<T>(B, trans, c->s, c->prof);
+    for (int id : vc) {
+      InvOp& op = c->ops[id];
+      if (k < op.count) launch_axpy<T>(op.n, (T*)op.xacc, (const T*)op.x, c->s);
+    }
+  }
+  for (int id : vc) {
+    InvOp& op = c->ops[id];
+    MGD_CUDA(cudaMemcpyAsync(op.x, op.xacc, sizeof(T) * op.n, cudaMemcpyDeviceToDevice, c->s));
+    MGD_CUDA(cudaMemcpyAsync(op.b, op.bsave, sizeof(T) * op.n, cudaMemcpyDeviceToDevice, c->s));
+  }
+}
+
+template <typename T>
+static void run_step(mgd_ctx* c, const Step& st, bool trans) {
+  {
+    switch (st.type) {
+      case Step::PRODUCE: {
+        int id = c->prof.begin(c->s);
+        launch_produce<T>((const ProduceDesc<T>*)st.descs, st.nd, st.len, c->io, c->s);
+        c->prof.end(id, 4, st.bytes, c->s);
+        break;
+      }
+      case Step::CONSUME: {
+        int id = c->prof.begin(c->s);
+        launch_consume<T>((const ConsumeDesc<T>*)st.descs, st.nd, st.len, c->io, c->s);
+        c->prof.end(id, 4, st.bytes, c->s);
+        break;
+      }
+      case Step::INVERT:
+        run_invert<T>(c, st, trans);
+        break;
+      case Step::BLOCKRESID: {
+        int id = c->prof.begin(c->s);
+        launch_block_resid(c->N, c->bd.nc, (const int* const*)c->bd.d_brp, (const int* const*)c->bd.d_bci,
+                           (const double* const*)c->bd.d_bv, (const double* const*)c->bd.d_dtab, c->io,
+                           c->rfull, c->s);
+        c->prof.end(id, 4, st.bytes, c->s);
+        break;
+      }
+    }
+  }
+}
+
+// Build the step program of each preconditioner kind and group the inverse
+// operators of each INVERT step into V-cycle batches.
+template <typename T>
+static void build_program(mgd_ctx* c) {
+  const int G = c->G, N = c->N, nc = G + 2, E = G, I = G + 1;
+  BlockData& bd = c->bd;
+  auto D = [&](int a, int b) -> const double* { return bd.d.empty() ? nullptr : bd.d[a * nc + b]; };
+  std::vector<Step>& S = c->steps;
+  S.clear();
+  auto blk = [&](int a) { return (long long)a * N; };
+  std::vector<int> opA(nc, -1);
+  auto produce1 = [&](int op, PRef a, std::vector<std::tuple<const double*, PRef, double>> t) {
+    std::vector<ProduceDesc<T>> v;
+    add_produce<T>(c, v, op, a, t);
+    push_produce<T>(c, S, v, c->ops[op].n);
+  };
+  auto consume1 = [&](int op, PRef dst, PRef base, double s) {
+    std::vector<ConsumeDesc<T>> v;
+    add_consume<T>(v, dst, base, s, c->ops[op].x);
+    push_consume<T>(c, S, v, c->ops[op].n);
+  };
+  switch (c->kind) {
+    case MGD_AMG: {
+      int op = 0;
+      produce1(op, VIN(0), {});
+      push_invert(S, {op});
+      consume1(op, ZOUT(0), NUL(), 1.0);
+      break;
+    }
+    case MGD_BD: {
+      std::vector<ProduceDesc<T>> pv;
+      std::vector<ConsumeDesc<T>> cv;
+      std::vector<int> all;
+      for (int a = 0; a < nc; ++a) {
+        add_produce<T>(c, pv, a, VIN(blk(a)), {});
+        add_consume<T>(cv, ZOUT(blk(a)), NUL(), 1.0, c->ops[a].x);
+        all.push_back(a);
+      }
+      push_produce<T>(c, S, pv, N);
+      push_invert(S, all);
+      push_consume<T>(c, S, cv, N);
+      break;
+    }
+    case MGD_BLT: {
+      std::vector<ProduceDesc<T>> pv;
+      std::vector<ConsumeDesc<T>> cv;
+      std::vector<int> groups;
+      for (int g = 0; g < G; ++g) {
+        add_produce<T>(c, pv, g, VIN(blk(g)), {});
+        add_consume<T>(cv, ZOUT(blk(g)), NUL(), 1.0, c->ops[g].x);
+        groups.push_back(g);
+      }
+      push_produce<T>(c, S, pv, N);
+      push_invert(S, groups);
+      push_consume<T>(c, S, cv, N);
+      std::vector<std::tuple<const double*, PRef, double>> t;
+      for (int g = 0; g < G; ++g)
+        if (D(E, g)) t.emplace_back(D(E, g), ZOUT(blk(g)), -1.0);
+      produce1(E, VIN(blk(E)), t);
+      push_invert(S, {E});
+      consume1(E, ZOUT(blk(E)), NUL(), 1.0);
+      t.clear();
+      if (D(I, E)) t.emplace_back(D(I, E), ZOUT(blk(E)), -1.0);
+      produce1(I, VIN(blk(I)), t);
+      push_invert(S, {I});
+      consume1(I, ZOUT(blk(I)), NUL(), 1.0);
+      break;
+    }
+    case MGD_SCHUR1: {
+      // ops: 0 = A_I, 1 = C_E, 2.. = C_g
+      int oAI = 0, oCE = 1;
+      std::vector<std::tuple<const double*, PRef, double>> t;
+      produce1(oAI, VIN(blk(I)), {});                                       // 1
+      push_invert(S, {oAI});
+      consume1(oAI, ABS(c->wIs), NUL(), 1.0);
+      if (D(E, I)) t.emplace_back(D(E, I), ABS(c->wIs), -1.0);               // 2
+      produce1(oCE, VIN(blk(E)), t);
+      push_invert(S, {oCE});
+      consume1(oCE, ABS(c->wEs), NUL(), 1.0);
+      std::vector<ProduceDesc<T>> pv;                                        // 3
+      std::vector<ConsumeDesc<T>> cv;
+      std::vector<int> gs;
+      for (int g = 0; g < G; ++g) {
+        t.clear();
+        if (D(g, E)) t.emplace_back(D(g, E), ABS(c->wEs), -1.0);
+        add_produce<T>(c, pv, 2 + g, VIN(blk(g)), t);
+        add_consume<T>(cv, ZOUT(blk(g)), NUL(), 1.0, c->ops[2 + g].x);
+        gs.push_back(2 + g);
+      }
+      push_produce<T>(c, S, pv, N);
+      push_invert(S, gs);
+      push_consume<T>(c, S, cv, N);
+      t.clear();                                                             // 4
+      for (int g = 0; g < G; ++g)
+        if (D(E, g)) t.emplace_back(D(E, g), ZOUT(blk(g)), 1.0);
+      produce1(oCE, NUL(), t);
+      push_invert(S, {oCE});
+      consume1(oCE, ZOUT(blk(E)), ABS(c->wEs), -1.0);
+      t.clear();                                                             // 5
+      if (D(I, E)) t.emplace_back(D(I, E), ZOUT(blk(E)), 1.0);
+      produce1(oAI, NUL(), t);
+      push_invert(S, {oAI});
+      consume1(oAI, ZOUT(blk(I)), ABS(c->wIs), -1.0);
+      break;
+    }
+    case MGD_SCHUR2: {
+      // ops: 0 = A_E, 1..G = S_g, G+1 = S_I
+      int oAE = 0, oSI = G + 1;
+      std::vector<std::tuple<const double*, PRef, double>> t;
+      produce1(oAE, VIN(blk(E)), {});                                        // 1
+      push_invert(S, {oAE});
+      consume1(oAE, ABS(c->wEs), NUL(), 1.0);
+      std::vector<ProduceDesc<T>> pv;                                        // 2
+      std::vector<ConsumeDesc<T>> cv;
+      std::vector<int> gs;
+      for (int g = 0; g < G; ++g) {
+        t.clear();
+        if (D(g, E)) t.emplace_back(D(g, E), ABS(c->wEs), -1.0);
+        add_produce<T>(c, pv, 1 + g, VIN(blk(g)), t);
+        add_consume<T>(cv, ZOUT(blk(g)), NUL(), 1.0, c->ops[1 + g].x);
+        gs.push_back(1 + g);
+      }
+      t.clear();
+      if (D(I, E)) t.emplace_back(D(I, E), ABS(c->wEs), -1.0);
+      add_produce<T>(c, pv, oSI, VIN(blk(I)), t);
+      add_consume<T>(cv, ZOUT(blk(I)), NUL(), 1.0, c->ops[oSI].x);
+      gs.push_back(oSI);
+      push_produce<T>(c, S, pv, N);
+      push_invert(S, gs);
+      push_consume<T>(c, S, cv, N);
+      t.clear();                                                             // 3
+      for (int g = 0; g < G; ++g)
+        if (D(E, g)) t.emplace_back(D(E, g), ZOUT(blk(g)), 1.0);
+      if (D(E, I)) t.emplace_back(D(E, I), ZOUT(blk(I)), 1.0);
+      produce1(oAE, NUL(), t);
+      push_invert(S, {oAE});
+      consume1(oAE, ZOUT(blk(E)), ABS(c->wEs), -1.0);
+      break;
+    }
+    case MGD_PCTL: {
+      // ops: 0..nc-1 = A_a, nc = A_c
+      int oAc = nc;
+      produce1(E, VIN(blk(E)), {});                                          // 1: E first
+      push_invert(S, {E});
+      consume1(E, ZOUT(blk(E)), NUL(), 1.0);
+      std::vector<ProduceDesc<T>> pv;
+      std::vector<ConsumeDesc<T>> cv;
+      std::vector<int> others;
+      for (int a = 0; a < nc; ++a) {
+        if (a == E) continue;
+        std::vector<std::tuple<const double*, PRef, double>> t;
+        if (D(a, E)) t.emplace_back(D(a, E), ZOUT(blk(E)), -1.0);
+        add_produce<T>(c, pv, a, VIN(blk(a)), t);
+        add_consume<T>(cv, ZOUT(blk(a)), NUL(), 1.0, c->ops[a].x);
+        others.push_back(a);
+      }
+      push_produce<T>(c, S, pv, N);
+      push_invert(S, others);
+      push_consume<T>(c, S, cv, N);
+      Step br;                                                               // 2: r = b - A w
+      br.type = Step::BLOCKRESID;
+      br.bytes = 0;
+      for (int a = 0; a < nc; ++a) br.bytes += sp_bytes(bd.Ab[a].nnz, N, 8) + 24.0 * N;
+      S.push_back(br);
+      std::vector<std::tuple<const double*, PRef, double>> t;
+      for (int a = 0; a < nc; ++a) t.emplace_back(a == E ? nullptr : bd.p[a], ABS(c->rfull + blk(a)), 1.0);
+      produce1(oAc, NUL(), t);
+      push_invert(S, {oAc});
+      // 3: w_a += p_a (.) w_c with p_E = 1: w_c to FP64, then a z-relative update
+      std::vector<ConsumeDesc<T>> cc;
+      add_consume<T>(cc, ABS(c->wEs), NUL(), 1.0, c->ops[oAc].x);  // w_c in FP64
+      push_consume<T>(c, S, cc, N);
+      Step upd;
+      upd.type = Step::PRODUCE;
+      {
+        // destination offsets relative to the z slot (dst holds the offset)
+        std::vector<ProduceDesc<double>> zp;
+        for (int a = 0; a < nc; ++a) {
+          ProduceDesc<double> d;
+          memset(&d, 0, sizeof(d));
+          d.dst = reinterpret_cast<double*>((long long)blk(a));  // offset, resolved against z
+          d.a = ZOUT(blk(a));
+          d.nt = 1;
+          d.d[0] = a == E ? nullptr : bd.p[a];
+          d.w[0] = ABS(c->wEs);
+          d.s[0] = 1.0;
+          zp.push_back(d);
+        }
+        upd.descs = upload_vec(c, zp);
+        upd.nd = nc;
+        upd.len = N;
+        upd.bytes = nc * 32.0 * N;
+        upd.batch = -2;  // marks the z-relative FP64 update
+      }
+      S.push_back(upd);
+      break;
+    }
+  }
+}
+
+}  // namespace mgd
+
+// z-relative FP64 update kernel used by the PCTL coarse-grid correction
+namespace mgd {
+__global__ void k_zupdate(const ProduceDesc<double>* __restrict__ ds, int N, const IOSlots* __restrict__ io) {
+  const ProduceDesc<double>* d = ds + blockIdx.y;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  double* z = io->z + (long long)d->dst;
+  const double* w = d->w[0].abs;
+  double t = w[k];
+  if (d->d[0]) t *= d->d[0][k];
+  z[k] = z[k] + t;
+}
+}  // namespace mgd
+
+namespace mgd {
+
+template <typename T>
+static void run_program(mgd_ctx* c, bool trans) {
+  for (const Step& st : c->steps) {
+    if (st.type == Step::PRODUCE && st.batch == -2) {
+      int id = c->prof.begin(c->s);
+      k_zupdate<<<dim3(cdiv(st.len, kThreads), st.nd), kThreads, 0, c->s>>>(
+          (const ProduceDesc<double>*)st.descs, st.len, c->io);
+      MGD_LAUNCH_CHECK();
+      c->prof.end(id, 4, st.bytes, c->s);
+      continue;
+    }
+    run_step<T>(c, st, trans);
+  }
+}
+
+// group INVERT steps into batches (one batch per step when batched, else one per op)
+template <typename T>
+static void build_batches(mgd_ctx* c) {
+  auto& B = batches<T>(c);
+  B.clear();
+  std::vector<Step> out;
+  for (Step& st : c->steps) {
+    if (st.type != Step::INVERT) {
+      out.push_back(st);
+      continue;
+    }
+    std::vector<int> vc;
+    for (int id : st.ops)
+      if (!c->ops[id].jacobi) vc.push_back(id);
+    std::vector<int> jac;
+    for (int id : st.ops)
+      if (c->ops[id].jacobi) jac.push_back(id);
+    if (c->o.batched || vc.size() <= 1) {
+      Step s2 = st;
+      if (!vc.empty()) {
+        B.emplace_back();
+        for (int id : vc) B.back().hs.push_back(&c->ops[id].h);
+        s2.batch = (int)B.size() - 1;
+      }
+      out.push_back(s2);
+    } else {
+      // one step per operator (plain launches)
+      bool first = true;
+      for (int id : vc) {
+        Step s2 = st;
+        s2.ops = {id};
+        if (first) {
+          for (int j : jac) s2.ops.push_back(j);
+          first = false;
+        }
+        B.emplace_back();
+        B.back().hs.push_back(&c->ops[id].h);
+        s2.batch = (int)B.size() - 1;
+        out.push_back(s2);
+      }
+    }
+  }
+  c->steps = out;
+  for (auto& vb : B) {
+    build_plan<T>(c->ar, vb, false, c->s);
+    if (c->o.keep_transpose) build_plan<T>(c->ar, vb, true, c->s);
+    if (c->o.autotune) {
+      autotune<T>(vb, false, c->s);
+      if (c->o.keep_transpose) autotune<T>(vb, true, c->s);
+    }
+  }
+}
+
+}  // namespace mgd
+
+using namespace mgd;
+
+// ------------------------------------------------------------------ helpers of the API
+static int fail(mgd_ctx* c, const Error& e) {
+  if (c) c->err = e.msg;
+  return e.code;
+}
+
+template <typename F>
+static int guarded(mgd_ctx* c, F&& f) {
+  if (!c) return MGD_EINVAL;
+  try {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != c->device) MGD_CUDA(cudaSetDevice(c->device));
+    int r = f();
+    if (dev != c->device) cudaSetDevice(dev);
+    return r;
+  } catch (const Error& e) {
+    return fail(c, e);
+  } catch (const std::exception& e) {
+    return fail(c, Error{MGD_ECUDA, e.what()});
+  }
+}
+
+static void precond_apply(mgd_ctx* c, const double* v, double* z, bool trans) {
+  launch_set_io(c->io, v, z, c->s);
+  if (!trans && c->graph_ok && !c->prof.on) {
+    MGD_CUDA(cudaGraphLaunch(c->graph, c->s));
+    __atomic_add_fetch(&g_kernel_launches, c->graph_nodes, __ATOMIC_RELAXED);
+    return;
+  }
+  if (mixed(c)) run_program<float>(c, trans);
+  else run_program<double>(c, trans);
+}
+
+static void capture_graph(mgd_ctx* c) {
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->graph_ok = false;
+  if (!c->o.use_graph) return;
+  cudaGraph_t g;
+  bool prof_on = c->prof.on;
+  c->prof.on = false;
+  MGD_CUDA(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+  try {
+    if (mixed(c)) run_program<float>(c, false);
+    else run_program<double>(c, false);
+  } catch (...) {
+    cudaStreamEndCapture(c->s, &g);
+    c->prof.on = prof_on;
+    throw;
+  }
+  c->prof.on = prof_on;
+  MGD_CUDA(cudaStreamEndCapture(c->s, &g));
+  size_t nn = 0;
+  MGD_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+  c->graph_nodes = (long long)nn;
+  MGD_CUDA(cudaGraphInstantiate(&c->graph, g, 0));
+  cudaGraphDestroy(g);
+  c->graph_ok = true;
+}
+
+static void free_setup(mgd_ctx* c) {
+  if (c->s) cudaStreamSynchronize(c->s);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  c->graph_ok = false;
+  c->ar.release();
+  c->ops.clear();
+  c->steps.clear();
+  c->vb64.clear();
+  c->vb32.clear();
+  c->bd = BlockData();
+  c->ready = false;
+  if (c->hpin) cudaFreeHost(c->hpin);
+  c->hpin = nullptr;
+}
+
+static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) {
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = c->s;
+  int G = c->G, N = c->N, n = c->n, nnz = c->nnz, nc = G + 2;
+  const mgd_opts& o = c->o;
+  c->ar.stream = s;
+  // validation
+  {
+    Scratch sc(s);
+    int* flags = sc.alloc<int>(3);
+    MGD_CUDA(cudaMemsetAsync(flags, 0, 3 * sizeof(int), s));
+    launch_validate(n, nnz, N, nc, rp, ci, v, flags, s);
+    int hf[3];
+    MGD_CUDA(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    MGD_CUDA(cudaStreamSynchronize(s));
+    int r0 = read_int(rp, s);
+    int rn = read_int(rp + n, s);
+    if (r0 != 0 || rn != nnz) throw Error{MGD_EINVAL, "row pointer does not span [0, nnz]"};
+    if (hf[0]) throw Error{MGD_EINVAL, "column index out of range, unsorted or duplicated"};
+    if (hf[1]) throw Error{MGD_EINVAL, "off-block entry couples different cells (D_ab must be diagonal)"};
+    if (hf[2]) throw Error{MGD_EINVAL, "missing or non-positive diagonal entry"};
+  }
+  // keep a copy of the monolithic operator
+  Csr in;
+  in.n = n;
+  in.m = n;
+  in.nnz = nnz;
+  in.rp = const_cast<int*>(rp);
+  in.ci = const_cast<int*>(ci);
+  in.v = const_cast<double*>(v);
+  c->A = csr_copy(c->ar, in, s);
+  c->Asell = build_sell(c->ar, c->A, false, s);
+  if (o.keep_transpose) {
+    c->AT = transpose(c->ar, c->A, s);
+    c->ATsell = build_sell(c->ar, c->AT, false, s);
+  }
+  c->wEs = c->ar.alloc<double>(N, true);
+  c->wIs = c->ar.alloc<double>(N, true);
+  c->rfull = c->ar.alloc<double>(n, true);
+  c->io = c->ar.alloc<IOSlots>(1, true);
+  c->ops.clear();
+  c->n_jacobi = 0;
+  int ndrop = 0;
+  if (c->kind == MGD_AMG) {
+    add_op(c, OP_MONO, 0, c->A);
+  } else {
+    // block extraction
+    BlockData& bd = c->bd;
+    bd.G = G;
+    bd.N = N;
+    bd.nc = nc;
+    Scratch sc(s);
+    int* cnt = sc.alloc<int>(n);
+    int* pairs = sc.alloc<int>(nc * nc);
+    MGD_CUDA(cudaMemsetAsync(pairs, 0, sizeof(int) * nc * nc, s));
+    launch_block_count(n, N, nc, c->A.rp, c->A.ci, cnt, pairs, s);
+    int* brp = sc.alloc<int>(n + 1);
+    exclusive_scan(cnt, brp, n, s);
+    int tot = read_int(brp + n, s);
+    std::vector<int> hpairs(nc * nc);
+    MGD_CUDA(cudaMemcpyAsync(hpairs.data(), pairs, sizeof(int) * nc * nc, cudaMemcpyDeviceToHost, s));
+    MGD_CUDA(cudaStreamSynchronize(s));
+    bd.d.assign(nc * nc, nullptr);
+    bd.dropped.assign(nc * nc, 0);
+    for (int k = 0; k < nc * nc; ++k)
+      if (hpairs[k]) bd.d[k] = c->ar.alloc<double>(N, true);
+    double** dtab = sc.alloc<double*>(nc * nc);
+    MGD_CUDA(cudaMemcpyAsync(dtab, bd.d.data(), sizeof(double*) * nc * nc, cudaMemcpyHostToDevice, s));
+    int* bci = c->ar.alloc<int>(tot);
+    double* bv = c->ar.alloc<double>(tot);
+    launch_block_fill(n, N, nc, c->A.rp, c->A.ci, c->A.v, brp, bci, bv, dtab, s);
+    std::vector<int> hbrp(n + 1);
+    MGD_CUDA(cudaMemcpyAsync(hbrp.data(), brp, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s));
+    MGD_CUDA(cudaStreamSynchronize(s));
+    bd.Ab.resize(nc);
+    bd.diag.resize(nc);
+    for (int a = 0; a < nc; ++a) {
+      Csr B;
+      B.n = N;
+      B.m = N;
+      int off = hbrp[(size_t)a * N];
+      B.nnz = hbrp[(size_t)(a + 1) * N] - off;
+      B.rp = c->ar.alloc<int>(N + 1);
+      std::vector<int> lrp(N + 1);
+      for (int k = 0; k <= N; ++k) lrp[k] = hbrp[(size_t)a * N + k] - off;
+      MGD_CUDA(cudaMemcpyAsync(B.rp, lrp.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, s));
+      B.ci = bci + off;
+      B.v = bv + off;
+      MGD_CUDA(cudaStreamSynchronize(s));
+      bd.Ab[a] = B;
+      bd.diag[a] = c->ar.alloc<double>(N);
+      launch_diag_extract(N, B.rp, B.ci, B.v, bd.diag[a], s);
+    }
+    // Section 3.6: drop D_ab when gamma_wc^{ab} > sigma_wc
+    if (o.adaptive) {
+      int* cntw = sc.alloc<int>(1);
+      for (int a = 0; a < nc; ++a)
+        for (int b = 0; b < nc; ++b) {
+          double* d = bd.d[a * nc + b];
+          if (!d) continue;
+          MGD_CUDA(cudaMemsetAsync(cntw, 0, sizeof(int), s));
+          launch_gamma_wc(N, d, bd.diag[a], o.theta_wc, cntw, s);
+          double g = (double)read_int(cntw, s) / N;
+          if (g > o.sigma_wc) {
+            bd.d[a * nc + b] = nullptr;
+            bd.dropped[a * nc + b] = 1;
+            ++ndrop;
+          }
+        }
+    }
+    auto D = [&](int a, int b) -> const double* { return bd.d[a * nc + b]; };
+    int E = G, I = G + 1;
+    switch (c->kind) {
+      case MGD_BD:
+      case MGD_BLT:
+        for (int a = 0; a < nc; ++a) add_op(c, OP_A, a, csr_copy(c->ar, bd.Ab[a], s));
+        break;
+      case MGD_SCHUR1: {
+        add_op(c, OP_A, I, csr_copy(c->ar, bd.Ab[I], s));
+        Csr CE = diag_modified(c, bd.Ab[E], D(E, I), D(I, E), bd.diag[I]);
+        double* dCE = c->ar.alloc<double>(N);
+        launch_diag_extract(N, CE.rp, CE.ci, CE.v, dCE, s);
+        add_op(c, OP_CE, E, CE);
+        for (int g = 0; g < G; ++g) add_op(c, OP_CG, g, diag_modified(c, bd.Ab[g], D(g, E), D(E, g), dCE));
+        break;
+      }
+      case MGD_SCHUR2:
+        add_op(c, OP_A, E, csr_copy(c->ar, bd.Ab[E], s));
+        for (int g = 0; g < G; ++g) add_op(c, OP_SG, g, diag_modified(c, bd.Ab[g], D(g, E), D(E, g), bd.diag[E]));
+        add_op(c, OP_SI, I, diag_modified(c, bd.Ab[I], D(I, E), D(E, I), bd.diag[E]));
+        break;
+      case MGD_PCTL:
+        for (int a = 0; a < nc; ++a) add_op(c, OP_A, a, csr_copy(c->ar, bd.Ab[a], s));
+        break;
+    }
+    // device tables of the blocks
+    std::vector<int*> hrp(nc), hci(nc);
+    std::vector<double*> hv(nc);
+    for (int a = 0; a < nc; ++a) {
+      hrp[a] = bd.Ab[a].rp;
+      hci[a] = bd.Ab[a].ci;
+      hv[a] = bd.Ab[a].v;
+    }
+    bd.d_brp = (int**)upload_vec(c, hrp);
+    bd.d_bci = (int**)upload_vec(c, hci);
+    bd.d_bv = (double**)upload_vec(c, hv);
+    bd.d_dtab = (double**)upload_vec(c, bd.d);
+  }
+  // hierarchies / Jacobi data
+  for (auto& op : c->ops) {
+    if (mixed(c)) finalize_op<float>(c, op);
+    else finalize_op<double>(c, op);
+    if (op.jacobi) c->n_jacobi++;
+  }
+  if (c->kind == MGD_PCTL) {
+    // p_a = -A_a^{-1} D_aE 1 by option #3 (V-cycles until ||r|| <= tol ||rhs||), FP64 arithmetic
+    BlockData& bd = c->bd;
+    int E = G;
+    bd.p.assign(nc, nullptr);
+    Scratch sc(s);
+    double* rhs = sc.alloc<double>(N);
+    double* r = sc.alloc<double>(N);
+    double* part = sc.alloc<double>(kDotBlocks * 32);
+    double* nrm = sc.alloc<double>(2);
+    for (int a = 0; a < nc; ++a) {
+      if (a == E) continue;
+      bd.p[a] = c->ar.alloc<double>(N, true);
+      const double* dE = bd.d[a * nc + E];
+      if (!dE) continue;
+      launch_lincomb(N, -1.0, dE, 0.0, dE, rhs, s);
+      launch_norm2(N, rhs, part, nrm, s);
+      double h0;
+      MGD_CUDA(cudaMemcpyAsync(&h0, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+      MGD_CUDA(cudaStreamSynchronize(s));
+      double nr0 = std::sqrt(h0);
+      InvOp& op = c->ops[a];
+      std::vector<Hier*> hh{&op.h};
+      VBatch<double> vb64;
+      VBatch<float> vb32;
+      if (!op.jacobi) {
+        if (mixed(c)) {
+          vb32.hs = hh;
+          build_plan<float>(c->ar, vb32, false, s);
+        } else {
+          vb64.hs = hh;
+          build_plan<double>(c->ar, vb64, false, s);
+        }
+      }
+      for (int it = 0; it < o.inner_maxit; ++it) {
+        launch_resid_f64(FMT_CSR4, N, op.A.rp, op.A.ci, op.A.v, nullptr, nullptr, nullptr, rhs, bd.p[a], r, s);
+        launch_norm2(N, r, part, nrm, s);
+        double h1;
+        MGD_CUDA(cudaMemcpyAsync(&h1, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+        MGD_CUDA(cudaStreamSynchronize(s));
+        if (std::sqrt(h1) <= o.inner_tol * nr0) break;
+        if (mixed(c)) {
+          launch_cast_f64_f32(N, r, (float*)op.b, s);
+          if (op.jacobi) {
+            JacDesc<float> jd{(float*)op.x, (const float*)op.b, op.jd32};
+            JacDesc<float>* dd = sc.alloc<JacDesc<float>>(1);
+            MGD_CUDA(cudaMemcpyAsync(dd, &jd, sizeof(jd), cudaMemcpyHostToDevice, s));
+            launch_jacobi<float>(dd, 1, N, s);
+          } else {
+            run_vbatch<float>(vb32, false, s, c->prof);
+          }
+          double* e = rhs + 0;  // reuse: e is added into p below
+          (void)e;
+          Scratch t2(s);
+          double* ed = t2.alloc<double>(N);
+          launch_cast_f32_f64(N, (const float*)op.x, ed, s);
+          launch_saxpy_vec(N, 1.0, ed, bd.p[a], s);
+          MGD_CUDA(cudaStreamSynchronize(s));
+        } else {
+          launch_copy_f64(N, r, (double*)op.b, s);
+          if (op.jacobi) {
+            JacDesc<double> jd{(double*)op.x, (const double*)op.b, op.jd};
+            JacDesc<double>* dd = sc.alloc<JacDesc<double>>(1);
+            MGD_CUDA(cudaMemcpyAsync(dd, &jd, sizeof(jd), cudaMemcpyHostToDevice, s));
+            launch_jacobi<double>(dd, 1, N, s);
+          } else {
+            run_vbatch<double>(vb64, false, s, c->prof);
+          }
+          launch_saxpy_vec(N, 1.0, (const double*)op.x, bd.p[a], s);
+        }
+      }
+    }
+    // Eq. 3.3 coarse operator on the union pattern
+    int* acnt = sc.alloc<int>(N);
+    launch_pctl_ac_count(N, nc, (const int* const*)bd.d_brp, (const int* const*)bd.d_bci, acnt, s);
+    Csr Ac;
+    Ac.n = N;
+    Ac.m = N;
+    Ac.rp = c->ar.alloc<int>(N + 1);
+    exclusive_scan(acnt, Ac.rp, N, s);
+    Ac.nnz = read_int(Ac.rp + N, s);
+    Ac.ci = c->ar.alloc<int>(Ac.nnz);
+    Ac.v = c->ar.alloc<double>(Ac.nnz);
+    std::vector<double*> hp(nc, nullptr);
+    for (int a = 0; a < nc; ++a) hp[a] = bd.p[a];
+    double** dp = (double**)upload_vec(c, hp);
+    launch_pctl_ac_fill(N, nc, G, (const int* const*)bd.d_brp, (const int* const*)bd.d_bci,
+                        (const double* const*)bd.d_bv, (const double* const*)dp, (const double* const*)bd.d_dtab,
+                        Ac.rp, Ac.ci, Ac.v, s);
+    bd.Ac = Ac;
+    int oAc = add_op(c, OP_AC, E, Ac);
+    if (mixed(c)) finalize_op<float>(c, c->ops[oAc]);
+    else finalize_op<double>(c, c->ops[oAc]);
+    if (c->ops[oAc].jacobi) c->n_jacobi++;
+  }
+  // program, batches, graph
+  if (mixed(c)) {
+    build_program<float>(c);
+    build_batches<float>(c);
+  } else {
+    build_program<double>(c);
+    build_batches<double>(c);
+  }
+  // FGMRES storage
+  c->m = std::max(1, std::min(o.restart, 30));
+  c->V = c->ar.alloc<double>((size_t)(c->m + 1) * n, true);
+  c->Z = c->ar.alloc<double>((size_t)c->m * n, true);
+  c->w = c->ar.alloc<double>(n, true);
+  c->r = c->ar.alloc<double>(n, true);
+  c->xtmp = c->ar.alloc<double>(n, true);
+  c->btmp = c->ar.alloc<double>(n, true);
+  c->hbuf = c->ar.alloc<double>(128, true);
+  c->partial = c->ar.alloc<double>((size_t)kDotBlocks * 32, true);
+  c->ybuf = c->ar.alloc<double>(64, true);
+  MGD_CUDA(cudaMallocHost(&c->hpin, 256 * sizeof(double)));
+  // monolithic SpMV layout
+  c->fmtMono = FMT_SELL;
+  if (o.autotune) {
+    cudaEvent_t e0, e1;
+    MGD_CUDA(cudaEventCreate(&e0));
+    MGD_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int f : {FMT_SELL, FMT_CSR1, FMT_CSR2, FMT_CSR4, FMT_CSR8}) {
+      launch_spmv_f64(f, n, c->A.rp, c->A.ci, c->A.v, c->Asell.sptr, c->Asell.ci, c->Asell.v, c->r, c->w, s);
+      MGD_CUDA(cudaEventRecord(e0, s));
+      for (int k = 0; k < 3; ++k)
+        launch_spmv_f64(f, n, c->A.rp, c->A.ci, c->A.v, c->Asell.sptr, c->Asell.ci, c->Asell.v, c->r, c->w, s);
+      MGD_CUDA(cudaEventRecord(e1, s));
+      MGD_CUDA(cudaEventSynchronize(e1));
+      float ms;
+      MGD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        c->fmtMono = f;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  capture_graph(c);
+  MGD_CUDA(cudaStreamSynchronize(s));
+  // stats
+  memset(&c->st, 0, sizeof(c->st));
+  mgd_stats& st = c->st;
+  st.kind = c->kind;
+  st.G = G;
+  st.N = N;
+  st.n = n;
+  st.nnz = nnz;
+  st.n_ops = (int)c->ops.size();
+  double n0 = 0, nall = 0, z0 = 0, zall = 0;
+  for (auto& op : c->ops) {
+    if (op.jacobi) continue;
+    st.max_levels_used = std::max(st.max_levels_used, op.h.nlev());
+    n0 += op.h.L[0].A.n;
+    z0 += op.h.L[0].A.nnz;
+    for (auto& lv : op.h.L) {
+      nall += lv.A.n;
+      zall += lv.A.nnz;
+    }
+  }
+  st.grid_complexity = n0 > 0 ? nall / n0 : 0;
+  st.op_complexity = z0 > 0 ? zall / z0 : 0;
+  double vbytes = 0;
+  auto count_bytes = [&](auto& B) {
+    for (const Step& s2 : c->steps) {
+      if (s2.type == Step::INVERT && s2.batch >= 0) {
+        int maxc = 1;
+        for (int id : s2.ops) maxc = std::max(maxc, c->ops[id].count);
+        vbytes += B[s2.batch].bytes_total * maxc;
+      }
+    }
+  };
+  if (mixed(c)) count_bytes(c->vb32);
+  else count_bytes(c->vb64);
+  double pbytes = vbytes;
+  for (const Step& s2 : c->steps)
+    if (s2.type != Step::INVERT) pbytes += s2.bytes;
+  st.vcycle_bytes = vbytes;
+  st.precond_bytes = pbytes;
+  st.iter_bytes_base = sp_bytes(nnz, n, 8) + 16.0 * n + 4 * 8.0 * 2 * n + 16.0 * n;
+  st.n_dropped = ndrop;
+  st.n_jacobi_ops = c->n_jacobi;
+  st.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  c->ready = true;
+}
+
+// Right-preconditioned FGMRES(m) with classical Gram-Schmidt applied twice
+// (CGS2); the small Hessenberg problem and its Givens rotations are solved on
+// the host in FP64 from one device-to-host copy per iteration.
+static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans, int* iters, double* relres) {
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = c->s;
+  int n = c->n, m = c->m;
+  const Csr& A = trans ? c->AT : c->A;
+  const Sell& AS = trans ? c->ATsell : c->Asell;
+  double* hp = c->hpin;
+  auto norm = [&](const double* v) {
+    launch_norm2(n, v, c->partial, c->hbuf + 96, s);
+    MGD_CUDA(cudaMemcpyAsync(hp + 200, c->hbuf + 96, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MGD_CUDA(cudaStreamSynchronize(s));
+    return std::sqrt(hp[200]);
+  };
+  auto spmv = [&](const double* in, double* out) {
+    int id = c->prof.begin(s);
+    launch_spmv_f64(c->fmtMono, n, A.rp, A.ci, A.v, AS.sptr, AS.ci, AS.v, in, out, s);
+    c->prof.end(id, 2, sp_bytes(A.nnz, n, 8) + 16.0 * n, s);
+  };
+  c->hist.clear();
+  double bnorm = norm(b);
+  *iters = 0;
+  if (bnorm == 0.0) {
+    MGD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    MGD_CUDA(cudaStreamSynchronize(s));
+    *relres = 0.0;
+    return MGD_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  auto Hm = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  int it = 0, status = MGD_ENOCONV;
+  for (;;) {
+    int id = c->prof.begin(s);
+    launch_resid_f64(c->fmtMono, n, A.rp, A.ci, A.v, AS.sptr, AS.ci, AS.v, b, x, c->r, s);
+    c->prof.end(id, 2, sp_bytes(A.nnz, n, 8) + 24.0 * n, s);
+    double beta = norm(c->r);
+    *relres = beta / bnorm;
+    if (!std::isfinite(beta)) {
+      status = MGD_ENAN;
+      break;
+    }
+    if (beta <= tol * bnorm) {
+      status = MGD_OK;
+      break;
+    }
+    if (it >= c->o.max_it) {
+      status = MGD_ENOCONV;
+      break;
+    }
+    // V_0 = r / beta  (scale_by_norm takes a squared norm)
+    hp[201] = beta * beta;
+    MGD_CUDA(cudaMemcpyAsync(c->hbuf + 101, hp + 201, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_scale_by_norm(n, c->r, c->hbuf + 101, c->V, s);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    bool breakdown = false;
+    while (j < m) {
+      double* vj = c->V + (size_t)j * n;
+      double* zj = c->Z + (size_t)j * n;
+      precond_apply(c, vj, zj, trans);
+      ++it;
+      spmv(zj, c->w);
+      int nv = j + 1;
+      int aid = c->prof.begin(s);
+      launch_mdot(n, c->V, n, nv, c->w, c->partial, c->hbuf, s);
+      launch_vupdate(n, c->V, n, nv, c->hbuf, c->w, c->partial, c->hbuf + 64, s);
+      launch_mdot(n, c->V, n, nv, c->w, c->partial, c->hbuf + 32, s);
+      launch_vupdate(n, c->V, n, nv, c->hbuf + 32, c->w, c->partial, c->hbuf + 64, s);
+      launch_scale_by_norm(n, c->w, c->hbuf + 64, c->V + (size_t)(j + 1) * n, s);
+      c->prof.end(aid, 3, 8.0 * n * (2.0 * (nv + 1) + 2.0 * (nv + 2) + 2.0), s);
+      MGD_CUDA(cudaMemcpyAsync(hp, c->hbuf, 65 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      MGD_CUDA(cudaStreamSynchronize(s));
+      for (int i = 0; i <= j; ++i) Hm(i, j) = hp[i] + hp[32 + i];
+      double hn = std::sqrt(hp[64]);
+      Hm(j + 1, j) = hn;
+      for (int i = 0; i < j; ++i) {
+        double t = cs[i] * Hm(i, j) + sn[i] * Hm(i + 1, j);
+        Hm(i + 1, j) = -sn[i] * Hm(i, j) + cs[i] * Hm(i + 1, j);
+        Hm(i, j) = t;
+      }
+      double h1 = Hm(j, j), h2 = Hm(j + 1, j);
+      if (h2 == 0.0) {
+        cs[j] = 1.0;
+        sn[j] = 0.0;
+      } else {
+        double tt = std::sqrt(h1 * h1 + h2 * h2);
+        cs[j] = h1 / tt;
+        sn[j] = h2 / tt;
+      }
+      Hm(j, j) = cs[j] * h1 + sn[j] * h2;
+      Hm(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      c->hist.push_back(std::fabs(g[j + 1]) / bnorm);
+      ++j;
+      if (hn == 0.0) breakdown = true;
+      if (std::fabs(g[j]) <= tol * bnorm || hn == 0.0 || it >= c->o.max_it || !std::isfinite(g[j])) break;
+    }
+    (void)breakdown;
+    for (int i = j - 1; i >= 0; --i) {
+      double sum = g[i];
+      for (int k = i + 1; k < j; ++k) sum -= Hm(i, k) * y[k];
+      y[i] = sum / Hm(i, i);
+    }
+    for (int i = 0; i < j; ++i) hp[100 + i] = y[i];
+    MGD_CUDA(cudaMemcpyAsync(c->ybuf, hp + 100, sizeof(double) * j, cudaMemcpyHostToDevice, s));
+    launch_vcomb(n, c->Z, n, j, c->ybuf, x, s);
+  }
+  MGD_CUDA(cudaStreamSynchronize(s));
+  *iters = it;
+  c->st.last_iters = it;
+  c->st.last_relres = *relres;
+  c->st.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (status != MGD_OK) {
+    if (status == MGD_ENOCONV) c->err = "iteration cap reached";
+    if (status == MGD_ENAN) c->err = "non-finite residual";
+  }
+  return status;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+int mgd_opts_default(mgd_opts* o) {
+  if (!o) return MGD_EINVAL;
+  memset(o, 0, sizeof(*o));
+  o->theta_str = 0.25;
+  o->max_coarse = 100;
+  o->max_levels = 25;
+  o->theta_wd = 0.9;
+  o->theta_wc = 1e-2;
+  o->sigma_wc = 0.5;
+  o->inner_tol = 1e-2;
+  o->inner_maxit = 100;
+  o->nvcyc_group = 1;
+  o->nvcyc_E = 1;
+  o->nvcyc_I = 1;
+  o->nvcyc_other = 1;
+  o->jacobi_sweeps = 1;
+  o->adaptive = 0;
+  o->seed = 0;
+  o->restart = 30;
+  o->max_it = 1000;
+  o->precision = 0;
+  o->batched = 0;
+  o->use_graph = 0;
+  o->autotune = 1;
+  o->keep_transpose = 0;
+  return MGD_OK;
+}
+
+int mgd_create(mgd_ctx** out, const mgd_opts* o, void* stream) {
+  if (!out) return MGD_EINVAL;
+  *out = nullptr;
+  mgd_ctx* c = new (std::nothrow) mgd_ctx();
+  if (!c) return MGD_ENOMEM;
+  if (o) c->o = *o;
+  else mgd_opts_default(&c->o);
+  if (c->o.max_coarse < 1 || c->o.max_coarse > 4096 || c->o.max_levels < 1 || c->o.restart < 1 ||
+      c->o.restart > 30 || c->o.precision < 0 || c->o.precision > 1) {
+    delete c;
+    return MGD_EINVAL;
+  }
+  c->s = (cudaStream_t)stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return MGD_ECUDA;
+  }
+  *out = c;
+  return MGD_OK;
+}
+
+int mgd_setup(mgd_ctx* c, int G, int N, int n, int nnz, const int* d_rowptr, const int* d_colidx,
+              const double* d_vals, int kind) {
+  return guarded(c, [&]() -> int {
+    if (G < 1 || N < 1 || n != (G + 2) * N || nnz < n || !d_rowptr || !d_colidx || !d_vals || kind < 0 ||
+        kind > MGD_BLT || G + 1 > kMaxTerms - 1)
+      throw Error{MGD_EINVAL, "invalid sizes or kind"};
+    free_setup(c);
+    c->G = G;
+    c->N = N;
+    c->n = n;
+    c->nnz = nnz;
+    c->kind = kind;
+    do_setup(c, d_rowptr, d_colidx, d_vals);
+    return MGD_OK;
+  });
+}
+
+int mgd_update_values(mgd_ctx* c, const double* d_vals) {
+  return guarded(c, [&]() -> int {
+    if (!c->ready) throw Error{MGD_ESTATE, "no setup"};
+    // keep the pattern of the current operator, replace the values, redo the setup
+    Scratch sc(c->s);
+    int* rp = sc.alloc<int>(c->n + 1);
+    int* ci = sc.alloc<int>(c->nnz);
+    double* v = sc.alloc<double>(c->nnz);
+    MGD_CUDA(cudaMemcpyAsync(rp, c->A.rp, sizeof(int) * (c->n + 1), cudaMemcpyDeviceToDevice, c->s));
+    MGD_CUDA(cudaMemcpyAsync(ci, c->A.ci, sizeof(int) * c->nnz, cudaMemcpyDeviceToDevice, c->s));
+    MGD_CUDA(cudaMemcpyAsync(v, d_vals, sizeof(double) * c->nnz, cudaMemcpyDeviceToDevice, c->s));
+    MGD_CUDA(cudaStreamSynchronize(c->s));
+    free_setup(c);
+    do_setup(c, rp, ci, v);
+    return MGD_OK;
+  });
+}
+
+int mgd_solve(mgd_ctx* c, const double* d_b, double tol, double* d_x, int* iters, double* relres) {
+  return guarded(c, [&]() -> int {
+    if (!c->ready) throw Error{MGD_ESTATE, "solve before setup"};
+    if (!d_b || !d_x || !(tol > 0)) throw Error{MGD_EINVAL, "invalid arguments"};
+    int it = 0;
+    double rr = 0;
+    int r = fgmres(c, d_b, d_x, tol, false, &it, &rr);
+    if (iters) *iters = it;
+    if (relres) *relres = rr;
+    return r;
+  });
+}
+
+int mgd_solve_host(mgd_ctx* c, const double* h_b, double tol, double* h_x, int* iters, double* relres) {
+  return guarded(c, [&]() -> int {
+    if (!c->ready) throw Error{MGD_ESTATE, "solve before setup"};
+    if (!h_b || !h_x || !(tol > 0)) throw Error{MGD_EINVAL, "invalid arguments"};
+    MGD_CUDA(cudaMemcpyAsync(c->btmp, h_b, sizeof(double) * c->n, cudaMemcpyHostToDevice, c->s));
+    MGD_CUDA(cudaMemcpyAsync(c->xtmp, h_x, sizeof(double) * c->n, cudaMemcpyHostToDevice, c->s));
+    int it = 0;
+    double rr = 0;
+    int r = fgmres(c, c->btmp, c->xtmp, tol, false, &it, &rr);
+    MGD_CUDA(cudaMemcpyAsync(h_x, c->xtmp, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->s));
+    MGD_CUDA(cudaStreamSynchronize(c->s));
+    if (iters) *iters = it;
+    if (relres) *relres = rr;
+    return r;
+  });
+}
+
+int mgd_solve_transpose(mgd_ctx* c, const double* d_g, double tol, double* d_lambda, int* iters, double* relres) {
+  return guarded(c, [&]() -> int {
+    if (!c->ready) throw Error{MGD_ESTATE, "solve before setup"};
+    if (!c->o.keep_transpose) throw Error{MGD_ESTATE, "setup without keep_transpose"};
+    if (c->kind != MGD_AMG && c->kind != MGD_BD) throw Error{MGD_EINVAL, "transposed solve needs AMG or BD"};
+    if (!d_g || !d_lambda || !(tol > 0)) throw Error{MGD_EINVAL, "invalid arguments"};
+    int it = 0;
+    double rr = 0;
+    int r = fgmres(c, d_g, d_lambda, tol, true, &it, &rr);
+    if (iters) *iters = it;
+    if (relres) *relres = rr;
+    return r;
+  });
+}
+
+int mgd_grad_values(mgd_ctx* c, const double* d_x, const double* d_lambda, double* d_grad) {
+  return guarded(c, [&]() -> int {
+    if (!c->ready) throw Error{MGD_ESTATE, "no setup"};
+    if (!d_x || !d_lambda || !d_grad) throw Error{MGD_EINVAL, "invalid arguments"};
+    launch_grad_vals(c->n, c->A.rp, c->A.ci, d_x, d_lambda, d_grad, c->s);
+    MGD_CUDA(cudaStreamSynchronize(c->s));
+    return MGD_OK;
+  });
+}
+
+int mgd_precond_apply(mgd_ctx* c, const double* d_v, double* d_z) {
+  return guarded(c, [&]() -> int {
+    if (!c->ready) throw Error{MGD_ESTATE, "no setup"};
+    if (!d_v || !d_z) throw Error{MGD_EINVAL, "invalid arguments"};
+    precond_apply(c, d_v, d_z, false);
+    MGD_CUDA(cudaStreamSynchronize(c->s));
+    return MGD_OK;
+  });
+}
+
+int mgd_get_stats(mgd_ctx* c, mgd_stats* s) {
+  if (!c || !s) return MGD_EINVAL;
+  *s = c->st;
+  return MGD_OK;
+}
+
+int mgd_get_history(mgd_ctx* c, double* h, int cap, int* count) {
+  if (!c || !count) return MGD_EINVAL;
+  int k = std::min<int>(cap, (int)c->hist.size());
+  for (int i = 0; i < k && h; ++i) h[i] = c->hist[i];
+  *count = (int)c->hist.size();
+  return MGD_OK;
+}
+
+int mgd_op_info(mgd_ctx* c, int op, int* kind, int* comp, int* nlevels, int* use_jacobi, int* coarse_lu) {
+  if (!c || !c->ready || op < 0 || op >= (int)c->ops.size()) return MGD_EINVAL;
+  InvOp& o = c->ops[op];
+  if (kind) *kind = o.kind;
+  if (comp) *comp = o.comp;
+  if (nlevels) *nlevels = o.jacobi ? 0 : o.h.nlev();
+  if (use_jacobi) *use_jacobi = o.jacobi;
+  if (coarse_lu) *coarse_lu = o.jacobi ? 0 : o.h.coarse_lu;
+  return MGD_OK;
+}
+
+int mgd_level_info(mgd_ctx* c, int op, int level, int* n, int* nnz, int* nnzP, int* ncoarse) {
+  if (!c || !c->ready || op < 0 || op >= (int)c->ops.size()) return MGD_EINVAL;
+  InvOp& o = c->ops[op];
+  if (o.jacobi || level < 0 || level >= o.h.nlev()) return MGD_EINVAL;
+  Level& lv = o.h.L[level];
+  if (n) *n = lv.A.n;
+  if (nnz) *nnz = lv.A.nnz;
+  if (nnzP) *nnzP = level < o.h.nlev() - 1 ? lv.P.nnz : 0;
+  if (ncoarse) *ncoarse = level < o.h.nlev() - 1 ? lv.nc : 0;
+  return MGD_OK;
+}
+
+int mgd_level_export(mgd_ctx* c, int op, int level, int* h_rp, int* h_ci, double* h_v, signed char* h_cf,
+                     int* h_prp, int* h_pci, double* h_pv) {
+  return guarded(c, [&]() -> int {
+    if (!c->ready || op < 0 || op >= (int)c->ops.size()) throw Error{MGD_EINVAL, "bad operator"};
+    InvOp& o = c->ops[op];
+    if (o.jacobi || level < 0 || level >= o.h.nlev()) throw Error{MGD_EINVAL, "bad level"};
+    Level& lv = o.h.L[level];
+    bool last = level == o.h.nlev() - 1;
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+      if (dst && src && bytes) MGD_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->s));
+    };
+    cp(h_rp, lv.A.rp, sizeof(int) * (lv.A.n + 1));
+    cp(h_ci, lv.A.ci, sizeof(int) * lv.A.nnz);
+    cp(h_v, lv.A.v, sizeof(double) * lv.A.nnz);
+    if (!last) {
+      cp(h_cf, lv.CF, lv.A.n);
+      cp(h_prp, lv.P.rp, sizeof(int) * (lv.A.n + 1));
+      cp(h_pci, lv.P.ci, sizeof(int) * lv.P.nnz);
+      cp(h_pv, lv.P.v, sizeof(double) * lv.P.nnz);
+    }
+    MGD_CUDA(cudaStreamSynchronize(c->s));
+    return MGD_OK;
+  });
+}
+
+int mgd_block_vector(mgd_ctx* c, int which, int comp, int comp2, double* h_out) {
+  return guarded(c, [&]() -> int {
+    if (!c->ready || c->kind == MGD_AMG || !h_out || comp < 0 || comp >= c->G + 2)
+      throw Error{MGD_EINVAL, "no block data"};
+    const double* src = nullptr;
+    int nc = c->G + 2;
+    if (which == 0 && !c->bd.p.empty()) src = c->bd.p[comp];
+    if (which == 1) src = c->bd.diag[comp];
+    if (which == 2 && comp2 >= 0 && comp2 < nc) src = c->bd.d[comp * nc + comp2];
+    if (!src) throw Error{MGD_EINVAL, "vector absent"};
+    MGD_CUDA(cudaMemcpyAsync(h_out, src, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->s));
+    MGD_CUDA(cudaStreamSynchronize(c->s));
+    return MGD_OK;
+  });
+}
+
+int mgd_coupling_dropped(mgd_ctx* c, int a, int b) {
+  if (!c || !c->ready || c->bd.dropped.empty()) return 0;
+  int nc = c->G + 2;
+  if (a < 0 || b < 0 || a >= nc || b >= nc) return 0;
+  return c->bd.dropped[a * nc + b];
+}
+
+int mgd_profile_enable(mgd_ctx* c, int on) {
+  if (!c) return MGD_EINVAL;
+  c->prof.on = on != 0;
+  c->prof.reset();
+  return MGD_OK;
+}
+
+int mgd_profile_read(mgd_ctx* c, int cls, long long* launches, double* ms, double* bytes) {
+  return guarded(c, [&]() -> int {
+    MGD_CUDA(cudaStreamSynchronize(c->s));
+    long long nl = 0;
+    double t = 0, by = 0;
+    for (auto& r : c->prof.recs) {
+      bool match = (r.cls == cls) || (cls == 1 && r.cls == 0);
+      if (!match || !r.b) continue;
+      float e = 0;
+      MGD_CUDA(cudaEventElapsedTime(&e, r.a, r.b));
+      ++nl;
+      t += e;
+      by += r.bytes;
+    }
+    if (launches) *launches = nl;
+    if (ms) *ms = t;
+    if (bytes) *bytes = by;
+    return MGD_OK;
+  });
+}
+
+const char* mgd_last_error(mgd_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+long long mgd_kernel_launches(void) { return __atomic_load_n(&g_kernel_launches, __ATOMIC_RELAXED); }
+
+void mgd_destroy(mgd_ctx* c) {
+  if (!c) return;
+  free_setup(c);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,271 @@
+// mgd_internal.cuh -- internal structures and kernel launchers of the
+// sm_103a solver library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace mgd {
+
+// ------------------------------------------------------------------ errors
+struct Error {
+  int code;
+  std::string msg;
+};
+
+#define MGD_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      throw ::mgd::Error{7, std::string(#call) + ": " + cudaGetErrorString(e_) + " at " +   \
+                                __FILE__ + ":" + std::to_string(__LINE__)};                 \
+  } while (0)
+
+// every kernel launch of the library is followed by this check, which also
+// counts the launch (see mgd_kernel_launches)
+extern long long g_kernel_launches;
+#define MGD_LAUNCH_CHECK()                                         \
+  do {                                                             \
+    __atomic_add_fetch(&::mgd::g_kernel_launches, 1, __ATOMIC_RELAXED); \
+    MGD_CUDA(cudaGetLastError());                                  \
+  } while (0)
+
+constexpr int kThreads = 256;
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------ memory
+// Device allocations owned by a context: freed together at destroy/re-setup.
+struct Arena {
+  std::vector<void*> ptrs;
+  cudaStream_t stream = nullptr;
+  template <typename T>
+  T* alloc(size_t n, bool zero = false) {
+    void* p = nullptr;
+    size_t bytes = (n ? n : 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Error{8, "cudaMalloc(" + std::to_string(bytes) + " bytes) failed: " + cudaGetErrorString(e)};
+    }
+    ptrs.push_back(p);
+    if (zero) MGD_CUDA(cudaMemsetAsync(p, 0, bytes, stream));
+    return (T*)p;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+// Scratch allocations for one setup step (stream-ordered)
+struct Scratch {
+  std::vector<void*> ptrs;
+  cudaStream_t stream;
+  explicit Scratch(cudaStream_t s) : stream(s) {}
+  template <typename T>
+  T* alloc(size_t n) {
+    void* p = nullptr;
+    size_t bytes = (n ? n : 1) * sizeof(T);
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Error{8, "cudaMallocAsync(" + std::to_string(bytes) + " bytes) failed"};
+    }
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, stream);
+  }
+};
+
+// ------------------------------------------------------------------ matrices
+struct Csr {  // device CSR, FP64 values
+  int n = 0, m = 0, nnz = 0;
+  int* rp = nullptr;
+  int* ci = nullptr;
+  double* v = nullptr;
+};
+
+// sparse-kernel formats chosen per level by the autotuner
+enum Fmt { FMT_SELL = 0, FMT_CSR1 = 1, FMT_CSR2 = 2, FMT_CSR4 = 3, FMT_CSR8 = 4, FMT_CSR16 = 5, FMT_CSR32 = 6 };
+constexpr int kNumFmt = 7;
+
+struct Sell {  // sliced ELL, slice height 32, column-major inside a slice
+  int n = 0, nslices = 0;
+  long long nstored = 0;
+  int* sptr = nullptr;  // [nslices+1] element offsets (multiples of 32)
+  int* ci = nullptr;
+  double* v = nullptr;
+  float* v32 = nullptr;
+};
+
+// Per-level device view used by the V-cycle kernels (T = double or float).
+template <typename T>
+struct LDesc {
+  int n, nc;
+  // operator (CSR and, when built, SELL)
+  const int* rp;
+  const int* ci;
+  const T* v;
+  const int* sptr;
+  const int* sci;
+  const T* sv;
+  const T* dinv;
+  // prolongation P (n x nc) and restriction R = P^T (nc x n), CSR
+  const int* prp;
+  const int* pci;
+  const T* pv;
+  const int* rrp;
+  const int* rci;
+  const T* rv;
+  // vectors
+  T* b;   // right-hand side of this level
+  T* x;   // output of this level's cycle
+  T* xt;  // smoothed iterate before post-smoothing
+  T* r;   // residual
+  T* bc;  // next level's right-hand side
+  T* xc;  // next level's output
+  // coarsest level: dense inverse (FP64, row-major cn x cn)
+  const double* cinv;
+  int cn;
+};
+
+// Block-level pointer reference: absolute, or relative to the current
+// preconditioner input v / output z held in device memory (graph-safe).
+struct PRef {
+  int slot;          // 0: absolute, 1: v + off, 2: z + off
+  long long off;
+  double* abs;
+};
+
+struct IOSlots {
+  const double* v;
+  double* z;
+};
+
+constexpr int kMaxTerms = 32;
+template <typename T>
+struct ProduceDesc {  // dst = (T)(a + sum_t s_t * d_t (.) w_t)
+  T* dst;
+  PRef a;             // a.slot == 0 && a.abs == nullptr: a = 0
+  int nt;
+  const double* d[kMaxTerms];  // nullptr: 1
+  PRef w[kMaxTerms];
+  double s[kMaxTerms];
+};
+template <typename T>
+struct ConsumeDesc {  // dst = base + s * (double)x
+  PRef dst;
+  PRef base;          // null: 0
+  double s;
+  const T* x;
+};
+template <typename T>
+struct JacDesc {      // option #1: x = dinv (.) b
+  T* x;
+  const T* b;
+  const T* dinv;
+};
+
+// ------------------------------------------------------------------ setup launchers (setup_kernels.cu)
+void exclusive_scan(const int* in, int* out, int n, cudaStream_t s);  // out[0..n], out[n] = total
+int read_int(const int* d, cudaStream_t s);
+
+void launch_validate(int n, int nnz, int N, int nc, const int* rp, const int* ci, const double* v, int* flags,
+                     cudaStream_t s);
+void launch_block_count(int n, int N, int nc, const int* rp, const int* ci, int* cnt, int* pairs, cudaStream_t s);
+void launch_block_fill(int n, int N, int nc, const int* rp, const int* ci, const double* v, const int* brp,
+                       int* bci, double* bv, double** dtab, cudaStream_t s);
+void launch_diag_extract(int n, const int* rp, const int* ci, const double* v, double* d, cudaStream_t s);
+void launch_diag_modify(int n, const int* rp, const int* ci, double* v, const double* x, const double* y,
+                        const double* z, cudaStream_t s);
+void launch_gamma_wd(int n, const int* rp, const int* ci, const double* v, double theta, int* count,
+                     cudaStream_t s);
+void launch_gamma_wc(int n, const double* d, const double* diag, double theta, int* count, cudaStream_t s);
+
+void launch_strength(int n, const int* rp, const int* ci, const double* v, double theta, uint8_t* S,
+                     cudaStream_t s);
+void launch_count_st(int n, const int* rp, const int* ci, const uint8_t* S, int* cnt, cudaStream_t s);
+void launch_fill_st(int n, const int* rp, const int* ci, const uint8_t* S, const int* strp, int* cursor,
+                    int* stci, cudaStream_t s);
+void launch_pmis_init(int n, const int* rp, const uint8_t* S, const int* cnt, unsigned long long seed, int level,
+                      double* w, signed char* CF, cudaStream_t s);
+void launch_pmis_round(int n, const int* rp, const int* ci, const uint8_t* S, const int* strp, const int* stci,
+                       const double* w, signed char* CF, uint8_t* newc, int* undecided, cudaStream_t s);
+void launch_interp_count(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF, int* cnt,
+                         int* isc, cudaStream_t s);
+void launch_interp_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S,
+                        const signed char* CF, const int* cidx, const int* prp, int* pci, double* pv,
+                        cudaStream_t s);
+void launch_transpose_count(int nnz, const int* ci, int* cnt, cudaStream_t s);
+void launch_transpose_fill(int n, const int* rp, const int* ci, const double* v, const int* trp, int* cursor,
+                           int* tci, double* tv, cudaStream_t s);
+void launch_sort_rows(int n, const int* rp, int* ci, double* v, cudaStream_t s);
+void launch_spgemm_ub(int n, const int* xrp, const int* xci, const int* yrp, int* ub, cudaStream_t s);
+void launch_spgemm_expand(int n, const int* xrp, const int* xci, const double* xv, const int* yrp,
+                          const int* yci, const double* yv, const long long* off, int* tc, double* tv,
+                          int* cnt, cudaStream_t s);
+void launch_spgemm_compact(int n, const long long* off, const int* tc, const double* tv, const int* crp,
+                           int* cci, double* cv, cudaStream_t s);
+void launch_l1_dinv(int n, const int* rp, const double* v, double* dinv, cudaStream_t s);
+void launch_diag_inv(int n, const int* rp, const int* ci, const double* v, double* dinv, cudaStream_t s);
+void launch_densify(int n, const int* rp, const int* ci, const double* v, double* a, cudaStream_t s);
+void launch_dense_inverse(int n, double* a, int* piv, double* inv, double* invT, int* status, cudaStream_t s);
+void launch_pctl_ac_count(int N, int nc, const int* const* brp, const int* const* bci, int* cnt, cudaStream_t s);
+void launch_pctl_ac_fill(int N, int nc, int G, const int* const* brp, const int* const* bci,
+                         const double* const* bv, const double* const* p, const double* const* dtab,
+                         const int* acrp, int* acci, double* acv, cudaStream_t s);
+void launch_sell_widths(int n, const int* rp, int* w, cudaStream_t s);
+void launch_sell_fill(int n, const int* rp, const int* ci, const double* v, const int* sptr, int* sci, double* sv,
+                      cudaStream_t s);
+void launch_grad_vals(int n, const int* rp, const int* ci, const double* x, const double* lam, double* g,
+                      cudaStream_t s);
+void launch_offsets64(const int* cnt, long long* off, int n, cudaStream_t s);
+
+// ------------------------------------------------------------------ solve launchers (solve_kernels.cu)
+enum Phase { PH_PRE = 0, PH_RESTRICT = 1, PH_PROLONG = 2, PH_POST = 3, PH_COARSE = 4, PH_JAC1 = 5 };
+
+template <typename T>
+void launch_phase(int phase, int fmtA, int tprRP, const LDesc<T>* d_descs, int ndesc, int maxrows,
+                  cudaStream_t s);
+template <typename T>
+void launch_produce(const ProduceDesc<T>* d, int nd, int N, const IOSlots* io, cudaStream_t s);
+template <typename T>
+void launch_consume(const ConsumeDesc<T>* d, int nd, int N, const IOSlots* io, cudaStream_t s);
+template <typename T>
+void launch_jacobi(const JacDesc<T>* d, int nd, int N, cudaStream_t s);
+template <typename T>
+void launch_residual(int fmt, int n, const int* rp, const int* ci, const T* v, const int* sptr, const int* sci,
+                     const T* sv, const T* b, const T* x, T* r, cudaStream_t s);
+template <typename T>
+void launch_axpy(int n, T* y, const T* x, cudaStream_t s);  // y += x
+
+void launch_spmv_f64(int fmt, int n, const int* rp, const int* ci, const double* v, const int* sptr,
+                     const int* sci, const double* sv, const double* x, double* y, cudaStream_t s);
+void launch_resid_f64(int fmt, int n, const int* rp, const int* ci, const double* v, const int* sptr,
+                      const int* sci, const double* sv, const double* b, const double* x, double* r,
+                      cudaStream_t s);
+void launch_set_io(IOSlots* io, const double* v, double* z, cudaStream_t s);
+void launch_cast_f64_f32(int n, const double* a, float* b, cudaStream_t s);
+void launch_cast_f32_f64(int n, const float* a, double* b, cudaStream_t s);
+void launch_copy_f64(int n, const double* a, double* b, cudaStream_t s);
+
+// Arnoldi / vector kernels (FP64)
+constexpr int kDotBlocks = 608;  // 4 x 152 SMs
+void launch_mdot(int n, const double* V, long long ldv, int nv, const double* w, double* partial, double* out,
+                 cudaStream_t s);
+void launch_vupdate(int n, const double* V, long long ldv, int nv, const double* h, double* w, double* partial,
+                    double* nrm2, cudaStream_t s);  // w -= V h; nrm2 = ||w||^2
+void launch_scale_by_norm(int n, const double* w, const double* nrm2, double* v, cudaStream_t s);
+void launch_vcomb(int n, const double* Z, long long ldz, int nv, const double* y, double* x, cudaStream_t s);
+void launch_norm2(int n, const double* x, double* partial, double* out, cudaStream_t s);
+void launch_block_resid(int N, int nc, const int* const* brp, const int* const* bci, const double* const* bv,
+                        const double* const* dtab, const IOSlots* io, double* r, cudaStream_t s);
+void launch_saxpy_vec(int n, double a, const double* x, double* y, cudaStream_t s);
+void launch_lincomb(int n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
+
+}  // namespace mgd

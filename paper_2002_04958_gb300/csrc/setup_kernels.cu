@@ -1,0 +1,909 @@
+// setup_kernels.cu -- device kernels of the AMG setup phase and of the block
+// extraction (Sections 3.1, 3.3-3.6).
+//
+// This translation unit is compiled with -fmad=false and writes every
+// floating-point step with an explicit round-to-nearest intrinsic, so each
+// product and sum is rounded once, in the order the method's definitions
+// state.  The C/F splittings and coarse operators therefore do not depend on
+// the thread mapping: every output entry is produced by one thread in a fixed
+// order.
+#include "mgd_internal.cuh"
+
+namespace mgd {
+
+// ------------------------------------------------------------------ scan
+template <typename I>
+__global__ void k_scan_block(const int* in, I* out, I* bsum, int n) {
+  // 256 threads x 4 items per block
+  __shared__ I sh[kThreads];
+  int base = blockIdx.x * kThreads * 4;
+  I v[4];
+  I tsum = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    int i = base + threadIdx.x * 4 + k;
+    v[k] = (i < n && in) ? (I)in[i] : 0;
+    tsum += v[k];
+  }
+  sh[threadIdx.x] = tsum;
+  __syncthreads();
+  for (int off = 1; off < kThreads; off <<= 1) {
+    I t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  I run = sh[threadIdx.x] - tsum;  // exclusive prefix of this thread
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    int i = base + threadIdx.x * 4 + k;
+    if (i < n) out[i] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kThreads - 1) bsum[blockIdx.x] = sh[kThreads - 1];
+}
+
+template <typename I>
+__global__ void k_scan_block_i(const I* in, I* out, I* bsum, int n) {
+  __shared__ I sh[kThreads];
+  int base = blockIdx.x * kThreads * 4;
+  I v[4];
+  I tsum = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    int i = base + threadIdx.x * 4 + k;
+    v[k] = i < n ? in[i] : 0;
+    tsum += v[k];
+  }
+  sh[threadIdx.x] = tsum;
+  __syncthreads();
+  for (int off = 1; off < kThreads; off <<= 1) {
+    I t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  I run = sh[threadIdx.x] - tsum;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    int i = base + threadIdx.x * 4 + k;
+    if (i < n) out[i] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kThreads - 1) bsum[blockIdx.x] = sh[kThreads - 1];
+}
+
+template <typename I>
+__global__ void k_scan_add(I* out, const I* boff, int n, I* total_out, const I* btotal) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += boff[i / (kThreads * 4)];
+  if (i == 0 && total_out) *total_out = *btotal;
+}
+
+// exclusive scan of I-typed values (recursive over block sums)
+template <typename I>
+static void scan_rec(const I* in, I* out, int n, cudaStream_t s, Scratch& sc) {
+  int nb = cdiv(n, kThreads * 4);
+  I* bsum = sc.alloc<I>(nb + 1);
+  I* boff = sc.alloc<I>(nb + 1);
+  k_scan_block_i<I><<<nb, kThreads, 0, s>>>(in, out, bsum, n);
+  MGD_LAUNCH_CHECK();
+  if (nb > 1) scan_rec<I>(bsum, boff, nb, s, sc);
+  else MGD_CUDA(cudaMemsetAsync(boff, 0, sizeof(I), s));
+  k_scan_add<I><<<cdiv(n, kThreads), kThreads, 0, s>>>(out, boff, n, nullptr, nullptr);
+  MGD_LAUNCH_CHECK();
+}
+
+// out[0..n]: exclusive prefix sums of in[0..n), out[n] = total
+void exclusive_scan(const int* in, int* out, int n, cudaStream_t s) {
+  Scratch sc(s);
+  if (n == 0) {
+    MGD_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
+    return;
+  }
+  int* ext = sc.alloc<int>(n + 1);
+  MGD_CUDA(cudaMemcpyAsync(ext, in, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+  MGD_CUDA(cudaMemsetAsync(ext + n, 0, sizeof(int), s));
+  scan_rec<int>(ext, out, n + 1, s, sc);
+}
+
+__global__ void k_widen(const int* in, long long* out, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[i];
+  if (i == n) out[n] = 0;
+}
+
+void launch_offsets64(const int* cnt, long long* off, int n, cudaStream_t s) {
+  Scratch sc(s);
+  long long* ext = sc.alloc<long long>(n + 1);
+  k_widen<<<cdiv(n + 1, kThreads), kThreads, 0, s>>>(cnt, ext, n);
+  MGD_LAUNCH_CHECK();
+  scan_rec<long long>(ext, off, n + 1, s, sc);
+}
+
+int read_int(const int* d, cudaStream_t s) {
+  int h = 0;
+  MGD_CUDA(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MGD_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+// ------------------------------------------------------------------ validation and block extraction
+// flags[0]: bad column (out of range / unsorted / duplicate); flags[1]: coupling
+// not in the same cell; flags[2]: non-positive or missing diagonal
+__global__ void k_validate(int n, int N, int nc, const int* rp, const int* ci, const double* v, int* flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int a = i / N, k = i - a * N;
+  int prev = -1;
+  bool diag = false;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = ci[p];
+    if (j < 0 || j >= n || j <= prev) atomicOr(&flags[0], 1);
+    prev = j;
+    int b = j / N;
+    if (b != a && j - b * N != k) atomicOr(&flags[1], 1);
+    if (j == i) {
+      diag = true;
+      if (!(v[p] > 0.0)) atomicOr(&flags[2], 1);
+    }
+  }
+  if (!diag) atomicOr(&flags[2], 1);
+}
+
+void launch_validate(int n, int nnz, int N, int nc, const int* rp, const int* ci, const double* v, int* flags,
+                     cudaStream_t s) {
+  (void)nnz;
+  (void)nc;
+  k_validate<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, N, nc, rp, ci, v, flags);
+  MGD_LAUNCH_CHECK();
+}
+
+// cnt[a*N+k]: same-block entries of row (a,k); pairs[a*nc+b] = 1 where D_ab exists
+__global__ void k_block_count(int n, int N, int nc, const int* rp, const int* ci, int* cnt, int* pairs) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int a = i / N;
+  int c = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int b = ci[p] / N;
+    if (b == a) ++c;
+    else pairs[a * nc + b] = 1;
+  }
+  cnt[i] = c;
+}
+
+void launch_block_count(int n, int N, int nc, const int* rp, const int* ci, int* cnt, int* pairs, cudaStream_t s) {
+  k_block_count<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, N, nc, rp, ci, cnt, pairs);
+  MGD_LAUNCH_CHECK();
+}
+
+// brp: block-stacked row pointer over all n rows (block a's rows are a*N..a*N+N-1);
+// block-local columns; couplings scattered into dtab[a*nc+b][k]
+__global__ void k_block_fill(int n, int N, int nc, const int* rp, const int* ci, const double* v, const int* brp,
+                             int* bci, double* bv, double** dtab) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int a = i / N, k = i - a * N;
+  int q = brp[i];
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = ci[p];
+    int b = j / N;
+    if (b == a) {
+      bci[q] = j - a * N;
+      bv[q] = v[p];
+      ++q;
+    } else {
+      double* d = dtab[a * nc + b];
+      if (d) d[k] = v[p];
+    }
+  }
+}
+
+void launch_block_fill(int n, int N, int nc, const int* rp, const int* ci, const double* v, const int* brp,
+                       int* bci, double* bv, double** dtab, cudaStream_t s) {
+  k_block_fill<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, N, nc, rp, ci, v, brp, bci, bv, dtab);
+  MGD_LAUNCH_CHECK();
+}
+
+__global__ void k_diag_extract(int n, const int* rp, const int* ci, const double* v, double* d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double r = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (ci[p] == i) r = v[p];
+  d[i] = r;
+}
+
+void launch_diag_extract(int n, const int* rp, const int* ci, const double* v, double* d, cudaStream_t s) {
+  k_diag_extract<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, d);
+  MGD_LAUNCH_CHECK();
+}
+
+// Section 3.5 diagonal Schur approximations: a_kk -= (x_k * y_k) / z_k
+__global__ void k_diag_modify(int n, const int* rp, const int* ci, double* v, const double* x, const double* y,
+                              const double* z) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (ci[p] == i) {
+      double t = __dmul_rn(x[i], y[i]);
+      t = __ddiv_rn(t, z[i]);
+      v[p] = __dsub_rn(v[p], t);
+    }
+}
+
+void launch_diag_modify(int n, const int* rp, const int* ci, double* v, const double* x, const double* y,
+                        const double* z, cudaStream_t s) {
+  k_diag_modify<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, x, y, z);
+  MGD_LAUNCH_CHECK();
+}
+
+// Definition 2: rows with sum_j a_kj < theta a_kk (row sum left to right)
+__global__ void k_gamma_wd(int n, const int* rp, const int* ci, const double* v, double theta, int* count) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double rs = 0.0, akk = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    rs = __dadd_rn(rs, v[p]);
+    if (ci[p] == i) akk = v[p];
+  }
+  if (rs < __dmul_rn(theta, akk)) atomicAdd(count, 1);
+}
+
+void launch_gamma_wd(int n, const int* rp, const int* ci, const double* v, double theta, int* count,
+                     cudaStream_t s) {
+  k_gamma_wd<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, theta, count);
+  MGD_LAUNCH_CHECK();
+}
+
+// Definition 1: rows with -d_kk <= theta a_kk
+__global__ void k_gamma_wc(int n, const double* d, const double* diag, double theta, int* count) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (-d[i] <= __dmul_rn(theta, diag[i])) atomicAdd(count, 1);
+}
+
+void launch_gamma_wc(int n, const double* d, const double* diag, double theta, int* count, cudaStream_t s) {
+  k_gamma_wc<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, d, diag, theta, count);
+  MGD_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ strength of connection (Section 3.1)
+__global__ void k_strength(int n, const int* rp, const int* ci, const double* v, double theta, uint8_t* S) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double mx = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (ci[p] != i && -v[p] > mx) mx = -v[p];
+  double thr = __dmul_rn(theta, mx);
+  for (int p = rp[i]; p < rp[i + 1]; ++p) S[p] = (uint8_t)(ci[p] != i && mx > 0.0 && -v[p] >= thr);
+}
+
+void launch_strength(int n, const int* rp, const int* ci, const double* v, double theta, uint8_t* S,
+                     cudaStream_t s) {
+  k_strength<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, theta, S);
+  MGD_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ PMIS
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+// u(seed, stream, i): i-th output of a splitmix64 stream keyed by (seed, stream)
+__device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t stream, uint64_t i) {
+  const uint64_t G = 0x9E3779B97F4A7C15ULL;
+  uint64_t key = mix64(mix64(seed + G) + stream * G);
+  uint64_t z = mix64(key + (i + 1) * G);
+  return __dmul_rn((double)(z >> 11), 1.0 / 9007199254740992.0);
+}
+
+__global__ void k_count_st(int n, const int* rp, const int* ci, const uint8_t* S, int* cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (S[p]) atomicAdd(&cnt[ci[p]], 1);
+}
+
+void launch_count_st(int n, const int* rp, const int* ci, const uint8_t* S, int* cnt, cudaStream_t s) {
+  k_count_st<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, S, cnt);
+  MGD_LAUNCH_CHECK();
+}
+
+__global__ void k_fill_st(int n, const int* rp, const int* ci, const uint8_t* S, const int* strp, int* cursor,
+                          int* stci) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (S[p]) {
+      int j = ci[p];
+      int q = strp[j] + atomicAdd(&cursor[j], 1);
+      stci[q] = i;
+    }
+}
+
+void launch_fill_st(int n, const int* rp, const int* ci, const uint8_t* S, const int* strp, int* cursor,
+                    int* stci, cudaStream_t s) {
+  k_fill_st<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, S, strp, cursor, stci);
+  MGD_LAUNCH_CHECK();
+}
+
+// weights w_i = |S^T_i| + u_i; isolated points and points nobody depends on are F
+__global__ void k_pmis_init(int n, const int* rp, const uint8_t* S, const int* cnt, unsigned long long seed,
+                            int level, double* w, signed char* CF) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double u = splitmix_uniform(seed, 1000ULL + (uint64_t)level, (uint64_t)i);
+  double wi = __dadd_rn((double)cnt[i], u);
+  w[i] = wi;
+  int ns = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) ns += S[p];
+  if (ns == 0 && cnt[i] == 0) CF[i] = -1;
+  else if (wi < 1.0) CF[i] = -1;
+  else CF[i] = 0;
+}
+
+void launch_pmis_init(int n, const int* rp, const uint8_t* S, const int* cnt, unsigned long long seed, int level,
+                      double* w, signed char* CF, cudaStream_t s) {
+  k_pmis_init<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, S, cnt, seed, level, w, CF);
+  MGD_LAUNCH_CHECK();
+}
+
+__device__ __forceinline__ bool beats(const double* w, int i, int j) {
+  return w[i] > w[j] || (w[i] == w[j] && i > j);
+}
+
+// round part 1: undecided local maxima over S_i and S^T_i become C (newc)
+__global__ void k_pmis_select(int n, const int* rp, const int* ci, const uint8_t* S, const int* strp,
+                              const int* stci, const double* w, const signed char* CF, uint8_t* newc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint8_t res = 0;
+  if (CF[i] == 0) {
+    bool ismax = true;
+    for (int p = rp[i]; p < rp[i + 1] && ismax; ++p)
+      if (S[p] && CF[ci[p]] == 0 && !beats(w, i, ci[p])) ismax = false;
+    for (int p = strp[i]; p < strp[i + 1] && ismax; ++p)
+      if (CF[stci[p]] == 0 && !beats(w, i, stci[p])) ismax = false;
+    res = ismax;
+  }
+  newc[i] = res;
+}
+
+__global__ void k_pmis_apply(int n, const uint8_t* newc, signed char* CF) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && newc[i]) CF[i] = 1;
+}
+
+// round part 2: undecided points that strongly depend on a C point become F
+__global__ void k_pmis_fmark(int n, const int* rp, const int* ci, const uint8_t* S, signed char* CF,
+                             int* undecided) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (CF[i] != 0) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (S[p] && CF[ci[p]] == 1) {
+      CF[i] = -1;
+      return;
+    }
+  atomicAdd(undecided, 1);
+}
+
+void launch_pmis_round(int n, const int* rp, const int* ci, const uint8_t* S, const int* strp, const int* stci,
+                       const double* w, signed char* CF, uint8_t* newc, int* undecided, cudaStream_t s) {
+  int nb = cdiv(n, kThreads);
+  k_pmis_select<<<nb, kThreads, 0, s>>>(n, rp, ci, S, strp, stci, w, CF, newc);
+  MGD_LAUNCH_CHECK();
+  k_pmis_apply<<<nb, kThreads, 0, s>>>(n, newc, CF);
+  MGD_LAUNCH_CHECK();
+  MGD_CUDA(cudaMemsetAsync(undecided, 0, sizeof(int), s));
+  k_pmis_fmark<<<nb, kThreads, 0, s>>>(n, rp, ci, S, CF, undecided);
+  MGD_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ classical modified interpolation
+__global__ void k_interp_count(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF,
+                               int* cnt, int* isc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  isc[i] = CF[i] == 1;
+  int c = 0;
+  if (CF[i] == 1) c = 1;
+  else
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (S[p] && CF[ci[p]] == 1) ++c;
+  cnt[i] = c;
+}
+
+void launch_interp_count(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF, int* cnt,
+                         int* isc, cudaStream_t s) {
+  k_interp_count<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, S, CF, cnt, isc);
+  MGD_LAUNCH_CHECK();
+}
+
+__device__ __forceinline__ bool opp_sign(double akm, double akk) { return akk > 0.0 ? (akm < 0.0) : (akm > 0.0); }
+
+// One thread per row.  Numerators start from a_ij (j in C_i, row order); strong
+// F neighbours k distribute a_ik abar_kj / sum_{m in C_i} abar_km, or are lumped
+// into the diagonal with the weak neighbours when that sum is zero;
+// w_ij = -num_j / (a_ii + sum_W a_in).
+__global__ void k_interp_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S,
+                              const signed char* CF, const int* cidx, const int* prp, int* pci, double* pv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int base = prp[i];
+  if (CF[i] == 1) {
+    pci[base] = cidx[i];
+    pv[base] = 1.0;
+    return;
+  }
+  int len = prp[i + 1] - base;
+  if (len == 0) return;
+  int t = 0;
+  double diag = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = ci[p];
+    if (j == i) diag = v[p];
+    if (S[p] && CF[j] == 1) {
+      pci[base + t] = j;
+      pv[base + t] = v[p];
+      ++t;
+    }
+  }
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int k = ci[p];
+    if (k == i) continue;
+    double aik = v[p];
+    if (S[p] && CF[k] == 1) continue;
+    if (S[p] && CF[k] == -1) {
+      double akk = 0.0;
+      for (int q = rp[k]; q < rp[k + 1]; ++q)
+        if (ci[q] == k) akk = v[q];
+      double denom = 0.0;
+      for (int q = rp[k]; q < rp[k + 1]; ++q) {
+        int m = ci[q];
+        for (int s = 0; s < len; ++s)
+          if (pci[base + s] == m) {
+            if (opp_sign(v[q], akk)) denom = __dadd_rn(denom, v[q]);
+            break;
+          }
+      }
+      if (denom == 0.0) {
+        diag = __dadd_rn(diag, aik);
+      } else {
+        for (int q = rp[k]; q < rp[k + 1]; ++q) {
+          int m = ci[q];
+          for (int s = 0; s < len; ++s)
+            if (pci[base + s] == m) {
+              if (opp_sign(v[q], akk)) {
+                double prod = __dmul_rn(aik, v[q]);
+                pv[base + s] = __dadd_rn(pv[base + s], __ddiv_rn(prod, denom));
+              }
+              break;
+            }
+        }
+      }
+    } else {
+      diag = __dadd_rn(diag, aik);
+    }
+  }
+  for (int s = 0; s < len; ++s) {
+    pv[base + s] = (diag != 0.0) ? __ddiv_rn(-pv[base + s], diag) : 0.0;
+    pci[base + s] = cidx[pci[base + s]];
+  }
+}
+
+void launch_interp_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S,
+                        const signed char* CF, const int* cidx, const int* prp, int* pci, double* pv,
+                        cudaStream_t s) {
+  k_interp_fill<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, S, CF, cidx, prp, pci, pv);
+  MGD_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ transpose
+__global__ void k_transpose_count(int nnz, const int* ci, int* cnt) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nnz) atomicAdd(&cnt[ci[p]], 1);
+}
+
+void launch_transpose_count(int nnz, const int* ci, int* cnt, cudaStream_t s) {
+  if (nnz == 0) return;
+  k_transpose_count<<<cdiv(nnz, kThreads), kThreads, 0, s>>>(nnz, ci, cnt);
+  MGD_LAUNCH_CHECK();
+}
+
+__global__ void k_transpose_fill(int n, const int* rp, const int* ci, const double* v, const int* trp,
+                                 int* cursor, int* tci, double* tv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = ci[p];
+    int q = trp[j] + atomicAdd(&cursor[j], 1);
+    tci[q] = i;
+    tv[q] = v[p];
+  }
+}
+
+void launch_transpose_fill(int n, const int* rp, const int* ci, const double* v, const int* trp, int* cursor,
+                           int* tci, double* tv, cudaStream_t s) {
+  k_transpose_fill<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, trp, cursor, tci, tv);
+  MGD_LAUNCH_CHECK();
+}
+
+// insertion sort of each row by column (columns of a row are distinct)
+__global__ void k_sort_rows(int n, const int* rp, int* ci, double* v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int b = rp[i], e = rp[i + 1];
+  for (int a = b + 1; a < e; ++a) {
+    int cc = ci[a];
+    double vv = v[a];
+    int q = a - 1;
+    while (q >= b && ci[q] > cc) {
+      ci[q + 1] = ci[q];
+      v[q + 1] = v[q];
+      --q;
+    }
+    ci[q + 1] = cc;
+    v[q + 1] = vv;
+  }
+}
+
+void launch_sort_rows(int n, const int* rp, int* ci, double* v, cudaStream_t s) {
+  k_sort_rows<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v);
+  MGD_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ SpGEMM C = X Y (Galerkin products)
+// For entry (i, j) the products x_ik y_kj are summed in the order of k along
+// row i of X, the first product initialising the sum: products are expanded
+// in that order, stably sorted by column, and each run is summed left to right.
+__global__ void k_spgemm_ub(int n, const int* xrp, const int* xci, const int* yrp, int* ub) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = 0;
+  for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
+    int k = xci[p];
+    c += yrp[k + 1] - yrp[k];
+  }
+  ub[i] = c;
+}
+
+void launch_spgemm_ub(int n, const int* xrp, const int* xci, const int* yrp, int* ub, cudaStream_t s) {
+  k_spgemm_ub<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, xrp, xci, yrp, ub);
+  MGD_LAUNCH_CHECK();
+}
+
+__global__ void k_spgemm_expand(int n, const int* xrp, const int* xci, const double* xv, const int* yrp,
+                                const int* yci, const double* yv, const long long* off, int* tc, double* tv,
+                                int* cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long b = off[i];
+  long long t = b;
+  for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
+    int k = xci[p];
+    double x = xv[p];
+    for (int q = yrp[k]; q < yrp[k + 1]; ++q) {
+      tc[t] = yci[q];
+      tv[t] = __dmul_rn(x, yv[q]);
+      ++t;
+    }
+  }
+  long long e = t;
+  // stable insertion sort by column
+  for (long long a = b + 1; a < e; ++a) {
+    int cc = tc[a];
+    double vv = tv[a];
+    long long q = a - 1;
+    while (q >= b && tc[q] > cc) {
+      tc[q + 1] = tc[q];
+      tv[q + 1] = tv[q];
+      --q;
+    }
+    tc[q + 1] = cc;
+    tv[q + 1] = vv;
+  }
+  // sum runs of equal columns left to right, compacting in place
+  long long w = b;
+  for (long long a = b; a < e;) {
+    int cc = tc[a];
+    double acc = tv[a];
+    long long q = a + 1;
+    while (q < e && tc[q] == cc) {
+      acc = __dadd_rn(acc, tv[q]);
+      ++q;
+    }
+    tc[w] = cc;
+    tv[w] = acc;
+    ++w;
+    a = q;
+  }
+  cnt[i] = (int)(w - b);
+}
+
+void launch_spgemm_expand(int n, const int* xrp, const int* xci, const double* xv, const int* yrp,
+                          const int* yci, const double* yv, const long long* off, int* tc, double* tv, int* cnt,
+                          cudaStream_t s) {
+  k_spgemm_expand<<<cdiv(n, 128), 128, 0, s>>>(n, xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt);
+  MGD_LAUNCH_CHECK();
+}
+
+__global__ void k_spgemm_compact(int n, const long long* off, const int* tc, const double* tv, const int* crp,
+                                 int* cci, double* cv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long b = off[i];
+  int len = crp[i + 1] - crp[i];
+  for (int k = 0; k < len; ++k) {
+    cci[crp[i] + k] = tc[b + k];
+    cv[crp[i] + k] = tv[b + k];
+  }
+}
+
+void launch_spgemm_compact(int n, const long long* off, const int* tc, const double* tv, const int* crp, int* cci,
+                           double* cv, cudaStream_t s) {
+  k_spgemm_compact<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, off, tc, tv, crp, cci, cv);
+  MGD_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ smoother diagonals, coarsest inverse
+__global__ void k_l1_dinv(int n, const int* rp, const double* v, double* dinv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) s = __dadd_rn(s, fabs(v[p]));
+  dinv[i] = __ddiv_rn(1.0, s);
+}
+
+void launch_l1_dinv(int n, const int* rp, const double* v, double* dinv, cudaStream_t s) {
+  k_l1_dinv<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, v, dinv);
+  MGD_LAUNCH_CHECK();
+}
+
+__global__ void k_diag_inv(int n, const int* rp, const int* ci, const double* v, double* dinv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d = 1.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (ci[p] == i) d = v[p];
+  dinv[i] = __ddiv_rn(1.0, d);
+}
+
+void launch_diag_inv(int n, const int* rp, const int* ci, const double* v, double* dinv, cudaStream_t s) {
+  k_diag_inv<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, dinv);
+  MGD_LAUNCH_CHECK();
+}
+
+__global__ void k_densify(int n, const int* rp, const int* ci, const double* v, double* a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int j = 0; j < n; ++j) a[(size_t)i * n + j] = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) a[(size_t)i * n + ci[p]] = v[p];
+}
+
+void launch_densify(int n, const int* rp, const int* ci, const double* v, double* a, cudaStream_t s) {
+  k_densify<<<cdiv(n, 128), 128, 0, s>>>(n, rp, ci, v, a);
+  MGD_LAUNCH_CHECK();
+}
+
+// Gaussian elimination with partial pivoting on one CTA (n <= a few hundred),
+// then the explicit inverse column by column (one thread per unit vector).
+__global__ void k_dense_inverse(int n, double* a, int* piv, double* inv, double* invT, int* status) {
+  __shared__ int s_pr;
+  __shared__ double s_best;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      int pr = k;
+      double best = fabs(a[(size_t)k * n + k]);
+      for (int i = k + 1; i < n; ++i) {
+        double t = fabs(a[(size_t)i * n + k]);
+        if (t > best) {
+          best = t;
+          pr = i;
+        }
+      }
+      s_pr = pr;
+      s_best = best;
+      piv[k] = pr;
+    }
+    __syncthreads();
+    if (s_best == 0.0) {
+      if (threadIdx.x == 0) *status = 1;
+      return;
+    }
+    int pr = s_pr;
+    if (pr != k)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double t = a[(size_t)k * n + j];
+        a[(size_t)k * n + j] = a[(size_t)pr * n + j];
+        a[(size_t)pr * n + j] = t;
+      }
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      double l = a[(size_t)i * n + k] / a[(size_t)k * n + k];
+      a[(size_t)i * n + k] = l;
+      for (int j = k + 1; j < n; ++j) a[(size_t)i * n + j] -= l * a[(size_t)k * n + j];
+    }
+    __syncthreads();
+  }
+  // column c of the inverse: solve A x = e_c
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    double* x = inv + (size_t)c * n;  // temporarily column-major in inv
+    for (int i = 0; i < n; ++i) x[i] = (i == c) ? 1.0 : 0.0;
+    for (int k = 0; k < n; ++k)
+      if (piv[k] != k) {
+        double t = x[k];
+        x[k] = x[piv[k]];
+        x[piv[k]] = t;
+      }
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < i; ++j) x[i] -= a[(size_t)i * n + j] * x[j];
+    for (int i = n - 1; i >= 0; --i) {
+      for (int j = i + 1; j < n; ++j) x[i] -= a[(size_t)i * n + j] * x[j];
+      x[i] /= a[(size_t)i * n + i];
+    }
+  }
+  __syncthreads();
+  // inv holds columns: invT[c*n + i] = (A^{-1})_{ic} is the row-major transpose
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) invT[e] = inv[e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int i = e / n, c = e % n;
+    inv[(size_t)i * n + c] = invT[(size_t)c * n + i];
+  }
+}
+
+void launch_dense_inverse(int n, double* a, int* piv, double* inv, double* invT, int* status, cudaStream_t s) {
+  k_dense_inverse<<<1, 128, 0, s>>>(n, a, piv, inv, invT, status);
+  MGD_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ PCTL coarse operator, Eq. 3.3
+__global__ void k_pctl_ac_count(int N, int nc, const int* const* brp, const int* const* bci, int* cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  // union of the row patterns of all diagonal blocks: count distinct columns
+  int c = 0;
+  for (int a = 0; a < nc; ++a)
+    for (int p = brp[a][i]; p < brp[a][i + 1]; ++p) {
+      int j = bci[a][p];
+      bool seen = false;
+      for (int b = 0; b < a && !seen; ++b)
+        for (int q = brp[b][i]; q < brp[b][i + 1]; ++q)
+          if (bci[b][q] == j) {
+            seen = true;
+            break;
+          }
+      if (!seen) ++c;
+    }
+  cnt[i] = c;
+}
+
+void launch_pctl_ac_count(int N, int nc, const int* const* brp, const int* const* bci, int* cnt, cudaStream_t s) {
+  k_pctl_ac_count<<<cdiv(N, 128), 128, 0, s>>>(N, nc, brp, bci, cnt);
+  MGD_LAUNCH_CHECK();
+}
+
+// values in the order of Eq. 3.3: sum_g p_g(i) a^g_ij p_g(j) + a^E_ij + p_I(i) a^I_ij p_I(j)
+// + [i == j] (sum_g d_Eg p_g + sum_g p_g d_gE + d_EI p_I + p_I d_IE)
+__global__ void k_pctl_ac_fill(int N, int nc, int G, const int* const* brp, const int* const* bci,
+                               const double* const* bv, const double* const* p, const double* const* dtab,
+                               const int* acrp, int* acci, double* acv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int base = acrp[i], len = 0;
+  for (int a = 0; a < nc; ++a)
+    for (int q = brp[a][i]; q < brp[a][i + 1]; ++q) {
+      int j = bci[a][q];
+      bool seen = false;
+      for (int s = 0; s < len; ++s)
+        if (acci[base + s] == j) {
+          seen = true;
+          break;
+        }
+      if (!seen) {
+        // insert sorted
+        int s = len - 1;
+        while (s >= 0 && acci[base + s] > j) {
+          acci[base + s + 1] = acci[base + s];
+          --s;
+        }
+        acci[base + s + 1] = j;
+        ++len;
+      }
+    }
+  int E = G, I = G + 1;
+  for (int s = 0; s < len; ++s) {
+    int j = acci[base + s];
+    double acc = 0.0;
+    for (int g = 0; g < G; ++g)
+      for (int q = brp[g][i]; q < brp[g][i + 1]; ++q)
+        if (bci[g][q] == j) acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(p[g][i], bv[g][q]), p[g][j]));
+    for (int q = brp[E][i]; q < brp[E][i + 1]; ++q)
+      if (bci[E][q] == j) acc = __dadd_rn(acc, bv[E][q]);
+    for (int q = brp[I][i]; q < brp[I][i + 1]; ++q)
+      if (bci[I][q] == j) acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(p[I][i], bv[I][q]), p[I][j]));
+    if (j == i) {
+      for (int g = 0; g < G; ++g)
+        if (dtab[E * nc + g]) acc = __dadd_rn(acc, __dmul_rn(dtab[E * nc + g][i], p[g][i]));
+      for (int g = 0; g < G; ++g)
+        if (dtab[g * nc + E]) acc = __dadd_rn(acc, __dmul_rn(p[g][i], dtab[g * nc + E][i]));
+      if (dtab[E * nc + I]) acc = __dadd_rn(acc, __dmul_rn(dtab[E * nc + I][i], p[I][i]));
+      if (dtab[I * nc + E]) acc = __dadd_rn(acc, __dmul_rn(p[I][i], dtab[I * nc + E][i]));
+    }
+    acv[base + s] = acc;
+  }
+}
+
+void launch_pctl_ac_fill(int N, int nc, int G, const int* const* brp, const int* const* bci,
+                         const double* const* bv, const double* const* p, const double* const* dtab,
+                         const int* acrp, int* acci, double* acv, cudaStream_t s) {
+  k_pctl_ac_fill<<<cdiv(N, 128), 128, 0, s>>>(N, nc, G, brp, bci, bv, p, dtab, acrp, acci, acv);
+  MGD_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ SELL-32 construction
+__global__ void k_sell_widths(int n, const int* rp, int* w) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int nsl = (n + 31) / 32;
+  if (s >= nsl) return;
+  int mx = 0;
+  for (int r = s * 32; r < min(n, s * 32 + 32); ++r) mx = max(mx, rp[r + 1] - rp[r]);
+  w[s] = mx * 32;
+}
+
+void launch_sell_widths(int n, const int* rp, int* w, cudaStream_t s) {
+  int nsl = (n + 31) / 32;
+  k_sell_widths<<<cdiv(nsl, kThreads), kThreads, 0, s>>>(n, rp, w);
+  MGD_LAUNCH_CHECK();
+}
+
+// padding: column = the row itself, value 0
+__global__ void k_sell_fill(int n, const int* rp, const int* ci, const double* v, const int* sptr, int* sci,
+                            double* sv) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int nsl = (n + 31) / 32;
+  if (r >= nsl * 32) return;
+  int s = r >> 5, lane = r & 31;
+  int base = sptr[s];
+  int width = (sptr[s + 1] - base) >> 5;
+  int len = r < n ? rp[r + 1] - rp[r] : 0;
+  int b = r < n ? rp[r] : 0;
+  int self = r < n ? r : 0;
+  for (int j = 0; j < width; ++j) {
+    int idx = base + j * 32 + lane;
+    if (j < len) {
+      sci[idx] = ci[b + j];
+      sv[idx] = v[b + j];
+    } else {
+      sci[idx] = self;
+      sv[idx] = 0.0;
+    }
+  }
+}
+
+void launch_sell_fill(int n, const int* rp, const int* ci, const double* v, const int* sptr, int* sci, double* sv,
+                      cudaStream_t s) {
+  int nsl = (n + 31) / 32;
+  k_sell_fill<<<cdiv(nsl * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, sptr, sci, sv);
+  MGD_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ adjoint gradient
+__global__ void k_grad_vals(int n, const int* rp, const int* ci, const double* x, const double* lam, double* g) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double l = lam[i];
+  for (int p = rp[i]; p < rp[i + 1]; ++p) g[p] = -l * x[ci[p]];
+}
+
+void launch_grad_vals(int n, const int* rp, const int* ci, const double* x, const double* lam, double* g,
+                      cudaStream_t s) {
+  k_grad_vals<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, x, lam, g);
+  MGD_LAUNCH_CHECK();
+}
+
+}  // namespace mgd

@@ -1,0 +1,235 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bar (FP64 mode): C/F splittings, coarse patterns, interpolation and coarse
+values bit-exact (the setup kernels round every step as the oracle does);
+FGMRES iteration counts equal; solution values within 1e-10 relative.
+FP32 V-cycle mode: iteration counts within +-1 of the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+from paper_2002_04958_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+KIND_NAMES = ["amg", "pctl", "schur1", "schur2", "bd", "blt"]
+
+CASES = [
+    # (G, dims, multigroup, inclusion) -- ragged sizes that span many 256-row tiles
+    (1, (45, 37), False, False),
+    (1, (40, 40), False, True),
+    (4, (29, 23), True, False),
+    (20, (13, 11), True, False),
+    (2, (9, 8, 7), True, False),
+]
+
+
+def _system(case, seed=0):
+    G, dims, mg, inc = case
+    return I.make_system(G, dims, seed=seed, multigroup=mg, inclusion=inc)
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2002_04958_gb300 import mgdamg
+    return mgdamg
+
+
+def _oracle_hierarchy(orc, ob, kind, op_kind, comp):
+    if kind == "amg":
+        return ob.amg(orc.OP_MONO, 0)
+    return ob.amg(op_kind, comp)
+
+
+def _compare_hierarchy(slv, op, oh):
+    info = slv.op_info(op)
+    assert info["nlevels"] == oh.nlevels, (info, oh.nlevels)
+    assert bool(info["coarse_lu"]) == oh.coarse_is_lu
+    for l in range(oh.nlevels):
+        g = slv.level(op, l)
+        rp, ci, v = oh.A(l).arrays()
+        assert np.array_equal(g["rp"], rp), f"level {l} rowptr"
+        assert np.array_equal(g["ci"], ci), f"level {l} columns"
+        assert np.array_equal(g["v"], v), f"level {l} values differ (max {abs(g['v'] - v).max():.3e})"
+        if l < oh.nlevels - 1:
+            assert np.array_equal(g["cf"], oh.CF(l)), f"level {l} C/F"
+            prp, pci, pv = oh.P(l).arrays()
+            assert np.array_equal(g["prp"], prp) and np.array_equal(g["pci"], pci), f"level {l} P pattern"
+            assert np.array_equal(g["pv"], pv), f"level {l} P values"
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"G{c[0]}_{'x'.join(map(str, c[1]))}{'_inc' if c[3] else ''}")
+@pytest.mark.parametrize("kind", KIND_NAMES)
+def test_setup_bit_exact(gpu, orc, case, kind):
+    s = _system(case)
+    slv = gpu.Solver().setup_system(s, kind)
+    Ao = orc.csr_of_system(s)
+    ob = orc.Block(Ao, s.G, s.N, kind)
+    st = slv.stats()
+    ops = [slv.op_info(k) for k in range(st["n_ops"])]
+    for k, info in enumerate(ops):
+        if kind == "pctl" and info["kind"] == 5:
+            continue  # A_c depends on the iterative p_a: compared by value below
+        if info["use_jacobi"]:
+            continue
+        oh = _oracle_hierarchy(orc, ob, kind, info["kind"], info["comp"])
+        _compare_hierarchy(slv, k, oh)
+    if kind == "pctl":
+        for a in range(s.nc):
+            if a == s.G:
+                continue
+            pg = slv.block_vector(0, a)
+            po = ob.vec(0, a)
+            assert np.allclose(pg, po, rtol=1e-10, atol=1e-12 * abs(po).max())
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"G{c[0]}_{'x'.join(map(str, c[1]))}{'_inc' if c[3] else ''}")
+@pytest.mark.parametrize("kind", KIND_NAMES)
+def test_solve_parity_fp64(gpu, orc, case, kind):
+    s = _system(case)
+    slv = gpu.Solver().setup_system(s, kind)
+    x, it, rr, rc = slv.solve(torch.from_numpy(s.b), tol=1e-8, allow_noconv=True)
+    Ao = orc.csr_of_system(s)
+    xo, ito, rro, sto, _ = orc.fgmres(Ao, s.b, orc.Block(Ao, s.G, s.N, kind), tol=1e-8, maxit=1000)
+    assert sto == 0 and rc == 0
+    assert it == ito, (it, ito)
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
+    # independent residual check in FP64 on the host
+    A = s.scipy()
+    assert np.linalg.norm(s.b - A @ xg) <= 1e-8 * np.linalg.norm(s.b) * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("kind", ["amg", "schur1", "schur2", "bd"])
+def test_precond_apply_matches_oracle(gpu, orc, kind):
+    s = _system(CASES[2])
+    slv = gpu.Solver().setup_system(s, kind)
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(s.n)
+    z = slv.precond_apply(torch.from_numpy(v)).cpu().numpy()
+    Ao = orc.csr_of_system(s)
+    zo = orc.Block(Ao, s.G, s.N, kind).apply(v)
+    assert np.linalg.norm(z - zo) <= 1e-12 * np.linalg.norm(zo)
+
+
+@pytest.mark.parametrize("kind", ["amg", "schur1", "schur2", "bd", "pctl"])
+def test_fp32_vcycle_iterations(gpu, orc, kind):
+    s = _system(CASES[2])
+    slv = gpu.Solver(precision=1).setup_system(s, kind)
+    x, it, rr, rc = slv.solve(torch.from_numpy(s.b), tol=1e-8, allow_noconv=True)
+    Ao = orc.csr_of_system(s)
+    _, ito, _, _, _ = orc.fgmres(Ao, s.b, orc.Block(Ao, s.G, s.N, kind), tol=1e-8)
+    assert rc == 0 and rr <= 1e-8
+    assert abs(it - ito) <= 1, (it, ito)
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(s.b - s.scipy() @ xg) <= 1.0000001e-8 * np.linalg.norm(s.b)
+
+
+@pytest.mark.parametrize("kind", ["bd", "schur2", "schur1", "blt"])
+def test_batched_and_graph_identical(gpu, kind):
+    s = _system(CASES[3])
+    b = torch.from_numpy(s.b)
+    ref = gpu.Solver(autotune=0).setup_system(s, kind)
+    xr, itr, _, _ = ref.solve(b)
+    for opts in [dict(batched=1), dict(use_graph=1), dict(batched=1, use_graph=1),
+                 dict(batched=1, use_graph=1, precision=0)]:
+        slv = gpu.Solver(autotune=0, **opts).setup_system(s, kind)
+        x, it, _, _ = slv.solve(b)
+        assert it == itr
+        assert torch.equal(x, xr), opts
+
+
+def test_adaptive_drops_match_oracle(gpu, orc):
+    s = _system(CASES[2])
+    for kind in ["schur1", "schur2", "pctl"]:
+        slv = gpu.Solver(adaptive=1).setup_system(s, kind)
+        Ao = orc.csr_of_system(s)
+        ob = orc.Block(Ao, s.G, s.N, kind, orc.opts(adaptive=1))
+        for a in range(s.nc):
+            for b in range(s.nc):
+                assert slv.coupling_dropped(a, b) == ob.dropped(a, b)
+        x, it, rr, rc = slv.solve(torch.from_numpy(s.b), allow_noconv=True)
+        _, ito, _, _, _ = orc.fgmres(Ao, s.b, ob, tol=1e-8)
+        assert it == ito
+
+
+def test_edge_cases(gpu):
+    from paper_2002_04958_gb300.mgdamg import MgdError
+    s = I.make_system(1, (1, 1))   # one cell: coarsest immediately
+    slv = gpu.Solver().setup_system(s, "amg")
+    x, it, rr, rc = slv.solve(torch.from_numpy(s.b))
+    assert it == 1 and rr <= 1e-12
+    s = I.make_system(1, (7, 5))
+    slv = gpu.Solver().setup_system(s, "schur1")
+    x, it, rr, rc = slv.solve(torch.zeros(s.n, dtype=torch.float64))
+    assert it == 0 and not x.any()
+    x, it, rr, rc = gpu.Solver(max_it=2).setup_system(s, "amg").solve(torch.from_numpy(s.b), tol=1e-14,
+                                                                        allow_noconv=True)
+    assert rc == 2 and it == 2
+    # invalid inputs are rejected before any kernel touches them
+    bad = s.col.copy()
+    r0 = s.rowptr[5]
+    bad[r0], bad[r0 + 1] = bad[r0 + 1], bad[r0]
+    with pytest.raises(MgdError) as e:
+        gpu.Solver().setup(s.G, s.N, torch.from_numpy(s.rowptr), torch.from_numpy(bad), torch.from_numpy(s.val),
+                           "amg")
+    assert e.value.code == 1
+    badv = s.val.copy()
+    d = [p for p in range(s.rowptr[3], s.rowptr[4]) if s.col[p] == 3][0]
+    badv[d] = -1.0
+    with pytest.raises(MgdError):
+        gpu.Solver().setup(s.G, s.N, torch.from_numpy(s.rowptr), torch.from_numpy(s.col), torch.from_numpy(badv),
+                           "amg")
+    badc = s.col.copy()
+    row = 2 * s.N   # first ion row: its coupling must sit in cell 0
+    p = [q for q in range(s.rowptr[row], s.rowptr[row + 1]) if s.col[q] // s.N == 1][0]
+    badc[p] = s.N + 1
+    badc_sorted = badc  # still sorted within the row (E block precedes the I block)
+    with pytest.raises(MgdError):
+        gpu.Solver().setup(s.G, s.N, torch.from_numpy(s.rowptr), torch.from_numpy(badc_sorted),
+                           torch.from_numpy(s.val), "bd")
+
+
+def test_solve_host_buffers(gpu, orc):
+    s = _system(CASES[0])
+    slv = gpu.Solver().setup_system(s, "schur2")
+    x, it, rr = slv.solve_host(s.b)
+    xd, itd, _, _ = slv.solve(torch.from_numpy(s.b))
+    assert it == itd and np.array_equal(x, xd.cpu().numpy())
+
+
+def test_adjoint_gradient(gpu, orc):
+    s = I.make_system(4, (12, 10), multigroup=True)
+    slv = gpu.Solver(keep_transpose=1).setup_system(s, "amg")
+    vals = torch.from_numpy(s.val).cuda().requires_grad_(True)
+    b = torch.from_numpy(s.b).cuda().requires_grad_(True)
+    x = gpu.mgd_solve(vals, b, slv, 1e-13)
+    loss = (x * x).sum()
+    loss.backward()
+    # oracle gradient
+    Ao = orc.csr_of_system(s)
+    M = orc.Block(Ao, s.G, s.N, "amg")
+    xo, *_ = orc.fgmres(Ao, s.b, M, tol=1e-14, maxit=2000)
+    lo, *_ = orc.fgmres(Ao, 2 * xo, M, tol=1e-14, maxit=2000, transpose=True)
+    go = orc.grad_vals(Ao, xo, lo)
+    gv = vals.grad.cpu().numpy()
+    assert np.linalg.norm(gv - go) <= 1e-8 * np.linalg.norm(go)
+    assert np.linalg.norm(b.grad.cpu().numpy() - lo) <= 1e-8 * np.linalg.norm(lo)
+    # central differences on relative perturbations of the values
+    rng = np.random.default_rng(0)
+    h = 1e-6
+    for _ in range(4):
+        d = rng.standard_normal(s.nnz)
+        d /= np.linalg.norm(d)
+        dv = torch.from_numpy(s.val * d).cuda()
+        lp = gpu.mgd_solve(vals.detach() + h * dv, b.detach(), slv, 1e-13)
+        lm = gpu.mgd_solve(vals.detach() - h * dv, b.detach(), slv, 1e-13)
+        fd = ((lp * lp).sum() - (lm * lm).sum()).item() / (2 * h)
+        an = (vals.grad * dv).sum().item()
+        assert fd == pytest.approx(an, rel=1e-5)
