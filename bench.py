@@ -135,7 +135,7 @@ def run_ours(args):
             dist.barrier()
 
     clocks = ClockSampler(local)
-    slv.profile(True)
+    slv.profile(1)            # bracket only the dominant level-0 kernels inside the timed region
     l0 = mgdamg.kernel_launches()
     barrier()
     torch.cuda.synchronize()
@@ -161,8 +161,11 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = t.item()
     n0, t0, by0 = slv.profile_read(0)    # level-0 smoothing + residual kernels (dominant)
-    n1, t1, by1 = slv.profile_read(1)    # every V-cycle kernel
-    slv.profile(False)
+    # V-cycle GB/s over every V-cycle kernel: one more (untimed) step with all V-cycle classes bracketed
+    slv.profile(0b11)
+    step()
+    n1, t1, by1 = slv.profile_read(1)
+    slv.profile(0)
     st = slv.stats()
     xg = x
     relres = rr
@@ -175,7 +178,7 @@ def run_ours(args):
     h_x = torch.zeros(sysm.n, dtype=torch.float64).pin_memory()
     d_rp, d_ci, d_va = torch.empty_like(rp), torch.empty_like(ci), torch.empty_like(va)
     e2e_ms = []
-    for k in range(max(2, args.steps // 2) + 1):
+    for k in range(0 if args.no_e2e else max(2, args.steps // 2) + 1):
         torch.cuda.synchronize()
         t_a = time.perf_counter()
         d_rp.copy_(h_rp, non_blocking=True)
@@ -247,7 +250,8 @@ def run_ours(args):
                      "achieved": round(ach, 1) if ach else None, "peak": peak, "unit": "GB/s",
                      "frac": round(ach / peak, 4) if ach else None, "traffic": traffic,
                      "peak_source": peak_kind, "launches": n0, "ms": round(t0, 4)},
-        "e2e": {"value": round(statistics.median(e2e_ms) / 1e3, 6), "unit": "s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": round(statistics.median(e2e_ms) / 1e3, 6) if e2e_ms else None, "unit": "s",
+                "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
@@ -364,6 +368,7 @@ def main():
     ap.add_argument("--full-iters", type=int, default=None)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -165,14 +165,17 @@ int mgd_block_vector(mgd_ctx *c, int which, int comp, int comp2, double *h_out);
 /* 1 if coupling D_{a,b} was dropped by the Section 3.6 rule. */
 int mgd_coupling_dropped(mgd_ctx *c, int a, int b);
 
-/* Kernel timing for the roofline: when enabled, CUDA events bracket every
- * launch of the tracked kernel classes on the context's stream.  The read
- * call synchronises the stream and returns, per class, the launch count, the
- * summed device time and the summed algorithmic bytes (classes: 0 = level-0
- * smoothing+residual kernels of the V-cycle, 1 = all V-cycle kernels, 2 = the
- * FGMRES operator SpMV, 3 = Arnoldi vector kernels).  Enabling also turns
- * off graph replay so that each launch is bracketed. */
-int mgd_profile_enable(mgd_ctx *c, int on);
+/* Kernel timing for the roofline: CUDA events bracket every launch of the
+ * kernel classes selected by the bit mask (bit k = class k; 0 turns timing
+ * off, -1 selects all) on the context's stream.  Classes: 0 = level-0
+ * smoothing+residual kernels of the V-cycle, 1 = the other V-cycle kernels,
+ * 2 = the FGMRES operator SpMV and residual, 3 = Arnoldi vector kernels,
+ * 4 = block-level updates of the block preconditioners.  The read call
+ * synchronises the stream and returns, for class cls (cls = 1 also counts
+ * class 0, i.e. every V-cycle kernel), the launch count, the summed device
+ * time and the summed algorithmic bytes.  While timing is on, graph replay is
+ * off so that each launch is bracketed. */
+int mgd_profile_enable(mgd_ctx *c, int mask);
 int mgd_profile_read(mgd_ctx *c, int cls, long long *launches, double *ms, double *bytes);
 
 /* Kernels this library has launched in the calling process so far (a graph

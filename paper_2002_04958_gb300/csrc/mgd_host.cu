@@ -25,6 +25,7 @@ enum OpKind { OP_A = 0, OP_CE = 1, OP_CG = 2, OP_SG = 3, OP_SI = 4, OP_AC = 5, O
 // ------------------------------------------------------------------ profiler
 struct Profiler {
   bool on = false;
+  unsigned mask = 0;  // classes to record
   struct Rec {
     int cls;
     cudaEvent_t a, b;
@@ -45,8 +46,8 @@ struct Profiler {
     recs.clear();
     used = 0;
   }
-  int begin(cudaStream_t s) {
-    if (!on) return -1;
+  int begin(cudaStream_t s, int cls) {
+    if (!on || !(mask & (1u << cls))) return -1;
     cudaEvent_t a = get();
     MGD_CUDA(cudaEventRecord(a, s));
     recs.push_back({-1, a, nullptr, 0.0});
@@ -434,20 +435,20 @@ static void run_vbatch(VBatch<T>& vb, bool trans, cudaStream_t s, Profiler& prof
   for (int l = 0; l < vb.depth; ++l) {
     auto& lp = plan[l];
     if (lp.ndown) {
-      int id = prof.begin(s);
+      int id = prof.begin(s, l == 0 ? 0 : 1);
       launch_phase<T>(PH_PRE, lp.fmtA, lp.fmtR, lp.d_down, lp.ndown, lp.maxn, s);
       prof.end(id, l == 0 ? 0 : 1, lp.bytes_pre, s);
-      id = prof.begin(s);
+      id = prof.begin(s, 1);
       launch_phase<T>(PH_RESTRICT, lp.fmtA, lp.fmtR, lp.d_down, lp.ndown, lp.maxnc, s);
       prof.end(id, 1, lp.bytes_restrict, s);
     }
     if (lp.nclu) {
-      int id = prof.begin(s);
+      int id = prof.begin(s, 1);
       launch_phase<T>(PH_COARSE, lp.fmtA, lp.fmtR, lp.d_clu, lp.nclu, lp.maxcn, s);
       prof.end(id, 1, lp.bytes_coarse, s);
     }
     if (lp.ncjac) {
-      int id = prof.begin(s);
+      int id = prof.begin(s, l == 0 ? 0 : 1);
       launch_phase<T>(PH_JAC1, lp.fmtA, lp.fmtR, lp.d_cjac, lp.ncjac, lp.maxcj, s);
       launch_phase<T>(PH_POST, lp.fmtA, lp.fmtR, lp.d_cjac, lp.ncjac, lp.maxcj, s);
       prof.end(id, l == 0 ? 0 : 1, lp.bytes_jac, s);
@@ -456,10 +457,10 @@ static void run_vbatch(VBatch<T>& vb, bool trans, cudaStream_t s, Profiler& prof
   for (int l = vb.depth - 2; l >= 0; --l) {
     auto& lp = plan[l];
     if (!lp.ndown) continue;
-    int id = prof.begin(s);
+    int id = prof.begin(s, 1);
     launch_phase<T>(PH_PROLONG, lp.fmtA, lp.fmtP, lp.d_down, lp.ndown, lp.maxn, s);
     prof.end(id, 1, lp.bytes_prolong, s);
-    id = prof.begin(s);
+    id = prof.begin(s, l == 0 ? 0 : 1);
     launch_phase<T>(PH_POST, lp.fmtA, lp.fmtP, lp.d_down, lp.ndown, lp.maxn, s);
     prof.end(id, l == 0 ? 0 : 1, lp.bytes_post, s);
   }
@@ -830,13 +831,13 @@ static void run_step(mgd_ctx* c, const Step& st, bool trans) {
   {
     switch (st.type) {
       case Step::PRODUCE: {
-        int id = c->prof.begin(c->s);
+        int id = c->prof.begin(c->s, 4);
         launch_produce<T>((const ProduceDesc<T>*)st.descs, st.nd, st.len, c->io, c->s);
         c->prof.end(id, 4, st.bytes, c->s);
         break;
       }
       case Step::CONSUME: {
-        int id = c->prof.begin(c->s);
+        int id = c->prof.begin(c->s, 4);
         launch_consume<T>((const ConsumeDesc<T>*)st.descs, st.nd, st.len, c->io, c->s);
         c->prof.end(id, 4, st.bytes, c->s);
         break;
@@ -845,7 +846,7 @@ static void run_step(mgd_ctx* c, const Step& st, bool trans) {
         run_invert<T>(c, st, trans);
         break;
       case Step::BLOCKRESID: {
-        int id = c->prof.begin(c->s);
+        int id = c->prof.begin(c->s, 4);
         launch_block_resid(c->N, c->bd.nc, (const int* const*)c->bd.d_brp, (const int* const*)c->bd.d_bci,
                            (const double* const*)c->bd.d_bv, (const double* const*)c->bd.d_dtab, c->io,
                            c->rfull, c->s);
@@ -1078,7 +1079,7 @@ template <typename T>
 static void run_program(mgd_ctx* c, bool trans) {
   for (const Step& st : c->steps) {
     if (st.type == Step::PRODUCE && st.batch == -2) {
-      int id = c->prof.begin(c->s);
+      int id = c->prof.begin(c->s, 4);
       k_zupdate<<<dim3(cdiv(st.len, kThreads), st.nd), kThreads, 0, c->s>>>(
           (const ProduceDesc<double>*)st.descs, st.len, c->io);
       MGD_LAUNCH_CHECK();
@@ -1583,7 +1584,7 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
     return std::sqrt(hp[200]);
   };
   auto spmv = [&](const double* in, double* out) {
-    int id = c->prof.begin(s);
+    int id = c->prof.begin(s, 2);
     launch_spmv_f64(c->fmtMono, n, A.rp, A.ci, A.v, AS.sptr, AS.ci, AS.v, in, out, s);
     c->prof.end(id, 2, sp_bytes(A.nnz, n, 8) + 16.0 * n, s);
   };
@@ -1600,7 +1601,7 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
   auto Hm = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
   int it = 0, status = MGD_ENOCONV;
   for (;;) {
-    int id = c->prof.begin(s);
+    int id = c->prof.begin(s, 2);
     launch_resid_f64(c->fmtMono, n, A.rp, A.ci, A.v, AS.sptr, AS.ci, AS.v, b, x, c->r, s);
     c->prof.end(id, 2, sp_bytes(A.nnz, n, 8) + 24.0 * n, s);
     double beta = norm(c->r);
@@ -1632,7 +1633,7 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
       ++it;
       spmv(zj, c->w);
       int nv = j + 1;
-      int aid = c->prof.begin(s);
+      int aid = c->prof.begin(s, 3);
       launch_mdot(n, c->V, n, nv, c->w, c->partial, c->hbuf, s);
       launch_vupdate(n, c->V, n, nv, c->hbuf, c->w, c->partial, c->hbuf + 64, s);
       launch_mdot(n, c->V, n, nv, c->w, c->partial, c->hbuf + 32, s);
@@ -1927,9 +1928,10 @@ int mgd_coupling_dropped(mgd_ctx* c, int a, int b) {
   return c->bd.dropped[a * nc + b];
 }
 
-int mgd_profile_enable(mgd_ctx* c, int on) {
+int mgd_profile_enable(mgd_ctx* c, int mask) {
   if (!c) return MGD_EINVAL;
-  c->prof.on = on != 0;
+  c->prof.on = mask != 0;
+  c->prof.mask = (unsigned)mask;
   c->prof.reset();
   return MGD_OK;
 }

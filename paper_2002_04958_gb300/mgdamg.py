@@ -261,8 +261,9 @@ class Solver:
     def coupling_dropped(self, a, b):
         return bool(lib().mgd_coupling_dropped(self.h, a, b))
 
-    def profile(self, on=True):
-        self._check(lib().mgd_profile_enable(self.h, int(on)))
+    def profile(self, mask=-1):
+        """mask: bit k records kernel class k (0 off, -1 all)."""
+        self._check(lib().mgd_profile_enable(self.h, int(mask)))
 
     def profile_read(self, cls):
         nl, ms, by = C.c_longlong(), C.c_double(), C.c_double()
