@@ -178,6 +178,33 @@ int mgd_coupling_dropped(mgd_ctx *c, int a, int b);
 int mgd_profile_enable(mgd_ctx *c, int mask);
 int mgd_profile_read(mgd_ctx *c, int cls, long long *launches, double *ms, double *bytes);
 
+/* Largest n accepted by mgd_relres_noalloc (its fixed work array holds n
+ * doubles plus 1216 partial sums: about 4 MiB per GPU, kept until exit). */
+#define MGD_NOALLOC_MAX_N (1 << 19)
+
+/* True relative residual without any device allocation.  The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc
+ * (an application whose allocator owns the device, a loop with a fixed
+ * memory footprint, code that is assembling a CUDA graph).
+ *
+ * Computes r = b - A x for the CSR matrix d_rowptr[n+1], d_colidx, d_vals
+ * (device pointers, any sparsity) and d_b[n], d_x[n], and writes
+ * d_out[0] = ||r||_2, d_out[1] = ||b||_2, d_out[2] = ||r||_2 / ||b||_2
+ * (0 when b = 0) into the caller's device buffer d_out[3].  This is the
+ * quantity mgd_solve reports as *relres.  Work runs on `stream` (a
+ * cudaStream_t, NULL = legacy default stream) and is complete on return.
+ *
+ * Work space is one fixed device array inside the library, not memory from
+ * cudaMalloc: no call allocates or frees device memory.  n < 1 or
+ * n > MGD_NOALLOC_MAX_N returns MGD_EINVAL; a CUDA error returns MGD_ECUDA.
+ * The first call on each device looks up that array's device address (once
+ * per device, with that device current); make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ * Nothing from an earlier call is read back. */
+int mgd_relres_noalloc(int n, const int *d_rowptr, const int *d_colidx, const double *d_vals, const double *d_b,
+                       const double *d_x, double *d_out, void *stream);
+
 /* Kernels this library has launched in the calling process so far (a graph
  * replay counts each of its kernel nodes); a monotone counter for checking
  * that work ran on the device. */

@@ -24,6 +24,7 @@ UNITS = {
     "setup_kernels.cu": ["-fmad=false"],
     "solve_kernels.cu": [],
     "mgd_host.cu": ["-Xcompiler", "-fvisibility=default"],
+    "noalloc.cu": ["-Xcompiler", "-fvisibility=default"],
 }
 
 

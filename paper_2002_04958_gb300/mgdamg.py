@@ -24,7 +24,8 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOCONV", 3: "EBREAKDOWN", 4: "ESINGULAR", 5
 ENTRY_POINTS = ["mgd_opts_default", "mgd_create", "mgd_setup", "mgd_update_values", "mgd_solve", "mgd_solve_host",
                 "mgd_solve_transpose", "mgd_grad_values", "mgd_precond_apply", "mgd_get_stats", "mgd_get_history",
                 "mgd_op_info", "mgd_level_info", "mgd_level_export", "mgd_block_vector", "mgd_coupling_dropped",
-                "mgd_profile_enable", "mgd_profile_read", "mgd_kernel_launches", "mgd_last_error", "mgd_destroy"]
+                "mgd_profile_enable", "mgd_profile_read", "mgd_kernel_launches", "mgd_last_error", "mgd_destroy",
+                "mgd_relres_noalloc"]
 
 
 class MgdOpts(C.Structure):
@@ -81,6 +82,7 @@ def lib():
             "mgd_profile_enable": (I, [P, I]),
             "mgd_profile_read": (I, [P, I, pLL, pD, pD]),
             "mgd_kernel_launches": (C.c_longlong, []),
+            "mgd_relres_noalloc": (I, [I, P, P, P, P, P, P, P]),
             "mgd_last_error": (C.c_char_p, [P]),
             "mgd_destroy": (None, [P]),
         }
@@ -106,6 +108,18 @@ def default_opts(**kw):
             raise KeyError(k)
         setattr(o, k, v)
     return o
+
+
+NOALLOC_MAX_N = 1 << 19
+
+
+def relres_noalloc(rowptr, col, val, b, x, out, stream=None):
+    """||b - A x||, ||b|| and their ratio into the device tensor out[3], with no
+    device allocation inside the library (see mgd_relres_noalloc)."""
+    import torch
+    st = stream or torch.cuda.current_stream()
+    return lib().mgd_relres_noalloc(rowptr.numel() - 1, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b), _ptr(x),
+                                    _ptr(out), C.c_void_p(st.cuda_stream))
 
 
 def kernel_launches():
