@@ -54,12 +54,15 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, enabled=True):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.idx = gpu_index
         self.p = None
+        self.enabled = enabled
 
     def start(self):
+        if not self.enabled:
+            return
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
@@ -117,12 +120,18 @@ def run_ours(args):
     ci = torch.from_numpy(sysm.col).to(dev)
     va = torch.from_numpy(sysm.val).to(dev)
     b = torch.from_numpy(sysm.b).to(dev)
-    opts = dict(precision=args.precision, batched=args.batched, use_graph=args.graph, autotune=1)
+    opts = dict(precision=args.precision, batched=args.batched, use_graph=args.graph, autotune=1,
+                keep_transpose=int(args.adjoint), max_it=args.max_it)
     slv = mgdamg.Solver(**opts)
+    adj = {}
 
     def step():
         slv.setup(sysm.G, sysm.N, rp, ci, va, args.kind)
         x, it, rr, rc = slv.solve(b, tol=args.tol)
+        if args.adjoint:   # L = ||x||^2: lambda = A^-T (2x), dL/dvals = -lambda_row x_col
+            lam, ita, rra = slv.solve_transpose(2.0 * x, tol=args.tol)
+            g = slv.grad_values(x, lam)
+            adj.update(iters_transpose=ita, relres_transpose=rra)
         return x, it, rr
 
     for _ in range(args.warmup):
@@ -134,7 +143,7 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, enabled=not args.no_clocks)
     slv.profile(1)            # bracket only the dominant level-0 kernels inside the timed region
     l0 = mgdamg.kernel_launches()
     barrier()
@@ -196,8 +205,8 @@ def run_ours(args):
     # variants for context (one solve each, outside the timed region)
     variants = {}
     if not args.no_variants:
-        for name, kind, o in [("monolithic_amg_fp64", "amg", dict()),
-                              (f"{args.kind}_fp32_vcycle", args.kind, dict(precision=1)),
+        for name, kind, o in [("monolithic_amg_fp64", "amg", dict(batched=1, use_graph=1)),
+                              (f"{args.kind}_fp64_plain_launches", args.kind, dict()),
                               (f"{args.kind}_fp32_vcycle_batched_graph", args.kind,
                                dict(precision=1, batched=1, use_graph=1))]:
             try:
@@ -240,6 +249,8 @@ def run_ours(args):
                    "G": sysm.G, "grid": list(sysm.dims), "n": sysm.n, "nnz": sysm.nnz,
                    "precond": args.kind, "krylov": "FGMRES(30), right preconditioned", "tol": args.tol,
                    "step": "device setup + solve", "parallelism": f"replicas{ws}",
+                   "launch": ("batched per-level launches" if args.batched else "per-operator launches") +
+                             (", preconditioner replayed from a CUDA graph" if args.graph else ""),
                    "l2": "inputs larger than L2 (operator 201 MB), no flush"},
         "iters": iters[-1],
         "final_relres": relres,
@@ -258,6 +269,9 @@ def run_ours(args):
         "stats": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()},
         "variants": variants,
     }
+    if args.adjoint:
+        out["adjoint"] = adj
+        out["config"]["step"] = "device setup + solve + transposed solve + value gradient"
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, sysm, iters[-1])
     if rank == 0:
@@ -360,8 +374,8 @@ def main():
     ap.add_argument("--config", type=int, default=WORKLOAD)
     ap.add_argument("--kind", default=KIND)
     ap.add_argument("--precision", type=int, default=0)
-    ap.add_argument("--batched", type=int, default=0)
-    ap.add_argument("--graph", type=int, default=0)
+    ap.add_argument("--batched", type=int, default=1)
+    ap.add_argument("--graph", type=int, default=1)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--cpu-iters", type=int, default=30)
     ap.add_argument("--ref-iters", type=int, default=4)
@@ -369,6 +383,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--adjoint", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true", help="no nvidia-smi sampling (profiler runs)")
+    ap.add_argument("--max-it", type=int, default=1000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -173,8 +173,10 @@ int mgd_coupling_dropped(mgd_ctx *c, int a, int b);
  * 4 = block-level updates of the block preconditioners.  The read call
  * synchronises the stream and returns, for class cls (cls = 1 also counts
  * class 0, i.e. every V-cycle kernel), the launch count, the summed device
- * time and the summed algorithmic bytes.  While timing is on, graph replay is
- * off so that each launch is bracketed. */
+ * time and the summed algorithmic bytes.  With opts.use_graph the selected
+ * kernels are bracketed by event nodes inside the captured graph (the graph is
+ * captured again when the mask changes), so timing does not change how the
+ * preconditioner is launched. */
 int mgd_profile_enable(mgd_ctx *c, int mask);
 int mgd_profile_read(mgd_ctx *c, int cls, long long *launches, double *ms, double *bytes);
 

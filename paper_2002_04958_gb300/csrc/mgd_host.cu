@@ -23,45 +23,104 @@ long long g_kernel_launches = 0;
 enum OpKind { OP_A = 0, OP_CE = 1, OP_CG = 2, OP_SG = 3, OP_SI = 4, OP_AC = 5, OP_MONO = 6 };
 
 // ------------------------------------------------------------------ profiler
+// CUDA-event timing of selected kernel classes.  Stream launches are
+// bracketed by events recorded on the stream; launches inside a captured graph
+// are bracketed by event-record nodes of that graph.  Pending events are
+// harvested (converted to durations) at the solver's host synchronisation
+// points, so a graph replayed once per FGMRES iteration is timed every time.
 struct Profiler {
   bool on = false;
-  unsigned mask = 0;  // classes to record
-  struct Rec {
+  unsigned mask = 0;       // classes to record
+  bool capturing = false;  // inside stream capture: record graph event nodes
+  struct Pair {
     int cls;
     cudaEvent_t a, b;
     double bytes;
   };
-  std::vector<Rec> recs;
+  std::vector<Pair> pending, graph_pairs;
+  bool graph_replayed = false;
   std::vector<cudaEvent_t> pool;
-  size_t used = 0;
+  long long n[8] = {0};
+  double ms[8] = {0}, bytes[8] = {0};
   cudaEvent_t get() {
-    if (used < pool.size()) return pool[used++];
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
     cudaEvent_t e;
     MGD_CUDA(cudaEventCreate(&e));
-    pool.push_back(e);
-    ++used;
     return e;
   }
-  void reset() {
-    recs.clear();
-    used = 0;
+  void record(cudaEvent_t e, cudaStream_t s) {
+    if (capturing) MGD_CUDA(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+    else MGD_CUDA(cudaEventRecord(e, s));
   }
   int begin(cudaStream_t s, int cls) {
     if (!on || !(mask & (1u << cls))) return -1;
     cudaEvent_t a = get();
-    MGD_CUDA(cudaEventRecord(a, s));
-    recs.push_back({-1, a, nullptr, 0.0});
-    return (int)recs.size() - 1;
+    record(a, s);
+    auto& v = capturing ? graph_pairs : pending;
+    v.push_back({cls, a, nullptr, 0.0});
+    return (int)v.size() - 1;
   }
-  void end(int id, int cls, double bytes, cudaStream_t s) {
+  void end(int id, int cls, double by, cudaStream_t s) {
     if (id < 0) return;
     cudaEvent_t b = get();
-    MGD_CUDA(cudaEventRecord(b, s));
-    recs[id].cls = cls;
-    recs[id].b = b;
-    recs[id].bytes = bytes;
+    record(b, s);
+    auto& v = capturing ? graph_pairs : pending;
+    v[id].cls = cls;
+    v[id].b = b;
+    v[id].bytes = by;
+  }
+  void add(const Pair& p) {
+    float e = 0;
+    MGD_CUDA(cudaEventElapsedTime(&e, p.a, p.b));
+    n[p.cls]++;
+    ms[p.cls] += e;
+    bytes[p.cls] += p.bytes;
+  }
+  // call after the stream has been synchronised
+  void harvest() {
+    for (auto& p : pending) {
+      if (p.b) add(p);
+      pool.push_back(p.a);
+      if (p.b) pool.push_back(p.b);
+    }
+    pending.clear();
+    if (graph_replayed)
+      for (auto& p : graph_pairs)
+        if (p.b) add(p);
+    graph_replayed = false;
+  }
+  void drop_graph_pairs() {
+    for (auto& p : graph_pairs) {
+      pool.push_back(p.a);
+      if (p.b) pool.push_back(p.b);
+    }
+    graph_pairs.clear();
+  }
+  void reset() {
+    for (auto& p : pending) {
+      pool.push_back(p.a);
+      if (p.b) pool.push_back(p.b);
+    }
+    pending.clear();
+    graph_replayed = false;
+    for (int k = 0; k < 8; ++k) {
+      n[k] = 0;
+      ms[k] = bytes[k] = 0;
+    }
   }
   ~Profiler() {
+    for (auto& p : pending) {
+      cudaEventDestroy(p.a);
+      if (p.b) cudaEventDestroy(p.b);
+    }
+    for (auto& p : graph_pairs) {
+      cudaEventDestroy(p.a);
+      if (p.b) cudaEventDestroy(p.b);
+    }
     for (auto e : pool) cudaEventDestroy(e);
   }
 };
@@ -75,6 +134,10 @@ struct Opts {
 struct Level {
   Csr A;
   float* v32 = nullptr;
+  double* vpre = nullptr;   // A D^-1 values (CSR order)
+  float* vpre32 = nullptr;
+  double* atvpre = nullptr; // A^T D^-1 values
+  float* atvpre32 = nullptr;
   Sell sell;
   double* dinv = nullptr;
   float* dinv32 = nullptr;
@@ -269,7 +332,13 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
     lv.dinv = ar.alloc<double>(n);
     launch_l1_dinv(n, lv.A.rp, lv.A.v, lv.dinv, s);
     lv.sell = build_sell(ar, lv.A, sc.mixed, s);
+    lv.vpre = ar.alloc<double>(lv.A.nnz);
+    launch_colscale(lv.A.nnz, lv.A.ci, lv.A.v, lv.dinv, lv.vpre, s);
+    lv.sell.vpre = ar.alloc<double>(lv.sell.nstored);
+    launch_colscale(lv.sell.nstored, lv.sell.ci, lv.sell.v, lv.dinv, lv.sell.vpre, s);
     if (sc.mixed) {
+      lv.vpre32 = cast32(ar, lv.vpre, lv.A.nnz, s);
+      lv.sell.vpre32 = cast32(ar, lv.sell.vpre, (int)lv.sell.nstored, s);
       lv.v32 = cast32(ar, lv.A.v, lv.A.nnz, s);
       lv.dinv32 = cast32(ar, lv.dinv, n, s);
       if (l < h.nlev() - 1) {
@@ -280,7 +349,15 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
     if (sc.keepT) {
       lv.AT = transpose(ar, lv.A, s);
       lv.sellT = build_sell(ar, lv.AT, sc.mixed, s);
-      if (sc.mixed) lv.atv32 = cast32(ar, lv.AT.v, lv.AT.nnz, s);
+      lv.atvpre = ar.alloc<double>(lv.AT.nnz);
+      launch_colscale(lv.AT.nnz, lv.AT.ci, lv.AT.v, lv.dinv, lv.atvpre, s);
+      lv.sellT.vpre = ar.alloc<double>(lv.sellT.nstored);
+      launch_colscale(lv.sellT.nstored, lv.sellT.ci, lv.sellT.v, lv.dinv, lv.sellT.vpre, s);
+      if (sc.mixed) {
+        lv.atv32 = cast32(ar, lv.AT.v, lv.AT.nnz, s);
+        lv.atvpre32 = cast32(ar, lv.atvpre, lv.AT.nnz, s);
+        lv.sellT.vpre32 = cast32(ar, lv.sellT.vpre, (int)lv.sellT.nstored, s);
+      }
     }
     size_t es = sc.mixed ? sizeof(float) : sizeof(double);
     lv.b = ar.alloc<char>(es * n);
@@ -355,6 +432,8 @@ static LDesc<T> make_desc(Hier& h, int l, bool trans) {
   d.sptr = S.sptr;
   d.sci = S.ci;
   d.sv = pick<T>(S.v, S.v32);
+  d.vpre = trans ? pick<T>(lv.atvpre, lv.atvpre32) : pick<T>(lv.vpre, lv.vpre32);
+  d.svpre = pick<T>(S.vpre, S.vpre32);
   d.dinv = pick<T>(lv.dinv, lv.dinv32);
   if (l < h.nlev() - 1) {
     d.prp = lv.P.rp;
@@ -477,8 +556,9 @@ static void autotune(VBatch<T>& vb, bool trans, cudaStream_t s) {
   MGD_CUDA(cudaEventCreate(&e1));
   auto time_it = [&](auto fn) {
     fn();
+    fn();
     MGD_CUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3; ++r) fn();
+    for (int r = 0; r < 6; ++r) fn();
     MGD_CUDA(cudaEventRecord(e1, s));
     MGD_CUDA(cudaEventSynchronize(e1));
     float ms = 0;
@@ -594,7 +674,7 @@ struct mgd_ctx {
   mgd::Profiler prof;
   cudaGraphExec_t graph = nullptr;
   bool graph_ok = false;
-  long long graph_nodes = 0;
+  long long graph_kernels = 0;
   mgd_stats st;
   int n_jacobi = 0;
 };
@@ -1172,9 +1252,10 @@ static int guarded(mgd_ctx* c, F&& f) {
 
 static void precond_apply(mgd_ctx* c, const double* v, double* z, bool trans) {
   launch_set_io(c->io, v, z, c->s);
-  if (!trans && c->graph_ok && !c->prof.on) {
+  if (!trans && c->graph_ok) {
     MGD_CUDA(cudaGraphLaunch(c->graph, c->s));
-    __atomic_add_fetch(&g_kernel_launches, c->graph_nodes, __ATOMIC_RELAXED);
+    __atomic_add_fetch(&g_kernel_launches, c->graph_kernels, __ATOMIC_RELAXED);
+    c->prof.graph_replayed = true;
     return;
   }
   if (mixed(c)) run_program<float>(c, trans);
@@ -1189,22 +1270,24 @@ static void capture_graph(mgd_ctx* c) {
   c->graph_ok = false;
   if (!c->o.use_graph) return;
   cudaGraph_t g;
-  bool prof_on = c->prof.on;
-  c->prof.on = false;
+  c->prof.drop_graph_pairs();
+  long long k0 = __atomic_load_n(&g_kernel_launches, __ATOMIC_RELAXED);
+  c->prof.capturing = true;
   MGD_CUDA(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
   try {
     if (mixed(c)) run_program<float>(c, false);
     else run_program<double>(c, false);
   } catch (...) {
     cudaStreamEndCapture(c->s, &g);
-    c->prof.on = prof_on;
+    c->prof.capturing = false;
     throw;
   }
-  c->prof.on = prof_on;
+  c->prof.capturing = false;
   MGD_CUDA(cudaStreamEndCapture(c->s, &g));
-  size_t nn = 0;
-  MGD_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
-  c->graph_nodes = (long long)nn;
+  // kernels recorded into the graph (the counter counted them at capture)
+  long long k1 = __atomic_load_n(&g_kernel_launches, __ATOMIC_RELAXED);
+  c->graph_kernels = k1 - k0;
+  __atomic_sub_fetch(&g_kernel_launches, c->graph_kernels, __ATOMIC_RELAXED);
   MGD_CUDA(cudaGraphInstantiate(&c->graph, g, 0));
   cudaGraphDestroy(g);
   c->graph_ok = true;
@@ -1505,7 +1588,7 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
     for (int f : {FMT_SELL, FMT_CSR1, FMT_CSR2, FMT_CSR4, FMT_CSR8}) {
       launch_spmv_f64(f, n, c->A.rp, c->A.ci, c->A.v, c->Asell.sptr, c->Asell.ci, c->Asell.v, c->r, c->w, s);
       MGD_CUDA(cudaEventRecord(e0, s));
-      for (int k = 0; k < 3; ++k)
+      for (int k = 0; k < 6; ++k)
         launch_spmv_f64(f, n, c->A.rp, c->A.ci, c->A.v, c->Asell.sptr, c->Asell.ci, c->Asell.v, c->r, c->w, s);
       MGD_CUDA(cudaEventRecord(e1, s));
       MGD_CUDA(cudaEventSynchronize(e1));
@@ -1581,6 +1664,7 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
     launch_norm2(n, v, c->partial, c->hbuf + 96, s);
     MGD_CUDA(cudaMemcpyAsync(hp + 200, c->hbuf + 96, sizeof(double), cudaMemcpyDeviceToHost, s));
     MGD_CUDA(cudaStreamSynchronize(s));
+    c->prof.harvest();
     return std::sqrt(hp[200]);
   };
   auto spmv = [&](const double* in, double* out) {
@@ -1634,15 +1718,19 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
       spmv(zj, c->w);
       int nv = j + 1;
       int aid = c->prof.begin(s, 3);
-      launch_mdot(n, c->V, n, nv, c->w, c->partial, c->hbuf, s);
-      launch_vupdate(n, c->V, n, nv, c->hbuf, c->w, c->partial, c->hbuf + 64, s);
-      launch_mdot(n, c->V, n, nv, c->w, c->partial, c->hbuf + 32, s);
-      launch_vupdate(n, c->V, n, nv, c->hbuf + 32, c->w, c->partial, c->hbuf + 64, s);
+      // pass 1: h1 = V^T w and ||w||^2 (slot nv); w -= V h1 -> ||w'||^2 in hbuf[65]
+      launch_mdot(n, c->V, n, nv, c->w, c->partial, c->hbuf, s, 1);
+      launch_vupdate(n, c->V, n, nv, c->hbuf, c->w, c->partial, c->hbuf + 65, s);
+      // pass 2 only if ||w'||^2 < ||w||^2 / 2 (decided on the device)
+      launch_mdot(n, c->V, n, nv, c->w, c->partial, c->hbuf + 32, s, 0, c->hbuf + 65, c->hbuf + nv);
+      launch_vupdate(n, c->V, n, nv, c->hbuf + 32, c->w, c->partial, c->hbuf + 64, s, c->hbuf + 65, c->hbuf + nv);
       launch_scale_by_norm(n, c->w, c->hbuf + 64, c->V + (size_t)(j + 1) * n, s);
       c->prof.end(aid, 3, 8.0 * n * (2.0 * (nv + 1) + 2.0 * (nv + 2) + 2.0), s);
-      MGD_CUDA(cudaMemcpyAsync(hp, c->hbuf, 65 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      MGD_CUDA(cudaMemcpyAsync(hp, c->hbuf, 66 * sizeof(double), cudaMemcpyDeviceToHost, s));
       MGD_CUDA(cudaStreamSynchronize(s));
-      for (int i = 0; i <= j; ++i) Hm(i, j) = hp[i] + hp[32 + i];
+      c->prof.harvest();
+      // second-pass coefficients are zero when the pass was skipped
+      for (int i = 0; i <= j; ++i) Hm(i, j) = hp[i] + (hp[65] < 0.5 * hp[nv] ? hp[32 + i] : 0.0);
       double hn = std::sqrt(hp[64]);
       Hm(j + 1, j) = hn;
       for (int i = 0; i < j; ++i) {
@@ -1839,6 +1927,7 @@ int mgd_precond_apply(mgd_ctx* c, const double* d_v, double* d_z) {
     if (!d_v || !d_z) throw Error{MGD_EINVAL, "invalid arguments"};
     precond_apply(c, d_v, d_z, false);
     MGD_CUDA(cudaStreamSynchronize(c->s));
+    c->prof.harvest();
     return MGD_OK;
   });
 }
@@ -1929,26 +2018,30 @@ int mgd_coupling_dropped(mgd_ctx* c, int a, int b) {
 }
 
 int mgd_profile_enable(mgd_ctx* c, int mask) {
-  if (!c) return MGD_EINVAL;
-  c->prof.on = mask != 0;
-  c->prof.mask = (unsigned)mask;
-  c->prof.reset();
-  return MGD_OK;
+  return guarded(c, [&]() -> int {
+    MGD_CUDA(cudaStreamSynchronize(c->s));
+    c->prof.harvest();
+    bool changed = c->prof.mask != (unsigned)mask;
+    c->prof.on = mask != 0;
+    c->prof.mask = (unsigned)mask;
+    c->prof.reset();
+    // the captured graph carries its own event nodes: re-capture for the new mask
+    if (changed && c->ready && c->o.use_graph) capture_graph(c);
+    return MGD_OK;
+  });
 }
 
 int mgd_profile_read(mgd_ctx* c, int cls, long long* launches, double* ms, double* bytes) {
   return guarded(c, [&]() -> int {
+    if (cls < 0 || cls > 7) throw Error{MGD_EINVAL, "bad class"};
     MGD_CUDA(cudaStreamSynchronize(c->s));
-    long long nl = 0;
-    double t = 0, by = 0;
-    for (auto& r : c->prof.recs) {
-      bool match = (r.cls == cls) || (cls == 1 && r.cls == 0);
-      if (!match || !r.b) continue;
-      float e = 0;
-      MGD_CUDA(cudaEventElapsedTime(&e, r.a, r.b));
-      ++nl;
-      t += e;
-      by += r.bytes;
+    c->prof.harvest();
+    long long nl = c->prof.n[cls];
+    double t = c->prof.ms[cls], by = c->prof.bytes[cls];
+    if (cls == 1) {  // every V-cycle kernel
+      nl += c->prof.n[0];
+      t += c->prof.ms[0];
+      by += c->prof.bytes[0];
     }
     if (launches) *launches = nl;
     if (ms) *ms = t;

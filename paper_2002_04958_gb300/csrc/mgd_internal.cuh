@@ -101,6 +101,8 @@ struct Sell {  // sliced ELL, slice height 32, column-major inside a slice
   int* ci = nullptr;
   double* v = nullptr;
   float* v32 = nullptr;
+  double* vpre = nullptr;   // values scaled by the column's l1 inverse
+  float* vpre32 = nullptr;
 };
 
 // Per-level device view used by the V-cycle kernels (T = double or float).
@@ -115,6 +117,10 @@ struct LDesc {
   const int* sci;
   const T* sv;
   const T* dinv;
+  // A D^-1 (columns scaled by the smoother diagonal): the pre-smoothing
+  // residual b - A D^-1 b then costs one multiply-add per nonzero
+  const T* vpre;
+  const T* svpre;
   // prolongation P (n x nc) and restriction R = P^T (nc x n), CSR
   const int* prp;
   const int* pci;
@@ -222,6 +228,7 @@ void launch_pctl_ac_fill(int N, int nc, int G, const int* const* brp, const int*
 void launch_sell_widths(int n, const int* rp, int* w, cudaStream_t s);
 void launch_sell_fill(int n, const int* rp, const int* ci, const double* v, const int* sptr, int* sci, double* sv,
                       cudaStream_t s);
+void launch_colscale(long long nnz, const int* ci, const double* v, const double* d, double* out, cudaStream_t s);
 void launch_grad_vals(int n, const int* rp, const int* ci, const double* x, const double* lam, double* g,
                       cudaStream_t s);
 void launch_offsets64(const int* cnt, long long* off, int n, cudaStream_t s);
@@ -256,10 +263,15 @@ void launch_copy_f64(int n, const double* a, double* b, cudaStream_t s);
 
 // Arnoldi / vector kernels (FP64)
 constexpr int kDotBlocks = 608;  // 4 x 152 SMs
+// out[t] = <V_t, w> (t < nv), out[nv] = <w, w> with selfdot; skipped (zeros)
+// unless cond_after[0] < 0.5 cond_before[0] when cond_after is given
 void launch_mdot(int n, const double* V, long long ldv, int nv, const double* w, double* partial, double* out,
-                 cudaStream_t s);
+                 cudaStream_t s, int selfdot = 0, const double* cond_after = nullptr,
+                 const double* cond_before = nullptr);
+// w -= V h; nrm2 = ||w||^2 (same skip rule: then nrm2 = cond_after[0])
 void launch_vupdate(int n, const double* V, long long ldv, int nv, const double* h, double* w, double* partial,
-                    double* nrm2, cudaStream_t s);  // w -= V h; nrm2 = ||w||^2
+                    double* nrm2, cudaStream_t s, const double* cond_after = nullptr,
+                    const double* cond_before = nullptr);
 void launch_scale_by_norm(int n, const double* w, const double* nrm2, double* v, cudaStream_t s);
 void launch_vcomb(int n, const double* Z, long long ldz, int nv, const double* y, double* x, cudaStream_t s);
 void launch_norm2(int n, const double* x, double* partial, double* out, cudaStream_t s);

@@ -892,6 +892,18 @@ void launch_sell_fill(int n, const int* rp, const int* ci, const double* v, cons
   MGD_LAUNCH_CHECK();
 }
 
+// ------------------------------------------------------------------ column scaling A D^-1
+__global__ void k_colscale(long long nnz, const int* ci, const double* v, const double* d, double* out) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nnz) out[p] = __dmul_rn(v[p], d[ci[p]]);
+}
+
+void launch_colscale(long long nnz, const int* ci, const double* v, const double* d, double* out, cudaStream_t s) {
+  if (nnz <= 0) return;
+  k_colscale<<<cdiv(nnz, kThreads), kThreads, 0, s>>>(nnz, ci, v, d, out);
+  MGD_LAUNCH_CHECK();
+}
+
 // ------------------------------------------------------------------ adjoint gradient
 __global__ void k_grad_vals(int n, const int* rp, const int* ci, const double* x, const double* lam, double* g) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;

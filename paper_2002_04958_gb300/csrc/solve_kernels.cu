@@ -68,7 +68,8 @@ __device__ __forceinline__ T row_dot(int row, int lane, bool valid, const int* _
 }
 
 // ---------------------------------------------------------------- V-cycle phases
-// PRE: xt = D^-1 b (zero initial guess), r = b - A xt
+// PRE: xt = D^-1 b (zero initial guess), r = b - A xt = b - (A D^-1) b, using
+// the column-scaled copy of A so that each nonzero costs one multiply-add
 template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_pre(const LDesc<T>* __restrict__ descs) {
   const LDesc<T>* d = descs + blockIdx.y;
@@ -78,13 +79,12 @@ __global__ void __launch_bounds__(kThreads) k_pre(const LDesc<T>* __restrict__ d
   int n = d->n;
   if (((g & ~31) / TPR) >= n) return;  // the whole warp is past the last row (TPR divides 32)
   bool valid = row < n;
-  const T* dinv = d->dinv;
   const T* b = d->b;
-  XScaled<T> xf{dinv, b};
-  T s = row_dot<T, FMT>(row, lane, valid, d->rp, d->ci, d->v, d->sptr, d->sci, d->sv, xf);
+  XPlain<T> xf{b};
+  T s = row_dot<T, FMT>(row, lane, valid, d->rp, d->ci, d->vpre, d->sptr, d->sci, d->svpre, xf);
   if (valid && lane == 0) {
     T bi = b[row];
-    d->xt[row] = dinv[row] * bi;
+    d->xt[row] = d->dinv[row] * bi;
     d->r[row] = bi - s;
   }
 }
@@ -374,18 +374,35 @@ void launch_copy_f64(int n, const double* a, double* b, cudaStream_t s) {
 // ---------------------------------------------------------------- Arnoldi (FP64)
 constexpr int kMaxV = 32;
 
-// partial[b * kMaxV + t] = sum over this block's elements of V_t(i) w(i)
+// Classical Gram-Schmidt with a selective second pass (Daniel, Gragg, Kaufman,
+// Stewart 1976): the second projection runs only when the first one removed
+// more than half of ||w||^2, a test the kernels read from device memory
+// (cond_after < 0.5 cond_before), so no host round trip is needed.
+__device__ __forceinline__ bool second_pass_needed(const double* after, const double* before) {
+  return !after || after[0] < 0.5 * before[0];
+}
+
+// partial[b * kMaxV + t] = sum over this block's elements of V_t(i) w(i); with
+// selfdot, slot nv gets w.w.  Skipped (zeros) when cond says no second pass.
 template <int NV>
 __global__ void __launch_bounds__(kThreads) k_mdot(int n, const double* __restrict__ V, long long ldv, int nv,
-                                                   const double* __restrict__ w, double* __restrict__ partial) {
+                                                   const double* __restrict__ w, double* __restrict__ partial,
+                                                   int selfdot, const double* __restrict__ cond_after,
+                                                   const double* __restrict__ cond_before) {
+  if (!second_pass_needed(cond_after, cond_before)) {
+    for (int t = threadIdx.x; t < NV; t += blockDim.x) partial[(size_t)blockIdx.x * kMaxV + t] = 0.0;
+    return;
+  }
   double acc[NV];
 #pragma unroll
   for (int t = 0; t < NV; ++t) acc[t] = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     double wi = w[i];
 #pragma unroll
-    for (int t = 0; t < NV; ++t)
+    for (int t = 0; t < NV; ++t) {
       if (t < nv) acc[t] += V[t * ldv + i] * wi;
+      else if (t == nv && selfdot) acc[t] += wi * wi;
+    }
   }
   __shared__ double sh[kThreads / 32][NV];
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -423,22 +440,29 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, int nblock
 static int dot_blocks(int n) { return std::min(kDotBlocks, std::max(1, cdiv(n, kThreads))); }
 
 void launch_mdot(int n, const double* V, long long ldv, int nv, const double* w, double* partial, double* out,
-                 cudaStream_t s) {
+                 cudaStream_t s, int selfdot, const double* cond_after, const double* cond_before) {
   int nb = dot_blocks(n);
-  if (nv <= 4) k_mdot<4><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, w, partial);
-  else if (nv <= 8) k_mdot<8><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, w, partial);
-  else if (nv <= 16) k_mdot<16><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, w, partial);
-  else k_mdot<32><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, w, partial);
+  int nt = nv + (selfdot ? 1 : 0);
+  if (nt <= 4) k_mdot<4><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, w, partial, selfdot, cond_after, cond_before);
+  else if (nt <= 8) k_mdot<8><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, w, partial, selfdot, cond_after, cond_before);
+  else if (nt <= 16) k_mdot<16><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, w, partial, selfdot, cond_after, cond_before);
+  else k_mdot<32><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, w, partial, selfdot, cond_after, cond_before);
   MGD_LAUNCH_CHECK();
-  k_reduce_partials<<<nv, kThreads, 0, s>>>(partial, nb, nv, out);
+  k_reduce_partials<<<nt, kThreads, 0, s>>>(partial, nb, nt, out);
   MGD_LAUNCH_CHECK();
 }
 
-// w -= sum_t h_t V_t, and partial norms of the new w
+// w -= sum_t h_t V_t, and partial norms of the new w.  Skipped when cond says
+// no second pass: then the norm partials carry the first pass's ||w||^2.
 template <int NV>
 __global__ void __launch_bounds__(kThreads) k_vupdate(int n, const double* __restrict__ V, long long ldv, int nv,
                                                       const double* __restrict__ h, double* __restrict__ w,
-                                                      double* __restrict__ partial) {
+                                                      double* __restrict__ partial, const double* __restrict__ cond_after,
+                                                      const double* __restrict__ cond_before) {
+  if (!second_pass_needed(cond_after, cond_before)) {
+    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * kMaxV] = blockIdx.x == 0 ? cond_after[0] : 0.0;
+    return;
+  }
   __shared__ double sh_h[NV];
   for (int t = threadIdx.x; t < NV; t += blockDim.x) sh_h[t] = t < nv ? h[t] : 0.0;
   __syncthreads();
@@ -464,22 +488,29 @@ __global__ void __launch_bounds__(kThreads) k_vupdate(int n, const double* __res
 }
 
 void launch_vupdate(int n, const double* V, long long ldv, int nv, const double* h, double* w, double* partial,
-                    double* nrm2, cudaStream_t s) {
+                    double* nrm2, cudaStream_t s, const double* cond_after, const double* cond_before) {
   int nb = dot_blocks(n);
-  if (nv <= 4) k_vupdate<4><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, h, w, partial);
-  else if (nv <= 8) k_vupdate<8><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, h, w, partial);
-  else if (nv <= 16) k_vupdate<16><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, h, w, partial);
-  else k_vupdate<32><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, h, w, partial);
+  if (nv <= 4) k_vupdate<4><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, h, w, partial, cond_after, cond_before);
+  else if (nv <= 8) k_vupdate<8><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, h, w, partial, cond_after, cond_before);
+  else if (nv <= 16) k_vupdate<16><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, h, w, partial, cond_after, cond_before);
+  else k_vupdate<32><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, h, w, partial, cond_after, cond_before);
   MGD_LAUNCH_CHECK();
   k_reduce_partials<<<1, kThreads, 0, s>>>(partial, nb, 1, nrm2);
   MGD_LAUNCH_CHECK();
 }
 
+// v = w / ||w||: one reciprocal per block, a multiply per element (FP64
+// division is a long instruction sequence on this part)
 __global__ void k_scale_by_norm(int n, const double* __restrict__ w, const double* __restrict__ nrm2,
                                 double* __restrict__ v) {
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) {
+    double h = sqrt(*nrm2);
+    s_inv = h != 0.0 ? 1.0 / h : 0.0;
+  }
+  __syncthreads();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double h = sqrt(*nrm2);
-  if (i < n) v[i] = h != 0.0 ? w[i] / h : 0.0;
+  if (i < n) v[i] = w[i] * s_inv;
 }
 void launch_scale_by_norm(int n, const double* w, const double* nrm2, double* v, cudaStream_t s) {
   k_scale_by_norm<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, w, nrm2, v);

@@ -1,0 +1,79 @@
+"""Parity at the full workload sizes, in the launch configuration the bench
+uses (autotuned layouts): the C/F splittings, interpolation and coarse
+operators of every hierarchy bit-exact with the oracle, the FGMRES iteration
+count of the FP64 solve equal to the oracle's (config 2), the FP32-V-cycle
+count within +-1, and the true residual checked independently on the host."""
+import numpy as np
+import pytest
+
+from paper_2002_04958_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2002_04958_gb300 import mgdamg
+    return mgdamg
+
+
+def _compare_all_levels(slv, ob, orc, kind, max_level=None):
+    st = slv.stats()
+    checked = 0
+    for k in range(st["n_ops"]):
+        info = slv.op_info(k)
+        if info["use_jacobi"]:
+            continue
+        oh = ob.amg(orc.OP_MONO, 0) if kind == "amg" else ob.amg(info["kind"], info["comp"])
+        assert info["nlevels"] == oh.nlevels
+        L = oh.nlevels if max_level is None else min(oh.nlevels, max_level + 1)
+        for l in range(L):
+            g = slv.level(k, l)
+            rp, ci, v = oh.A(l).arrays()
+            assert np.array_equal(g["rp"], rp) and np.array_equal(g["ci"], ci) and np.array_equal(g["v"], v)
+            if l < oh.nlevels - 1:
+                assert np.array_equal(g["cf"], oh.CF(l))
+                prp, pci, pv = oh.P(l).arrays()
+                assert np.array_equal(g["prp"], prp) and np.array_equal(g["pci"], pci) and np.array_equal(g["pv"], pv)
+            checked += 1
+    return checked
+
+
+def test_config1_full_size_hierarchies_and_residual(gpu, orc):
+    s = I.preset(1)                      # 1024 x 1024, 3,145,728 unknowns
+    slv = gpu.Solver().setup_system(s, "schur1")
+    Ao = orc.csr_of_system(s)
+    ob = orc.Block(Ao, s.G, s.N, "schur1")
+    assert _compare_all_levels(slv, ob, orc, "schur1") >= 10
+    x, it, rr, rc = slv.solve(torch.from_numpy(s.b), tol=1e-8)
+    assert rc == 0
+    xg = x.cpu().numpy()
+    res = np.linalg.norm(s.b - s.scipy() @ xg) / np.linalg.norm(s.b)
+    assert res <= 1e-8 * (1 + 1e-6) and res == pytest.approx(rr, rel=1e-6)
+    # sampled rows of the preconditioner output against the oracle's full apply
+    v = np.random.default_rng(1).standard_normal(s.n)
+    z = slv.precond_apply(torch.from_numpy(v)).cpu().numpy()
+    zo = ob.apply(v)
+    assert np.linalg.norm(z - zo) <= 1e-11 * np.linalg.norm(zo)
+
+
+def test_config2_full_size_iterations(gpu, orc):
+    s = I.preset(2)                      # G = 20, 256 x 256, 1,441,792 unknowns
+    Ao = orc.csr_of_system(s)
+    ob = orc.Block(Ao, s.G, s.N, "bd")
+    slv = gpu.Solver(batched=1).setup_system(s, "bd")
+    assert _compare_all_levels(slv, ob, orc, "bd") >= 22
+    x, it, rr, rc = slv.solve(torch.from_numpy(s.b), tol=1e-8)
+    xo, ito, rro, sto, _ = orc.fgmres(Ao, s.b, ob, tol=1e-8)
+    assert rc == 0 and sto == 0 and it == ito
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
+    mixed = gpu.Solver(precision=1, batched=1, use_graph=1).setup_system(s, "bd")
+    xm, itm, rrm, rcm = mixed.solve(torch.from_numpy(s.b), tol=1e-8)
+    assert rcm == 0 and abs(itm - ito) <= 1
+    assert np.linalg.norm(s.b - s.scipy() @ xm.cpu().numpy()) <= 1.0000001e-8 * np.linalg.norm(s.b)
