@@ -286,16 +286,23 @@ def _traffic_from_profiles():
     summary, when it was taken from the current kernel source."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
-    src = os.path.join(ROOT, "paper_2002_04958_gb300", "csrc", "solve_kernels.cu")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    with open(src, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()
-    if d.get("solve_kernels_sha256") != h:
+    if d.get("kernel_source_sha256") != kernel_source_sha256():
         return None
     return d.get("traffic_bytes_per_launch")
+
+
+def kernel_source_sha256():
+    """Hash of the V-cycle kernel sources (the dominant kernels' code)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("vcycle_kernels.cu", "row_dot.cuh"):
+        with open(os.path.join(ROOT, "paper_2002_04958_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def cpu_baseline(args, sysm, gpu_iters):

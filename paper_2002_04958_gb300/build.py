@@ -23,6 +23,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
 UNITS = {
     "setup_kernels.cu": ["-fmad=false"],
     "solve_kernels.cu": [],
+    "vcycle_kernels.cu": [],
     "mgd_host.cu": ["-Xcompiler", "-fvisibility=default"],
     "noalloc.cu": ["-Xcompiler", "-fvisibility=default"],
 }

@@ -9,8 +9,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/mgdamg.h"
@@ -19,6 +21,8 @@
 namespace mgd {
 
 long long g_kernel_launches = 0;
+thread_local cudaMemPool_t tl_pool = nullptr;
+thread_local cudaStream_t tl_stream = nullptr;
 
 enum OpKind { OP_A = 0, OP_CE = 1, OP_CG = 2, OP_SG = 3, OP_SI = 4, OP_AC = 5, OP_MONO = 6 };
 
@@ -188,8 +192,9 @@ static Csr csr_copy(Arena& a, const Csr& x, cudaStream_t s) {
 }
 
 // C = X Y with the accumulation order of the Galerkin products (see setup_kernels.cu)
-static Csr spgemm(Arena& a, const Csr& X, const Csr& Y, cudaStream_t s) {
-  Scratch sc(s);
+// C = X Y; C's arrays come from `keep` when given (a scratch that outlives C), else from the arena
+static Csr spgemm(Arena& a, const Csr& X, const Csr& Y, cudaStream_t s, Scratch* keep = nullptr) {
+  Scratch sc(s, a.pool);
   int n = X.n;
   int* ub = sc.alloc<int>(n);
   launch_spgemm_ub(n, X.rp, X.ci, Y.rp, ub, s);
@@ -205,11 +210,11 @@ static Csr spgemm(Arena& a, const Csr& X, const Csr& Y, cudaStream_t s) {
   Csr C;
   C.n = n;
   C.m = Y.m;
-  C.rp = a.alloc<int>(n + 1);
+  C.rp = keep ? keep->alloc<int>(n + 1) : a.alloc<int>(n + 1, false, s);
   exclusive_scan(cnt, C.rp, n, s);
   C.nnz = read_int(C.rp + n, s);
-  C.ci = a.alloc<int>(C.nnz);
-  C.v = a.alloc<double>(C.nnz);
+  C.ci = keep ? keep->alloc<int>(C.nnz) : a.alloc<int>(C.nnz, false, s);
+  C.v = keep ? keep->alloc<double>(C.nnz) : a.alloc<double>(C.nnz, false, s);
   launch_spgemm_compact(n, off, tc, tv, C.rp, C.ci, C.v, s);
   return C;
 }
@@ -316,12 +321,9 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
     launch_interp_fill(n, lv.A.rp, lv.A.ci, lv.A.v, S, CF, cidx, P.rp, P.ci, P.v, s);
     lv.P = P;
     lv.R = transpose(ar, P, s);
-    Arena apa;
-    apa.stream = s;
-    Csr AP = spgemm(apa, lv.A, P, s);
+    Scratch apk(s, ar.pool);
+    Csr AP = spgemm(ar, lv.A, P, s, &apk);
     Csr Ac = spgemm(ar, lv.R, AP, s);
-    MGD_CUDA(cudaStreamSynchronize(s));
-    apa.release();
     h.L.emplace_back();
     h.L.back().A = Ac;
   }
@@ -401,6 +403,7 @@ struct VBatch {
     int ncjac = 0, maxcj = 0;
     int fmtA = FMT_SELL, fmtR = FMT_CSR4, fmtP = FMT_CSR1;
     double bytes_pre = 0, bytes_post = 0, bytes_restrict = 0, bytes_prolong = 0, bytes_coarse = 0, bytes_jac = 0;
+    double bytes_post_cj = 0;  // post-smoothing of the stalled coarsest levels
   };
   std::vector<LP> plan, planT;
   double bytes_total = 0;
@@ -488,7 +491,7 @@ static void build_plan(Arena& ar, VBatch<T>& vb, bool trans, cudaStream_t s) {
         cjac.push_back(d);
         lp.maxcj = std::max<int>(lp.maxcj, (int)n);
         lp.bytes_jac += 3.0 * sv * n;
-        lp.bytes_post += sp_bytes(nnz, n, sv) + 4.0 * sv * n;
+        lp.bytes_post_cj += sp_bytes(nnz, n, sv) + 4.0 * sv * n;
       }
     }
     auto upload = [&](std::vector<LDesc<T>>& v, LDesc<T>*& dst) {
@@ -502,7 +505,8 @@ static void build_plan(Arena& ar, VBatch<T>& vb, bool trans, cudaStream_t s) {
     lp.ndown = (int)down.size();
     lp.nclu = (int)clu.size();
     lp.ncjac = (int)cjac.size();
-    total += lp.bytes_pre + lp.bytes_post + lp.bytes_restrict + lp.bytes_prolong + lp.bytes_coarse + lp.bytes_jac;
+    total += lp.bytes_pre + lp.bytes_post + lp.bytes_restrict + lp.bytes_prolong + lp.bytes_coarse + lp.bytes_jac +
+             lp.bytes_post_cj;
   }
   if (!trans) vb.bytes_total = total;
   MGD_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope
@@ -530,7 +534,7 @@ static void run_vbatch(VBatch<T>& vb, bool trans, cudaStream_t s, Profiler& prof
       int id = prof.begin(s, l == 0 ? 0 : 1);
       launch_phase<T>(PH_JAC1, lp.fmtA, lp.fmtR, lp.d_cjac, lp.ncjac, lp.maxcj, s);
       launch_phase<T>(PH_POST, lp.fmtA, lp.fmtR, lp.d_cjac, lp.ncjac, lp.maxcj, s);
-      prof.end(id, l == 0 ? 0 : 1, lp.bytes_jac, s);
+      prof.end(id, l == 0 ? 0 : 1, lp.bytes_jac + lp.bytes_post_cj, s);
     }
   }
   for (int l = vb.depth - 2; l >= 0; --l) {
@@ -650,6 +654,7 @@ struct mgd_ctx {
   cudaStream_t s = nullptr;
   int device = 0;
   std::string err;
+  mgd::Pool pool;
   mgd::Arena ar;
   bool ready = false;
   int kind = 0, G = 0, N = 0, n = 0, nnz = 0;
@@ -757,38 +762,82 @@ static void push_invert(std::vector<Step>& steps, std::vector<int> ops) {
 
 // ------------------------------------------------------------------ inverse operators
 template <typename T>
-static void finalize_op(mgd_ctx* c, InvOp& op) {
+static void finalize_op(mgd_ctx* c, InvOp& op, cudaStream_t st) {
   const size_t es = sizeof(T);
   op.n = op.A.n;
   if (op.jacobi) {
     op.jd = c->ar.alloc<double>(op.n);
-    launch_diag_inv(op.n, op.A.rp, op.A.ci, op.A.v, op.jd, c->s);
+    launch_diag_inv(op.n, op.A.rp, op.A.ci, op.A.v, op.jd, st);
     if (mixed(c)) {
-      op.jd32 = cast32(c->ar, op.jd, op.n, c->s);
-      op.v32 = cast32(c->ar, op.A.v, op.A.nnz, c->s);
+      op.jd32 = cast32(c->ar, op.jd, op.n, st);
+      op.v32 = cast32(c->ar, op.A.v, op.A.nnz, st);
     }
-    op.b = c->ar.alloc<char>(es * op.n, true);
-    op.x = c->ar.alloc<char>(es * op.n, true);
+    op.b = c->ar.alloc<char>(es * op.n, true, st);
+    op.x = c->ar.alloc<char>(es * op.n, true, st);
   } else {
-    SetupCtx sc{&c->ar, c->s, &c->o, mixed(c), c->o.keep_transpose != 0};
+    SetupCtx sc{&c->ar, st, &c->o, mixed(c), c->o.keep_transpose != 0};
     build_hierarchy(sc, op.h, op.A);
     op.b = op.h.L[0].b;
     op.x = op.h.L[0].x;
   }
   if (op.count > 1) {
-    op.bsave = c->ar.alloc<char>(es * op.n, true);
-    op.xacc = c->ar.alloc<char>(es * op.n, true);
+    op.bsave = c->ar.alloc<char>(es * op.n, true, st);
+    op.xacc = c->ar.alloc<char>(es * op.n, true, st);
   }
   if (op.jacobi) {
     JacDesc<T> j1{(T*)op.x, (const T*)op.b, pick<T>(op.jd, op.jd32)};
     JacDesc<T> j2{(T*)op.xacc, (const T*)op.bsave, pick<T>(op.jd, op.jd32)};
     JacDesc<T>* d = c->ar.alloc<JacDesc<T>>(2);
-    MGD_CUDA(cudaMemcpyAsync(d, &j1, sizeof(j1), cudaMemcpyHostToDevice, c->s));
-    MGD_CUDA(cudaMemcpyAsync(d + 1, &j2, sizeof(j2), cudaMemcpyHostToDevice, c->s));
-    MGD_CUDA(cudaStreamSynchronize(c->s));
+    MGD_CUDA(cudaMemcpyAsync(d, &j1, sizeof(j1), cudaMemcpyHostToDevice, st));
+    MGD_CUDA(cudaMemcpyAsync(d + 1, &j2, sizeof(j2), cudaMemcpyHostToDevice, st));
     op.d_jac = d;
     op.d_jac2 = d + 1;
   }
+  MGD_CUDA(cudaStreamSynchronize(st));
+}
+
+// Setup of independent operators runs concurrently: each worker thread owns a
+// CUDA stream and builds whole hierarchies, so the many small host round
+// trips of one hierarchy (scan totals, PMIS rounds) overlap with the others.
+template <typename T>
+static void finalize_ops_parallel(mgd_ctx* c, size_t first, size_t last) {
+  size_t nops = last - first;
+  if (nops == 0) return;
+  MGD_CUDA(cudaStreamSynchronize(c->s));
+  unsigned hw = std::thread::hardware_concurrency();
+  size_t nthreads = std::min<size_t>(nops, std::max<unsigned>(1u, std::min<unsigned>(hw ? hw : 4, 16)));
+  if (nthreads <= 1) {
+    for (size_t k = first; k < last; ++k) finalize_op<T>(c, c->ops[k], c->s);
+    return;
+  }
+  std::atomic<size_t> next(first);
+  std::vector<Error> errs;
+  std::mutex emu;
+  auto worker = [&]() {
+    cudaStream_t st = nullptr;
+    try {
+      MGD_CUDA(cudaSetDevice(c->device));
+      MGD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      tl_pool = c->ar.pool;
+      tl_stream = st;
+      for (size_t k = next++; k < last; k = next++) finalize_op<T>(c, c->ops[k], st);
+    } catch (const Error& e) {
+      std::lock_guard<std::mutex> lk(emu);
+      errs.push_back(e);
+    } catch (const std::exception& e) {
+      std::lock_guard<std::mutex> lk(emu);
+      errs.push_back(Error{MGD_ECUDA, e.what()});
+    }
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+    tl_stream = nullptr;
+  };
+  std::vector<std::thread> th;
+  for (size_t t = 0; t < nthreads; ++t) th.emplace_back(worker);
+  for (auto& t : th) t.join();
+  if (!errs.empty()) throw errs.front();
 }
 
 static int cycles_for(const mgd_opts& o, int kind, int comp, int G) {
@@ -1240,6 +1289,8 @@ static int guarded(mgd_ctx* c, F&& f) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != c->device) MGD_CUDA(cudaSetDevice(c->device));
+    tl_pool = c->ar.pool;
+    tl_stream = nullptr;
     int r = f();
     if (dev != c->device) cudaSetDevice(dev);
     return r;
@@ -1458,11 +1509,10 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
     bd.d_dtab = (double**)upload_vec(c, bd.d);
   }
   // hierarchies / Jacobi data
-  for (auto& op : c->ops) {
-    if (mixed(c)) finalize_op<float>(c, op);
-    else finalize_op<double>(c, op);
+  if (mixed(c)) finalize_ops_parallel<float>(c, 0, c->ops.size());
+  else finalize_ops_parallel<double>(c, 0, c->ops.size());
+  for (auto& op : c->ops)
     if (op.jacobi) c->n_jacobi++;
-  }
   if (c->kind == MGD_PCTL) {
     // p_a = -A_a^{-1} D_aE 1 by option #3 (V-cycles until ||r|| <= tol ||rhs||), FP64 arithmetic
     BlockData& bd = c->bd;
@@ -1554,8 +1604,8 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
                         Ac.rp, Ac.ci, Ac.v, s);
     bd.Ac = Ac;
     int oAc = add_op(c, OP_AC, E, Ac);
-    if (mixed(c)) finalize_op<float>(c, c->ops[oAc]);
-    else finalize_op<double>(c, c->ops[oAc]);
+    if (mixed(c)) finalize_op<float>(c, c->ops[oAc], s);
+    else finalize_op<double>(c, c->ops[oAc], s);
     if (c->ops[oAc].jacobi) c->n_jacobi++;
   }
   // program, batches, graph
@@ -1827,6 +1877,14 @@ int mgd_create(mgd_ctx** out, const mgd_opts* o, void* stream) {
     delete c;
     return MGD_ECUDA;
   }
+  try {
+    c->pool.create(c->device);
+  } catch (const Error& e) {
+    delete c;
+    return e.code;
+  }
+  c->ar.pool = c->pool.pool;
+  c->ar.stream = c->s;
   *out = c;
   return MGD_OK;
 }
@@ -2057,6 +2115,8 @@ long long mgd_kernel_launches(void) { return __atomic_load_n(&g_kernel_launches,
 void mgd_destroy(mgd_ctx* c) {
   if (!c) return;
   free_setup(c);
+  if (c->hpin) cudaFreeHost(c->hpin);
+  c->pool.destroy();
   delete c;
 }
 

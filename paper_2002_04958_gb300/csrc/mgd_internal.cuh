@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -37,43 +38,80 @@ constexpr int kThreads = 256;
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // ------------------------------------------------------------------ memory
-// Device allocations owned by a context: freed together at destroy/re-setup.
+// Device memory of a context comes from its own stream-ordered memory pool
+// (cudaMemPool with a high release threshold, so freed blocks stay cached and
+// no allocation or free synchronises the device).
+struct Pool {
+  cudaMemPool_t pool = nullptr;
+  void create(int device) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    MGD_CUDA(cudaMemPoolCreate(&pool, &props));
+    unsigned long long thr = ~0ULL;
+    MGD_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  }
+  void destroy() {
+    if (pool) cudaMemPoolDestroy(pool);
+    pool = nullptr;
+  }
+};
+
+// the pool and (in setup worker threads) the stream of the calling thread
+extern thread_local cudaMemPool_t tl_pool;
+extern thread_local cudaStream_t tl_stream;
+
+inline void* pool_alloc(cudaMemPool_t pool, size_t bytes, cudaStream_t s) {
+  if (!pool) pool = tl_pool;
+  void* p = nullptr;
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{8, "device allocation of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e)};
+  }
+  return p;
+}
+
+// Allocations owned by a context, freed together at destroy / re-setup.
+// Safe to use from the setup worker threads: each allocates (and zeroes) on
+// its own stream and synchronises it before the memory is used elsewhere.
 struct Arena {
   std::vector<void*> ptrs;
   cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+  std::mutex mu;
   template <typename T>
-  T* alloc(size_t n, bool zero = false) {
-    void* p = nullptr;
+  T* alloc(size_t n, bool zero = false, cudaStream_t zs = nullptr) {
     size_t bytes = (n ? n : 1) * sizeof(T);
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      throw Error{8, "cudaMalloc(" + std::to_string(bytes) + " bytes) failed: " + cudaGetErrorString(e)};
+    cudaStream_t st = zs ? zs : (tl_stream ? tl_stream : stream);
+    void* p = pool_alloc(pool, bytes, st);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      ptrs.push_back(p);
     }
-    ptrs.push_back(p);
-    if (zero) MGD_CUDA(cudaMemsetAsync(p, 0, bytes, stream));
+    if (zero) MGD_CUDA(cudaMemsetAsync(p, 0, bytes, st));
     return (T*)p;
   }
   void release() {
-    for (void* p : ptrs) cudaFree(p);
+    std::lock_guard<std::mutex> lk(mu);
+    if (stream) cudaStreamSynchronize(stream);
+    for (void* p : ptrs) cudaFreeAsync(p, stream);
+    if (stream) cudaStreamSynchronize(stream);
     ptrs.clear();
   }
 };
 
-// Scratch allocations for one setup step (stream-ordered)
+// Scratch allocations for one setup step (stream-ordered, freed at scope exit)
 struct Scratch {
   std::vector<void*> ptrs;
   cudaStream_t stream;
-  explicit Scratch(cudaStream_t s) : stream(s) {}
+  cudaMemPool_t pool;
+  explicit Scratch(cudaStream_t s, cudaMemPool_t p = nullptr) : stream(s), pool(p ? p : tl_pool) {}
   template <typename T>
   T* alloc(size_t n) {
-    void* p = nullptr;
-    size_t bytes = (n ? n : 1) * sizeof(T);
-    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      throw Error{8, "cudaMallocAsync(" + std::to_string(bytes) + " bytes) failed"};
-    }
+    void* p = pool_alloc(pool, (n ? n : 1) * sizeof(T), stream);
     ptrs.push_back(p);
     return (T*)p;
   }

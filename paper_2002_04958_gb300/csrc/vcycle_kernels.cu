@@ -1,0 +1,143 @@
+// vcycle_kernels.cu -- the V(1,1) cycle phases (Section 3.1) on every level:
+// pre-smoothing + residual, restriction, prolongation, post-smoothing, and the
+// coarsest-level solve.
+//
+// HBM-bound sparse kernels.  Rows are read either from a sliced ELL layout
+// (32-row slices stored column-major, so a warp reads 32 consecutive values
+// per step: fully coalesced) or from CSR with TPR threads per row
+// (warp-shuffle reduction); the layout is chosen per level at setup by timing.
+// Every launch serves all subsystems of a batch: blockIdx.y selects the
+// subsystem's level descriptor.
+#include "mgd_internal.cuh"
+#include "row_dot.cuh"
+
+namespace mgd {
+
+// ---------------------------------------------------------------- V-cycle phases
+// PRE: xt = D^-1 b (zero initial guess), r = b - A xt = b - (A D^-1) b, using
+// the column-scaled copy of A so that each nonzero costs one multiply-add
+template <typename T, int FMT>
+__global__ void __launch_bounds__(kThreads) k_pre(const LDesc<T>* __restrict__ descs) {
+  const LDesc<T>* d = descs + blockIdx.y;
+  constexpr int TPR = FmtTraits<FMT>::tpr;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = g / TPR, lane = g % TPR;
+  int n = d->n;
+  if (((g & ~31) / TPR) >= n) return;  // the whole warp is past the last row (TPR divides 32)
+  bool valid = row < n;
+  const T* b = d->b;
+  XPlain<T> xf{b};
+  T s = row_dot<T, FMT>(row, lane, valid, d->rp, d->ci, d->vpre, d->sptr, d->sci, d->svpre, xf);
+  if (valid && lane == 0) {
+    T bi = b[row];
+    d->xt[row] = d->dinv[row] * bi;
+    d->r[row] = bi - s;
+  }
+}
+
+// POST: x = xt + D^-1 (b - A xt)
+template <typename T, int FMT>
+__global__ void __launch_bounds__(kThreads) k_post(const LDesc<T>* __restrict__ descs) {
+  const LDesc<T>* d = descs + blockIdx.y;
+  constexpr int TPR = FmtTraits<FMT>::tpr;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = g / TPR, lane = g % TPR;
+  int n = d->n;
+  if (((g & ~31LL) / TPR) >= n) return;
+  bool valid = row < n;
+  XPlain<T> xf{d->xt};
+  T s = row_dot<T, FMT>(row, lane, valid, d->rp, d->ci, d->v, d->sptr, d->sci, d->sv, xf);
+  if (valid && lane == 0) d->x[row] = d->xt[row] + d->dinv[row] * (d->b[row] - s);
+}
+
+// RESTRICT: bc = R r ; PROLONG: xt += P xc  (CSR, TPR threads per row)
+template <typename T, int FMT>
+__global__ void __launch_bounds__(kThreads) k_restrict(const LDesc<T>* __restrict__ descs) {
+  const LDesc<T>* d = descs + blockIdx.y;
+  constexpr int TPR = FmtTraits<FMT>::tpr;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = g / TPR, lane = g % TPR;
+  int n = d->nc;
+  if (((g & ~31LL) / TPR) >= n) return;
+  bool valid = row < n;
+  XPlain<T> xf{d->r};
+  T s = row_dot<T, FMT>(row, lane, valid, d->rrp, d->rci, d->rv, nullptr, nullptr, nullptr, xf);
+  if (valid && lane == 0) d->bc[row] = s;
+}
+
+template <typename T, int FMT>
+__global__ void __launch_bounds__(kThreads) k_prolong(const LDesc<T>* __restrict__ descs) {
+  const LDesc<T>* d = descs + blockIdx.y;
+  constexpr int TPR = FmtTraits<FMT>::tpr;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = g / TPR, lane = g % TPR;
+  int n = d->n;
+  if (((g & ~31LL) / TPR) >= n) return;
+  bool valid = row < n;
+  XPlain<T> xf{d->xc};
+  T s = row_dot<T, FMT>(row, lane, valid, d->prp, d->pci, d->pv, nullptr, nullptr, nullptr, xf);
+  if (valid && lane == 0) d->xt[row] += s;
+}
+
+// stalled coarsest level, first l1-Jacobi sweep from zero: xt = D^-1 b
+template <typename T>
+__global__ void k_jac1(const LDesc<T>* __restrict__ descs) {
+  const LDesc<T>* d = descs + blockIdx.y;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d->n) d->xt[i] = d->dinv[i] * d->b[i];
+}
+
+// coarsest level: x = A_L^{-1} b with the dense FP64 inverse (one CTA per subsystem)
+template <typename T>
+__global__ void k_coarse(const LDesc<T>* __restrict__ descs) {
+  const LDesc<T>* d = descs + blockIdx.y;
+  extern __shared__ double sb[];
+  int n = d->cn;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) sb[j] = (double)d->b[j];
+  __syncthreads();
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < n; i += nw) {
+    const double* row = d->cinv + (size_t)i * n;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s += row[j] * sb[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) d->x[i] = (T)s;
+  }
+}
+
+#define MGD_DISPATCH_FMT(K, fmt, maxrows, ny, s, descs)                                        \
+  do {                                                                                         \
+    auto g_ = [&](int tpr) { return dim3(cdiv((long long)(maxrows) * tpr + 32, kThreads), (ny)); }; \
+    switch (fmt) {                                                                             \
+      case FMT_SELL: K<T, FMT_SELL><<<g_(1), kThreads, 0, s>>>(descs); break;                  \
+      case FMT_CSR1: K<T, FMT_CSR1><<<g_(1), kThreads, 0, s>>>(descs); break;                  \
+      case FMT_CSR2: K<T, FMT_CSR2><<<g_(2), kThreads, 0, s>>>(descs); break;                  \
+      case FMT_CSR4: K<T, FMT_CSR4><<<g_(4), kThreads, 0, s>>>(descs); break;                  \
+      case FMT_CSR8: K<T, FMT_CSR8><<<g_(8), kThreads, 0, s>>>(descs); break;                  \
+      case FMT_CSR16: K<T, FMT_CSR16><<<g_(16), kThreads, 0, s>>>(descs); break;               \
+      default: K<T, FMT_CSR32><<<g_(32), kThreads, 0, s>>>(descs); break;                      \
+    }                                                                                          \
+  } while (0)
+
+template <typename T>
+void launch_phase(int phase, int fmtA, int fmtRP, const LDesc<T>* d_descs, int ndesc, int maxrows, cudaStream_t s) {
+  if (ndesc <= 0 || maxrows <= 0) return;
+  int rp = fmtRP == FMT_SELL ? FMT_CSR1 : fmtRP;
+  switch (phase) {
+    case PH_PRE: MGD_DISPATCH_FMT(k_pre, fmtA, maxrows, ndesc, s, d_descs); break;
+    case PH_POST: MGD_DISPATCH_FMT(k_post, fmtA, maxrows, ndesc, s, d_descs); break;
+    case PH_RESTRICT: MGD_DISPATCH_FMT(k_restrict, rp, maxrows, ndesc, s, d_descs); break;
+    case PH_PROLONG: MGD_DISPATCH_FMT(k_prolong, rp, maxrows, ndesc, s, d_descs); break;
+    case PH_JAC1: k_jac1<T><<<dim3(cdiv(maxrows, kThreads), ndesc), kThreads, 0, s>>>(d_descs); break;
+    case PH_COARSE:
+      k_coarse<T><<<dim3(1, ndesc), kThreads, sizeof(double) * maxrows, s>>>(d_descs);
+      break;
+  }
+  MGD_LAUNCH_CHECK();
+}
+
+template void launch_phase<double>(int, int, int, const LDesc<double>*, int, int, cudaStream_t);
+template void launch_phase<float>(int, int, int, const LDesc<float>*, int, int, cudaStream_t);
+
+}  // namespace mgd

@@ -46,8 +46,7 @@ def main():
         slv.profile(-1)
     for _ in range(args.applies):
         slv.precond_apply(v)
-    import torch as _t
-    _t.cuda.synchronize()
+    torch.cuda.synchronize()
     out = {"workload": inputs.PRESET_NAMES[args.config], "kind": args.kind, "n": s.n, "applies": args.applies}
     if args.timing:
         for cls, name in [(0, "level0_smoothing"), (1, "vcycle_all"), (4, "block_updates")]:
