@@ -78,6 +78,9 @@ typedef struct mgd_opts {
   int use_graph;          /* 1: the preconditioner apply is replayed from a captured CUDA graph */
   int autotune;           /* 1: time sparse-kernel variants per level at setup and keep the fastest */
   int keep_transpose;     /* 1: keep A_l^T per level so that mgd_solve_transpose can run */
+  int fuse_rows;          /* levels below level 0 whose subsystems all have <= fuse_rows rows run, with every
+                             coarser level, in one thread-block-cluster launch per V-cycle; 0: chosen by the
+                             autotuner (not fused when autotune is off); -1: never */
 } mgd_opts;
 
 /* Fill *o with the defaults listed above.  Returns MGD_EINVAL if o is NULL. */
@@ -165,6 +168,15 @@ int mgd_block_vector(mgd_ctx *c, int which, int comp, int comp2, double *h_out);
 /* 1 if coupling D_{a,b} was dropped by the Section 3.6 rule. */
 int mgd_coupling_dropped(mgd_ctx *c, int a, int b);
 
+/* Launch plan of the V-cycle batches: *nbatches batches (independent V-cycles
+ * launched together); for batch `batch` and level `level`, the number of
+ * subsystems descending through that level, the largest row count, and the
+ * autotuned layouts of the operator / restriction / prolongation kernels
+ * (0 = SELL-32, 1..6 = CSR with 1, 2, 4, 8, 16, 32 threads per row); *tail =
+ * first level handled by the fused coarse-level kernel (depth if none). */
+int mgd_plan_info(mgd_ctx *c, int batch, int level, int *nbatches, int *depth, int *nsub, int *maxrows, int *fmtA,
+                  int *fmtR, int *fmtP, int *tail);
+
 /* Kernel timing for the roofline: CUDA events bracket every launch of the
  * kernel classes selected by the bit mask (bit k = class k; 0 turns timing
  * off, -1 selects all) on the context's stream.  Classes: 0 = level-0
@@ -173,7 +185,10 @@ int mgd_coupling_dropped(mgd_ctx *c, int a, int b);
  * 4 = block-level updates of the block preconditioners.  The read call
  * synchronises the stream and returns, for class cls (cls = 1 also counts
  * class 0, i.e. every V-cycle kernel), the launch count, the summed device
- * time and the summed algorithmic bytes.  With opts.use_graph the selected
+ * time and the summed algorithmic bytes.  V-cycle launches are also counted
+ * under detail classes: 16 + 4*level + phase (phase 0 pre-smoothing +
+ * residual, 1 restriction, 2 prolongation, 3 post-smoothing), 400 + level for
+ * coarsest-level solves, 15 for the fused coarse-level kernel.  With opts.use_graph the selected
  * kernels are bracketed by event nodes inside the captured graph (the graph is
  * captured again when the mask changes), so timing does not change how the
  * preconditioner is launched. */

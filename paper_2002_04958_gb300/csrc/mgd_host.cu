@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <map>
 #include <memory>
 #include <string>
 #include <thread>
@@ -40,12 +41,15 @@ struct Profiler {
     int cls;
     cudaEvent_t a, b;
     double bytes;
+    int detail;  // second class (per level and phase), -1 if none
   };
+  static constexpr int kClasses = 512;
   std::vector<Pair> pending, graph_pairs;
   bool graph_replayed = false;
   std::vector<cudaEvent_t> pool;
-  long long n[8] = {0};
-  double ms[8] = {0}, bytes[8] = {0};
+  long long n[kClasses] = {0};
+  double ms[kClasses] = {0}, bytes[kClasses] = {0};
+  int next_detail = -1;  // detail class of the next begin()
   cudaEvent_t get() {
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();
@@ -61,11 +65,15 @@ struct Profiler {
     else MGD_CUDA(cudaEventRecord(e, s));
   }
   int begin(cudaStream_t s, int cls) {
-    if (!on || !(mask & (1u << cls))) return -1;
+    if (!on || !(mask & (1u << cls))) {
+      next_detail = -1;
+      return -1;
+    }
     cudaEvent_t a = get();
     record(a, s);
     auto& v = capturing ? graph_pairs : pending;
-    v.push_back({cls, a, nullptr, 0.0});
+    v.push_back({cls, a, nullptr, 0.0, next_detail});
+    next_detail = -1;
     return (int)v.size() - 1;
   }
   void end(int id, int cls, double by, cudaStream_t s) {
@@ -83,6 +91,11 @@ struct Profiler {
     n[p.cls]++;
     ms[p.cls] += e;
     bytes[p.cls] += p.bytes;
+    if (p.detail >= 0 && p.detail < kClasses) {
+      n[p.detail]++;
+      ms[p.detail] += e;
+      bytes[p.detail] += p.bytes;
+    }
   }
   // call after the stream has been synchronised
   void harvest() {
@@ -111,7 +124,7 @@ struct Profiler {
     }
     pending.clear();
     graph_replayed = false;
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kClasses; ++k) {
       n[k] = 0;
       ms[k] = bytes[k] = 0;
     }
@@ -407,6 +420,14 @@ struct VBatch {
   };
   std::vector<LP> plan, planT;
   double bytes_total = 0;
+  // fused coarse-level kernel: levels >= tail_level of every subsystem in one
+  // cluster launch (tail_level >= depth: not used)
+  int tail_level = 1 << 20;
+  int tail_cs = 8;
+  TailSub<T>* d_tail = nullptr;
+  TailSub<T>* d_tailT = nullptr;
+  int ntail = 0;
+  double tail_bytes = 0;
 };
 
 template <typename T>
@@ -515,38 +536,128 @@ static void build_plan(Arena& ar, VBatch<T>& vb, bool trans, cudaStream_t s) {
 template <typename T>
 static void run_vbatch(VBatch<T>& vb, bool trans, cudaStream_t s, Profiler& prof) {
   auto& plan = trans ? vb.planT : vb.plan;
-  for (int l = 0; l < vb.depth; ++l) {
+  const bool tail = vb.tail_level < vb.depth && vb.ntail > 0;
+  const int ltop = tail ? vb.tail_level : vb.depth;  // levels run with per-level launches
+  for (int l = 0; l < ltop; ++l) {
     auto& lp = plan[l];
     if (lp.ndown) {
+      prof.next_detail = 16 + 4 * l + 0;
       int id = prof.begin(s, l == 0 ? 0 : 1);
       launch_phase<T>(PH_PRE, lp.fmtA, lp.fmtR, lp.d_down, lp.ndown, lp.maxn, s);
       prof.end(id, l == 0 ? 0 : 1, lp.bytes_pre, s);
+      prof.next_detail = 16 + 4 * l + 1;
       id = prof.begin(s, 1);
       launch_phase<T>(PH_RESTRICT, lp.fmtA, lp.fmtR, lp.d_down, lp.ndown, lp.maxnc, s);
       prof.end(id, 1, lp.bytes_restrict, s);
     }
     if (lp.nclu) {
+      prof.next_detail = 400 + l;
       int id = prof.begin(s, 1);
       launch_phase<T>(PH_COARSE, lp.fmtA, lp.fmtR, lp.d_clu, lp.nclu, lp.maxcn, s);
       prof.end(id, 1, lp.bytes_coarse, s);
     }
     if (lp.ncjac) {
+      prof.next_detail = 400 + l;
       int id = prof.begin(s, l == 0 ? 0 : 1);
       launch_phase<T>(PH_JAC1, lp.fmtA, lp.fmtR, lp.d_cjac, lp.ncjac, lp.maxcj, s);
       launch_phase<T>(PH_POST, lp.fmtA, lp.fmtR, lp.d_cjac, lp.ncjac, lp.maxcj, s);
       prof.end(id, l == 0 ? 0 : 1, lp.bytes_jac + lp.bytes_post_cj, s);
     }
   }
-  for (int l = vb.depth - 2; l >= 0; --l) {
+  if (tail) {
+    prof.next_detail = 15;
+    int id = prof.begin(s, 1);
+    launch_vtail<T>(trans ? vb.d_tailT : vb.d_tail, vb.ntail, vb.tail_cs, s);
+    prof.end(id, 1, vb.tail_bytes, s);
+  }
+  for (int l = std::min(vb.depth - 2, ltop - 1); l >= 0; --l) {
     auto& lp = plan[l];
     if (!lp.ndown) continue;
+    prof.next_detail = 16 + 4 * l + 2;
     int id = prof.begin(s, 1);
     launch_phase<T>(PH_PROLONG, lp.fmtA, lp.fmtP, lp.d_down, lp.ndown, lp.maxn, s);
     prof.end(id, 1, lp.bytes_prolong, s);
+    prof.next_detail = 16 + 4 * l + 3;
     id = prof.begin(s, l == 0 ? 0 : 1);
     launch_phase<T>(PH_POST, lp.fmtA, lp.fmtP, lp.d_down, lp.ndown, lp.maxn, s);
     prof.end(id, l == 0 ? 0 : 1, lp.bytes_post, s);
   }
+}
+
+// Descriptors of the fused coarse-level kernel for the first fused level Lt:
+// every subsystem with more than Lt levels contributes its levels Lt..coarsest.
+template <typename T>
+static void build_tail(Arena& ar, VBatch<T>& vb, int Lt, bool keepT, cudaStream_t s) {
+  vb.tail_level = Lt;
+  vb.ntail = 0;
+  vb.tail_bytes = 0;
+  if (Lt >= vb.depth) return;
+  for (int pass = 0; pass < (keepT ? 2 : 1); ++pass) {
+    bool trans = pass == 1;
+    std::vector<TailSub<T>> subs;
+    std::vector<std::vector<LDesc<T>>> keep;
+    for (Hier* h : vb.hs) {
+      if (h->nlev() <= Lt) continue;
+      std::vector<LDesc<T>> lv;
+      for (int l = Lt; l < h->nlev(); ++l) lv.push_back(make_desc<T>(*h, l, trans));
+      LDesc<T>* d = ar.alloc<LDesc<T>>(lv.size());
+      MGD_CUDA(cudaMemcpyAsync(d, lv.data(), sizeof(LDesc<T>) * lv.size(), cudaMemcpyHostToDevice, s));
+      keep.push_back(std::move(lv));
+      subs.push_back(TailSub<T>{d, h->nlev() - Lt, h->coarse_lu ? 1 : 0});
+    }
+    TailSub<T>* dt = subs.empty() ? nullptr : ar.alloc<TailSub<T>>(subs.size());
+    if (dt) MGD_CUDA(cudaMemcpyAsync(dt, subs.data(), sizeof(TailSub<T>) * subs.size(), cudaMemcpyHostToDevice, s));
+    MGD_CUDA(cudaStreamSynchronize(s));
+    (trans ? vb.d_tailT : vb.d_tail) = dt;
+    vb.ntail = (int)subs.size();
+  }
+  for (int l = Lt; l < vb.depth; ++l) {
+    auto& lp = vb.plan[l];
+    vb.tail_bytes += lp.bytes_pre + lp.bytes_post + lp.bytes_restrict + lp.bytes_prolong + lp.bytes_coarse +
+                     lp.bytes_jac + lp.bytes_post_cj;
+  }
+}
+
+// Autotune the first fused level: time whole V-cycles with no fusion and with
+// fusion from the first level whose largest row count is below each threshold.
+template <typename T>
+static void autotune_tail(Arena& ar, VBatch<T>& vb, bool keepT, cudaStream_t s) {
+  Profiler none;
+  std::vector<int> cand{vb.depth};
+  for (int thr : {4096, 16384, 65536, 262144}) {
+    int Lt = vb.depth;
+    for (int l = 1; l < vb.depth; ++l) {
+      auto& lp = vb.plan[l];
+      int rows = std::max(lp.maxn, std::max(lp.maxcn, lp.maxcj));
+      if (rows <= thr) {
+        Lt = l;
+        break;
+      }
+    }
+    if (std::find(cand.begin(), cand.end(), Lt) == cand.end()) cand.push_back(Lt);
+  }
+  cudaEvent_t e0, e1;
+  MGD_CUDA(cudaEventCreate(&e0));
+  MGD_CUDA(cudaEventCreate(&e1));
+  int best_lt = vb.depth;
+  float best = 1e30f;
+  for (int Lt : cand) {
+    build_tail<T>(ar, vb, Lt, keepT, s);
+    run_vbatch<T>(vb, false, s, none);
+    MGD_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 5; ++r) run_vbatch<T>(vb, false, s, none);
+    MGD_CUDA(cudaEventRecord(e1, s));
+    MGD_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    MGD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best * 0.97f) {  // prefer fewer fused levels unless clearly faster
+      best = ms;
+      best_lt = Lt;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  build_tail<T>(ar, vb, best_lt, keepT, s);
 }
 
 // Autotuner: per level of a batch, time the operator phase (PRE) under each
@@ -1219,6 +1330,30 @@ static void run_program(mgd_ctx* c, bool trans) {
   }
 }
 
+// Autotuner decisions keyed by the batch's shape (value type, depth, and per
+// level the subsystem count, largest row count and nonzeros): a setup of a
+// system with the same hierarchy shape reuses them instead of re-timing.
+struct TuneResult {
+  std::vector<int> fmtA, fmtR, fmtP;
+  int tail_level;
+};
+static std::mutex g_tune_mu;
+static std::map<std::vector<long long>, TuneResult> g_tune_cache;
+
+template <typename T>
+static std::vector<long long> tune_key(const VBatch<T>& vb, bool trans, int fuse_rows) {
+  std::vector<long long> k{(long long)sizeof(T), vb.depth, trans ? 1 : 0, fuse_rows};
+  for (int l = 0; l < vb.depth; ++l) {
+    long long nnz = 0;
+    for (Hier* h : vb.hs)
+      if (l < h->nlev()) nnz += h->L[l].A.nnz;
+    k.push_back(vb.plan[l].ndown);
+    k.push_back(vb.plan[l].maxn);
+    k.push_back(nnz);
+  }
+  return k;
+}
+
 // group INVERT steps into batches (one batch per step when batched, else one per op)
 template <typename T>
 static void build_batches(mgd_ctx* c) {
@@ -1265,9 +1400,56 @@ static void build_batches(mgd_ctx* c) {
   for (auto& vb : B) {
     build_plan<T>(c->ar, vb, false, c->s);
     if (c->o.keep_transpose) build_plan<T>(c->ar, vb, true, c->s);
+    bool cached = false;
+    std::vector<long long> key = tune_key<T>(vb, false, c->o.fuse_rows);
+    if (c->o.autotune) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end() && (int)it->second.fmtA.size() == vb.depth) {
+        for (int l = 0; l < vb.depth; ++l) {
+          vb.plan[l].fmtA = it->second.fmtA[l];
+          vb.plan[l].fmtR = it->second.fmtR[l];
+          vb.plan[l].fmtP = it->second.fmtP[l];
+          if (c->o.keep_transpose) {
+            vb.planT[l].fmtA = it->second.fmtA[l];
+            vb.planT[l].fmtR = it->second.fmtR[l];
+            vb.planT[l].fmtP = it->second.fmtP[l];
+          }
+        }
+        cached = true;
+      }
+    }
+    if (cached) {
+      build_tail<T>(c->ar, vb, g_tune_cache[key].tail_level, c->o.keep_transpose != 0, c->s);
+      continue;
+    }
     if (c->o.autotune) {
       autotune<T>(vb, false, c->s);
       if (c->o.keep_transpose) autotune<T>(vb, true, c->s);
+    }
+    if (c->o.fuse_rows > 0) {
+      int Lt = vb.depth;
+      for (int l = 1; l < vb.depth; ++l) {
+        auto& lp = vb.plan[l];
+        if (std::max(lp.maxn, std::max(lp.maxcn, lp.maxcj)) <= c->o.fuse_rows) {
+          Lt = l;
+          break;
+        }
+      }
+      build_tail<T>(c->ar, vb, Lt, c->o.keep_transpose != 0, c->s);
+    } else if (c->o.fuse_rows == 0 && c->o.autotune) {
+      autotune_tail<T>(c->ar, vb, c->o.keep_transpose != 0, c->s);
+    }
+    if (c->o.autotune) {
+      TuneResult r;
+      for (int l = 0; l < vb.depth; ++l) {
+        r.fmtA.push_back(vb.plan[l].fmtA);
+        r.fmtR.push_back(vb.plan[l].fmtR);
+        r.fmtP.push_back(vb.plan[l].fmtP);
+      }
+      r.tail_level = vb.tail_level;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_cache[key] = r;
     }
   }
 }
@@ -1768,19 +1950,14 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
       spmv(zj, c->w);
       int nv = j + 1;
       int aid = c->prof.begin(s, 3);
-      // pass 1: h1 = V^T w and ||w||^2 (slot nv); w -= V h1 -> ||w'||^2 in hbuf[65]
-      launch_mdot(n, c->V, n, nv, c->w, c->partial, c->hbuf, s, 1);
-      launch_vupdate(n, c->V, n, nv, c->hbuf, c->w, c->partial, c->hbuf + 65, s);
-      // pass 2 only if ||w'||^2 < ||w||^2 / 2 (decided on the device)
-      launch_mdot(n, c->V, n, nv, c->w, c->partial, c->hbuf + 32, s, 0, c->hbuf + 65, c->hbuf + nv);
-      launch_vupdate(n, c->V, n, nv, c->hbuf + 32, c->w, c->partial, c->hbuf + 64, s, c->hbuf + 65, c->hbuf + nv);
+      // modified Gram-Schmidt, one fused pass per basis vector: h in hbuf[0..j], ||w||^2 in hbuf[64]
+      launch_mgs(n, c->V, n, nv, c->w, c->hbuf, c->hbuf + 64, c->partial, c->partial + kDotBlocks, s);
       launch_scale_by_norm(n, c->w, c->hbuf + 64, c->V + (size_t)(j + 1) * n, s);
-      c->prof.end(aid, 3, 8.0 * n * (2.0 * (nv + 1) + 2.0 * (nv + 2) + 2.0), s);
-      MGD_CUDA(cudaMemcpyAsync(hp, c->hbuf, 66 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      c->prof.end(aid, 3, 8.0 * n * (4.0 * nv + 2.0 + 2.0), s);
+      MGD_CUDA(cudaMemcpyAsync(hp, c->hbuf, 65 * sizeof(double), cudaMemcpyDeviceToHost, s));
       MGD_CUDA(cudaStreamSynchronize(s));
       c->prof.harvest();
-      // second-pass coefficients are zero when the pass was skipped
-      for (int i = 0; i <= j; ++i) Hm(i, j) = hp[i] + (hp[65] < 0.5 * hp[nv] ? hp[32 + i] : 0.0);
+      for (int i = 0; i <= j; ++i) Hm(i, j) = hp[i];
       double hn = std::sqrt(hp[64]);
       Hm(j + 1, j) = hn;
       for (int i = 0; i < j; ++i) {
@@ -2091,7 +2268,7 @@ int mgd_profile_enable(mgd_ctx* c, int mask) {
 
 int mgd_profile_read(mgd_ctx* c, int cls, long long* launches, double* ms, double* bytes) {
   return guarded(c, [&]() -> int {
-    if (cls < 0 || cls > 7) throw Error{MGD_EINVAL, "bad class"};
+    if (cls < 0 || cls >= Profiler::kClasses) throw Error{MGD_EINVAL, "bad class"};
     MGD_CUDA(cudaStreamSynchronize(c->s));
     c->prof.harvest();
     long long nl = c->prof.n[cls];
@@ -2109,6 +2286,28 @@ int mgd_profile_read(mgd_ctx* c, int cls, long long* launches, double* ms, doubl
 }
 
 const char* mgd_last_error(mgd_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int mgd_plan_info(mgd_ctx* c, int batch, int level, int* nbatches, int* depth, int* nsub, int* maxrows, int* fmtA,
+                  int* fmtR, int* fmtP, int* tail) {
+  if (!c || !c->ready) return MGD_EINVAL;
+  bool m = mixed(c);
+  int nb = m ? (int)c->vb32.size() : (int)c->vb64.size();
+  if (nbatches) *nbatches = nb;
+  if (batch < 0 || batch >= nb) return MGD_EINVAL;
+  auto fill = [&](auto& vb) -> int {
+    if (depth) *depth = vb.depth;
+    if (tail) *tail = vb.tail_level;
+    if (level < 0 || level >= vb.depth) return MGD_EINVAL;
+    auto& lp = vb.plan[level];
+    if (nsub) *nsub = lp.ndown;
+    if (maxrows) *maxrows = lp.maxn;
+    if (fmtA) *fmtA = lp.fmtA;
+    if (fmtR) *fmtR = lp.fmtR;
+    if (fmtP) *fmtP = lp.fmtP;
+    return MGD_OK;
+  };
+  return m ? fill(c->vb32[batch]) : fill(c->vb64[batch]);
+}
 
 long long mgd_kernel_launches(void) { return __atomic_load_n(&g_kernel_launches, __ATOMIC_RELAXED); }
 

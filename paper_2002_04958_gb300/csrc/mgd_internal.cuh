@@ -178,6 +178,15 @@ struct LDesc {
   int cn;
 };
 
+// One subsystem's share of the fused coarse-level kernel: its level
+// descriptors from the first fused level to its coarsest level.
+template <typename T>
+struct TailSub {
+  const LDesc<T>* lev;  // device array, nlev entries (first = first fused level)
+  int nlev;             // fused levels including the coarsest (>= 1)
+  int coarse_lu;        // coarsest: 1 dense inverse, 0 two l1-Jacobi sweeps
+};
+
 // Block-level pointer reference: absolute, or relative to the current
 // preconditioner input v / output z held in device memory (graph-safe).
 struct PRef {
@@ -277,6 +286,11 @@ enum Phase { PH_PRE = 0, PH_RESTRICT = 1, PH_PROLONG = 2, PH_POST = 3, PH_COARSE
 template <typename T>
 void launch_phase(int phase, int fmtA, int tprRP, const LDesc<T>* d_descs, int ndesc, int maxrows,
                   cudaStream_t s);
+// fused coarse-level V-cycle: one thread-block cluster of `cs` CTAs per subsystem
+template <typename T>
+void launch_vtail(const TailSub<T>* d_subs, int nsub, int cs, cudaStream_t s);
+constexpr int kTailThreads = 512;
+
 template <typename T>
 void launch_produce(const ProduceDesc<T>* d, int nd, int N, const IOSlots* io, cudaStream_t s);
 template <typename T>
@@ -301,15 +315,9 @@ void launch_copy_f64(int n, const double* a, double* b, cudaStream_t s);
 
 // Arnoldi / vector kernels (FP64)
 constexpr int kDotBlocks = 608;  // 4 x 152 SMs
-// out[t] = <V_t, w> (t < nv), out[nv] = <w, w> with selfdot; skipped (zeros)
-// unless cond_after[0] < 0.5 cond_before[0] when cond_after is given
-void launch_mdot(int n, const double* V, long long ldv, int nv, const double* w, double* partial, double* out,
-                 cudaStream_t s, int selfdot = 0, const double* cond_after = nullptr,
-                 const double* cond_before = nullptr);
-// w -= V h; nrm2 = ||w||^2 (same skip rule: then nrm2 = cond_after[0])
-void launch_vupdate(int n, const double* V, long long ldv, int nv, const double* h, double* w, double* partial,
-                    double* nrm2, cudaStream_t s, const double* cond_after = nullptr,
-                    const double* cond_before = nullptr);
+// modified Gram-Schmidt of w against V[:, 0..nv-1]: h[i], *nrm2 = ||w||^2
+void launch_mgs(int n, const double* V, long long ldv, int nv, double* w, double* h, double* nrm2, double* pa,
+                double* pb, cudaStream_t s);
 void launch_scale_by_norm(int n, const double* w, const double* nrm2, double* v, cudaStream_t s);
 void launch_vcomb(int n, const double* Z, long long ldz, int nv, const double* y, double* x, cudaStream_t s);
 void launch_norm2(int n, const double* x, double* partial, double* out, cudaStream_t s);

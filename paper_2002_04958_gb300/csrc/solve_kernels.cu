@@ -187,53 +187,6 @@ void launch_copy_f64(int n, const double* a, double* b, cudaStream_t s) {
 // ---------------------------------------------------------------- Arnoldi (FP64)
 constexpr int kMaxV = 32;
 
-// Classical Gram-Schmidt with a selective second pass (Daniel, Gragg, Kaufman,
-// Stewart 1976): the second projection runs only when the first one removed
-// more than half of ||w||^2, a test the kernels read from device memory
-// (cond_after < 0.5 cond_before), so no host round trip is needed.
-__device__ __forceinline__ bool second_pass_needed(const double* after, const double* before) {
-  return !after || after[0] < 0.5 * before[0];
-}
-
-// partial[b * kMaxV + t] = sum over this block's elements of V_t(i) w(i); with
-// selfdot, slot nv gets w.w.  Skipped (zeros) when cond says no second pass.
-template <int NV>
-__global__ void __launch_bounds__(kThreads) k_mdot(int n, const double* __restrict__ V, long long ldv, int nv,
-                                                   const double* __restrict__ w, double* __restrict__ partial,
-                                                   int selfdot, const double* __restrict__ cond_after,
-                                                   const double* __restrict__ cond_before) {
-  if (!second_pass_needed(cond_after, cond_before)) {
-    for (int t = threadIdx.x; t < NV; t += blockDim.x) partial[(size_t)blockIdx.x * kMaxV + t] = 0.0;
-    return;
-  }
-  double acc[NV];
-#pragma unroll
-  for (int t = 0; t < NV; ++t) acc[t] = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double wi = w[i];
-#pragma unroll
-    for (int t = 0; t < NV; ++t) {
-      if (t < nv) acc[t] += V[t * ldv + i] * wi;
-      else if (t == nv && selfdot) acc[t] += wi * wi;
-    }
-  }
-  __shared__ double sh[kThreads / 32][NV];
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int t = 0; t < NV; ++t) {
-    double s = acc[t];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) sh[warp][t] = s;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < NV; t += blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < kThreads / 32; ++k) s += sh[k][t];
-    partial[(size_t)blockIdx.x * kMaxV + t] = s;
-  }
-}
-
 // out[t] = sum_b partial[b * kMaxV + t]  (fixed order: deterministic)
 __global__ void k_reduce_partials(const double* __restrict__ partial, int nblocks, int nv, double* __restrict__ out) {
   int t = blockIdx.x;
@@ -252,63 +205,92 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, int nblock
 
 static int dot_blocks(int n) { return std::min(kDotBlocks, std::max(1, cdiv(n, kThreads))); }
 
-void launch_mdot(int n, const double* V, long long ldv, int nv, const double* w, double* partial, double* out,
-                 cudaStream_t s, int selfdot, const double* cond_after, const double* cond_before) {
-  int nb = dot_blocks(n);
-  int nt = nv + (selfdot ? 1 : 0);
-  if (nt <= 4) k_mdot<4><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, w, partial, selfdot, cond_after, cond_before);
-  else if (nt <= 8) k_mdot<8><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, w, partial, selfdot, cond_after, cond_before);
-  else if (nt <= 16) k_mdot<16><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, w, partial, selfdot, cond_after, cond_before);
-  else k_mdot<32><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, w, partial, selfdot, cond_after, cond_before);
-  MGD_LAUNCH_CHECK();
-  k_reduce_partials<<<nt, kThreads, 0, s>>>(partial, nb, nt, out);
-  MGD_LAUNCH_CHECK();
+// Modified Gram-Schmidt, one fused pass per basis vector (the orthogonalisation
+// the oracle uses, Saad's MGS-Arnoldi): step i reads the partial sums of
+// <v_i, w> left by the previous pass, forms h_i (every block reduces them in
+// the same fixed order, so all blocks agree bit for bit), updates
+// w -= h_i v_i and accumulates the partial sums of <v_{i+1}, w> -- or of
+// <w, w> after the last vector.  Two FP64 multiply-adds per element per basis
+// vector, which on this part's FP64 rate is what the orthogonalisation costs.
+__global__ void __launch_bounds__(kThreads) k_dot_partial(int n, const double* __restrict__ a,
+                                                          const double* __restrict__ b,
+                                                          double* __restrict__ partial) {
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += a[i] * b[i];
+  __shared__ double sh[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[k];
+    partial[blockIdx.x] = t;
+  }
 }
 
-// w -= sum_t h_t V_t, and partial norms of the new w.  Skipped when cond says
-// no second pass: then the norm partials carry the first pass's ||w||^2.
-template <int NV>
-__global__ void __launch_bounds__(kThreads) k_vupdate(int n, const double* __restrict__ V, long long ldv, int nv,
-                                                      const double* __restrict__ h, double* __restrict__ w,
-                                                      double* __restrict__ partial, const double* __restrict__ cond_after,
-                                                      const double* __restrict__ cond_before) {
-  if (!second_pass_needed(cond_after, cond_before)) {
-    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * kMaxV] = blockIdx.x == 0 ? cond_after[0] : 0.0;
-    return;
-  }
-  __shared__ double sh_h[NV];
-  for (int t = threadIdx.x; t < NV; t += blockDim.x) sh_h[t] = t < nv ? h[t] : 0.0;
+__device__ __forceinline__ double block_sum_partials(const double* __restrict__ partial, int nb) {
+  __shared__ double sh[kThreads];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[b];
+  sh[threadIdx.x] = s;
   __syncthreads();
-  double nrm = 0.0;
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kThreads) k_mgs_step(int n, const double* __restrict__ vi,
+                                                       const double* __restrict__ vnext, double* __restrict__ w,
+                                                       const double* __restrict__ pin, int nb,
+                                                       double* __restrict__ pout, double* __restrict__ hout) {
+  const double h = block_sum_partials(pin, nb);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *hout = h;
+  double s = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double wi = w[i];
-#pragma unroll
-    for (int t = 0; t < NV; ++t)
-      if (t < nv) wi -= sh_h[t] * V[t * ldv + i];
+    double wi = w[i] - h * vi[i];
     w[i] = wi;
-    nrm += wi * wi;
+    s += (vnext ? vnext[i] : wi) * wi;
   }
   __shared__ double sh[kThreads / 32];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nrm;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < kThreads / 32; ++k) s += sh[k];
-    partial[(size_t)blockIdx.x * kMaxV] = s;
+    double t = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[k];
+    pout[blockIdx.x] = t;
   }
 }
 
-void launch_vupdate(int n, const double* V, long long ldv, int nv, const double* h, double* w, double* partial,
-                    double* nrm2, cudaStream_t s, const double* cond_after, const double* cond_before) {
-  int nb = dot_blocks(n);
-  if (nv <= 4) k_vupdate<4><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, h, w, partial, cond_after, cond_before);
-  else if (nv <= 8) k_vupdate<8><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, h, w, partial, cond_after, cond_before);
-  else if (nv <= 16) k_vupdate<16><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, h, w, partial, cond_after, cond_before);
-  else k_vupdate<32><<<nb, kThreads, 0, s>>>(n, V, ldv, nv, h, w, partial, cond_after, cond_before);
+__global__ void k_sum_partials(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  double r = block_sum_partials(partial, nb);
+  if (threadIdx.x == 0) *out = r;
+}
+
+// h[0..nv-1] = Gram-Schmidt coefficients of w against V[:, 0..nv-1] (in order),
+// w orthogonalised in place, *nrm2 = ||w||^2.  pa / pb: partial buffers of
+// kDotBlocks entries each (ping-pong).
+void launch_mgs(int n, const double* V, long long ldv, int nv, double* w, double* h, double* nrm2, double* pa,
+                double* pb, cudaStream_t s) {
+  int nb = std::min(kDotBlocks, std::max(1, cdiv(n, kThreads)));
+  k_dot_partial<<<nb, kThreads, 0, s>>>(n, V, w, pa);
   MGD_LAUNCH_CHECK();
-  k_reduce_partials<<<1, kThreads, 0, s>>>(partial, nb, 1, nrm2);
+  double* pin = pa;
+  double* pout = pb;
+  for (int i = 0; i < nv; ++i) {
+    const double* vnext = i + 1 < nv ? V + (long long)(i + 1) * ldv : nullptr;
+    k_mgs_step<<<nb, kThreads, 0, s>>>(n, V + (long long)i * ldv, vnext, w, pin, nb, pout, h + i);
+    MGD_LAUNCH_CHECK();
+    std::swap(pin, pout);
+  }
+  k_sum_partials<<<1, kThreads, 0, s>>>(pin, nb, nrm2);
   MGD_LAUNCH_CHECK();
 }
 

@@ -11,6 +11,8 @@
 #include "mgd_internal.cuh"
 #include "row_dot.cuh"
 
+#include <cooperative_groups.h>
+
 namespace mgd {
 
 // ---------------------------------------------------------------- V-cycle phases
@@ -139,5 +141,138 @@ void launch_phase(int phase, int fmtA, int fmtRP, const LDesc<T>* d_descs, int n
 
 template void launch_phase<double>(int, int, int, const LDesc<double>*, int, int, cudaStream_t);
 template void launch_phase<float>(int, int, int, const LDesc<float>*, int, int, cudaStream_t);
+
+// ---------------------------------------------------------------- fused coarse levels
+// All levels from the first fused level down to the coarsest, and back up,
+// in one launch: one thread-block cluster per subsystem, the phases separated
+// by the cluster's hardware barrier (release / acquire at cluster scope).
+// Vectors written inside the kernel are read through L2 (__ldcg); matrices,
+// which are read-only here, through the read-only path.  Rows are handled by
+// groups of 4 lanes; every warp runs the same number of row steps so that the
+// shuffles and barriers are reached by all threads.
+namespace cg = cooperative_groups;
+
+constexpr int kTailTpr = 4;
+
+template <typename T, bool MUT>
+__device__ __forceinline__ T tail_load(const T* p) {
+  if (MUT) return __ldcg(p);
+  return __ldg(p);
+}
+
+// sum_p a_ip x_{ci_p} over one CSR row, by a group of kTailTpr lanes
+template <typename T>
+__device__ __forceinline__ T tail_row(const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ v,
+                                      const T* x, int row, int lane, bool valid) {
+  T s = T(0);
+  if (valid) {
+    int b = __ldg(rp + row), e = __ldg(rp + row + 1);
+    for (int p = b + lane; p < e; p += kTailTpr) s += __ldg(v + p) * __ldcg(x + __ldg(ci + p));
+  }
+#pragma unroll
+  for (int o = kTailTpr / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) k_vtail(const TailSub<T>* __restrict__ subs) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int cs = (int)cl.num_blocks();
+  const TailSub<T> S = subs[blockIdx.x / cs];
+  const int rank = (int)cl.block_rank();
+  const int lane = threadIdx.x % kTailTpr;
+  const int gwarp = rank * (kTailThreads / 32) + (int)(threadIdx.x >> 5);
+  const int nwarps = cs * (kTailThreads / 32);
+  constexpr int kRowsPerWarp = 32 / kTailTpr;
+  const int wrow = (threadIdx.x & 31) / kTailTpr;
+  // rows r = step * nwarps * 8 + gwarp * 8 + wrow, the same step count for every warp
+  auto for_rows = [&](int nrows, auto&& body) {
+    int steps = (nrows + nwarps * kRowsPerWarp - 1) / (nwarps * kRowsPerWarp);
+    for (int st = 0; st < steps; ++st) {
+      int r = (st * nwarps + gwarp) * kRowsPerWarp + wrow;
+      body(r, r < nrows);
+    }
+  };
+  const int L = S.nlev;
+  for (int k = 0; k < L - 1; ++k) {
+    const LDesc<T>* d = S.lev + k;
+    const int n = d->n, nc = d->nc;
+    // pre-smoothing from zero + residual: xt = D^-1 b, r = b - (A D^-1) b
+    for_rows(n, [&](int r, bool ok) {
+      T s = tail_row<T>(d->rp, d->ci, d->vpre, d->b, r, lane, ok);
+      if (ok && lane == 0) {
+        T bi = __ldcg(d->b + r);
+        d->xt[r] = __ldg(d->dinv + r) * bi;
+        d->r[r] = bi - s;
+      }
+    });
+    cl.sync();
+    for_rows(nc, [&](int r, bool ok) {  // restriction
+      T s = tail_row<T>(d->rrp, d->rci, d->rv, d->r, r, lane, ok);
+      if (ok && lane == 0) d->bc[r] = s;
+    });
+    cl.sync();
+  }
+  {
+    const LDesc<T>* d = S.lev + (L - 1);
+    if (S.coarse_lu) {  // x = A_L^{-1} b, one warp per row
+      const int n = d->cn;
+      for (int i = gwarp; i < n; i += nwarps) {
+        const double* row = d->cinv + (size_t)i * n;
+        double s = 0.0;
+        for (int j = threadIdx.x & 31; j < n; j += 32) s += __ldg(row + j) * (double)__ldcg(d->b + j);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) d->x[i] = (T)s;
+      }
+    } else {  // two l1-Jacobi sweeps from zero
+      const int n = d->n;
+      for (int i = rank * kTailThreads + threadIdx.x; i < n; i += cs * kTailThreads)
+        d->xt[i] = __ldg(d->dinv + i) * __ldcg(d->b + i);
+      cl.sync();
+      for_rows(n, [&](int r, bool ok) {
+        T s = tail_row<T>(d->rp, d->ci, d->v, d->xt, r, lane, ok);
+        if (ok && lane == 0) d->x[r] = __ldcg(d->xt + r) + __ldg(d->dinv + r) * (__ldcg(d->b + r) - s);
+      });
+    }
+  }
+  cl.sync();
+  for (int k = L - 2; k >= 0; --k) {
+    const LDesc<T>* d = S.lev + k;
+    const int n = d->n;
+    for_rows(n, [&](int r, bool ok) {  // prolongation
+      T s = tail_row<T>(d->prp, d->pci, d->pv, d->xc, r, lane, ok);
+      if (ok && lane == 0) d->xt[r] = __ldcg(d->xt + r) + s;
+    });
+    cl.sync();
+    for_rows(n, [&](int r, bool ok) {  // post-smoothing
+      T s = tail_row<T>(d->rp, d->ci, d->v, d->xt, r, lane, ok);
+      if (ok && lane == 0) d->x[r] = __ldcg(d->xt + r) + __ldg(d->dinv + r) * (__ldcg(d->b + r) - s);
+    });
+    cl.sync();
+  }
+}
+
+template <typename T>
+void launch_vtail(const TailSub<T>* d_subs, int nsub, int cs, cudaStream_t s) {
+  if (nsub <= 0) return;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nsub * cs, 1, 1);
+  cfg.blockDim = dim3(kTailThreads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  MGD_CUDA(cudaLaunchKernelEx(&cfg, k_vtail<T>, d_subs));
+  MGD_LAUNCH_CHECK();
+}
+
+template void launch_vtail<double>(const TailSub<double>*, int, int, cudaStream_t);
+template void launch_vtail<float>(const TailSub<float>*, int, int, cudaStream_t);
 
 }  // namespace mgd

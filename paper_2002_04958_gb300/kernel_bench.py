@@ -30,6 +30,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--applies", type=int, default=5)
     ap.add_argument("--timing", type=int, default=1, help="0: no CUDA events (for profiler runs)")
+    ap.add_argument("--solve", action="store_true", help="also time one full solve by kernel class")
     args = ap.parse_args()
 
     import torch
@@ -53,8 +54,39 @@ def main():
             nl, ms, by = slv.profile_read(cls)
             out[name] = {"launches": nl, "ms": round(ms, 4), "GB": round(by / 1e9, 4),
                          "GBps": round(by / (ms * 1e-3) / 1e9, 1) if ms > 0 else None}
+        per = {}
+        for lvl in range(40):
+            row = []
+            for ph in range(4):
+                nl, ms, by = slv.profile_read(16 + 4 * lvl + ph)
+                row.append(round(ms / max(args.applies, 1) * 1e3, 1))
+            nl, ms, by = slv.profile_read(400 + lvl)
+            row.append(round(ms / max(args.applies, 1) * 1e3, 1))
+            if any(row):
+                per[lvl] = row
+        nl, ms, by = slv.profile_read(15)
+        out["per_level_us_per_apply"] = {"columns": ["pre", "restrict", "prolong", "post", "coarse"], **per,
+                                         "fused_tail": round(ms / max(args.applies, 1) * 1e3, 1)}
+        slv.profile(0)
+    if args.solve and not args.timing:
+        slv.solve(v, tol=1e-8, allow_noconv=True)
+    if args.solve and args.timing:
+        import time
+        slv.profile(-1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, it, rr, rc = slv.solve(v, tol=1e-8, allow_noconv=True)
+        wall = (time.perf_counter() - t0) * 1e3
+        cls = {}
+        for k, name in [(0, "vcycle_level0"), (1, "vcycle_all"), (2, "spmv"), (3, "arnoldi"), (4, "block_updates")]:
+            nl, ms, by = slv.profile_read(k)
+            cls[name] = {"launches": nl, "ms": round(ms, 3), "GBps": round(by / (ms * 1e-3) / 1e9, 1) if ms > 0 else None}
+        busy = sum(cls[k]["ms"] for k in ["vcycle_all", "spmv", "arnoldi", "block_updates"])
+        out["solve"] = {"iters": it, "wall_ms": round(wall, 3), "kernel_ms": round(busy, 3),
+                        "idle_ms": round(wall - busy, 3), "classes": cls}
         slv.profile(0)
     st = slv.stats()
+    out["plan"] = slv.plan()
     out["vcycle_bytes_per_apply"] = st["vcycle_bytes"]
     out["levels"] = st["max_levels_used"]
     print(json.dumps(out))

@@ -24,7 +24,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOCONV", 3: "EBREAKDOWN", 4: "ESINGULAR", 5
 ENTRY_POINTS = ["mgd_opts_default", "mgd_create", "mgd_setup", "mgd_update_values", "mgd_solve", "mgd_solve_host",
                 "mgd_solve_transpose", "mgd_grad_values", "mgd_precond_apply", "mgd_get_stats", "mgd_get_history",
                 "mgd_op_info", "mgd_level_info", "mgd_level_export", "mgd_block_vector", "mgd_coupling_dropped",
-                "mgd_profile_enable", "mgd_profile_read", "mgd_kernel_launches", "mgd_last_error", "mgd_destroy",
+                "mgd_profile_enable", "mgd_profile_read", "mgd_kernel_launches", "mgd_last_error", "mgd_destroy", "mgd_plan_info",
                 "mgd_relres_noalloc"]
 
 
@@ -35,7 +35,8 @@ class MgdOpts(C.Structure):
                 ("nvcyc_E", C.c_int), ("nvcyc_I", C.c_int), ("nvcyc_other", C.c_int),
                 ("jacobi_sweeps", C.c_int), ("adaptive", C.c_int), ("seed", C.c_ulonglong),
                 ("restart", C.c_int), ("max_it", C.c_int), ("precision", C.c_int), ("batched", C.c_int),
-                ("use_graph", C.c_int), ("autotune", C.c_int), ("keep_transpose", C.c_int)]
+                ("use_graph", C.c_int), ("autotune", C.c_int), ("keep_transpose", C.c_int),
+                ("fuse_rows", C.c_int)]
 
 
 class MgdStats(C.Structure):
@@ -83,6 +84,7 @@ def lib():
             "mgd_profile_read": (I, [P, I, pLL, pD, pD]),
             "mgd_kernel_launches": (C.c_longlong, []),
             "mgd_relres_noalloc": (I, [I, P, P, P, P, P, P, P]),
+            "mgd_plan_info": (I, [P, I, I, pI, pI, pI, pI, pI, pI, pI, pI]),
             "mgd_last_error": (C.c_char_p, [P]),
             "mgd_destroy": (None, [P]),
         }
@@ -265,6 +267,24 @@ class Solver:
         out = dict(n=n, rp=rp, ci=ci[:nnz], v=v[:nnz], nc=ncoarse.value)
         if nnzp:
             out.update(cf=cf[:n], prp=prp, pci=pci[:nnzp], pv=pv[:nnzp])
+        return out
+
+    def plan(self):
+        """Autotuned launch plan: one list of per-level dicts per V-cycle batch."""
+        out = []
+        nb = C.c_int()
+        v = [C.c_int() for _ in range(7)]  # depth, nsub, maxrows, fmtA, fmtR, fmtP, tail
+        if lib().mgd_plan_info(self.h, 0, 0, C.byref(nb), *[C.byref(x) for x in v]) != 0:
+            return out
+        for b in range(nb.value):
+            lib().mgd_plan_info(self.h, b, 0, C.byref(nb), *[C.byref(x) for x in v])
+            depth, tail = v[0].value, v[6].value
+            levels = []
+            for l in range(depth):
+                lib().mgd_plan_info(self.h, b, l, C.byref(nb), *[C.byref(x) for x in v])
+                levels.append(dict(nsub=v[1].value, maxrows=v[2].value, fmtA=v[3].value, fmtR=v[4].value,
+                                   fmtP=v[5].value))
+            out.append(dict(depth=depth, tail=tail, levels=levels))
         return out
 
     def block_vector(self, which, comp, comp2=0):

@@ -145,6 +145,39 @@ def test_batched_and_graph_identical(gpu, kind):
         assert torch.equal(x, xr), opts
 
 
+@pytest.mark.parametrize("kind,prec", [("amg", 0), ("schur1", 0), ("schur2", 1), ("bd", 0)])
+@pytest.mark.parametrize("case", [CASES[0], CASES[3], CASES[4]], ids=["G1", "G20", "G2_3d"])
+def test_fused_coarse_levels(gpu, orc, kind, prec, case):
+    # every level below level 0 in the cluster kernel vs per-level launches
+    s = _system(case)
+    v = torch.from_numpy(np.random.default_rng(7).standard_normal(s.n))
+    ref = gpu.Solver(autotune=0, precision=prec, fuse_rows=-1, batched=1).setup_system(s, kind)
+    fus = gpu.Solver(autotune=0, precision=prec, fuse_rows=1 << 30, batched=1, use_graph=1).setup_system(s, kind)
+    assert all(b["tail"] == 1 for b in fus.plan() if b["depth"] > 1)
+    z0 = ref.precond_apply(v).cpu().numpy()
+    z1 = fus.precond_apply(v).cpu().numpy()
+    tol = 1e-12 if prec == 0 else 1e-5
+    assert np.linalg.norm(z1 - z0) <= tol * np.linalg.norm(z0)
+    if prec == 0:
+        Ao = orc.csr_of_system(s)
+        zo = orc.Block(Ao, s.G, s.N, kind).apply(v.numpy())
+        assert np.linalg.norm(z1 - zo) <= 1e-12 * np.linalg.norm(zo)
+    x1, it1, rr1, _ = fus.solve(torch.from_numpy(s.b))
+    x0, it0, rr0, _ = ref.solve(torch.from_numpy(s.b))
+    assert abs(it1 - it0) <= (0 if prec == 0 else 1) and rr1 <= 1e-8
+
+
+def test_fused_coarse_levels_transposed(gpu):
+    s = _system(CASES[2])
+    ref = gpu.Solver(autotune=0, keep_transpose=1, fuse_rows=-1).setup_system(s, "amg")
+    fus = gpu.Solver(autotune=0, keep_transpose=1, fuse_rows=1 << 30).setup_system(s, "amg")
+    g = torch.from_numpy(np.random.default_rng(8).standard_normal(s.n))
+    l0, it0, _ = ref.solve_transpose(g)
+    l1, it1, _ = fus.solve_transpose(g)
+    assert it0 == it1
+    assert torch.linalg.vector_norm(l1 - l0) <= 1e-10 * torch.linalg.vector_norm(l0)
+
+
 def test_adaptive_drops_match_oracle(gpu, orc):
     s = _system(CASES[2])
     for kind in ["schur1", "schur2", "pctl"]:
