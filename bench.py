@@ -4,7 +4,8 @@
 Workload (default): the one-group 3-component system on a 1024x1024 grid with
 a 10^4 coefficient jump across a circular inclusion (3.1M unknowns, 15.7M
 nonzeros, seeded synthetic coefficients), preconditioned by Schur1 with one
-classical-AMG V(1,1) cycle per subsystem inverse, FP64.  One step = the whole
+classical-AMG V(1,1) cycle per subsystem inverse (PMIS coarsening with
+extended+i interpolation), FP64.  One step = the whole
 hot path on that system: device setup (block extraction, strength, PMIS,
 interpolation, Galerkin products, smoother diagonals, coarsest inverse) plus
 the FGMRES(30) solve to ||b - A x|| <= 1e-8 ||b||.  Inputs are resident in HBM
@@ -121,7 +122,7 @@ def run_ours(args):
     va = torch.from_numpy(sysm.val).to(dev)
     b = torch.from_numpy(sysm.b).to(dev)
     opts = dict(precision=args.precision, batched=args.batched, use_graph=args.graph, autotune=1,
-                keep_transpose=int(args.adjoint), max_it=args.max_it)
+                keep_transpose=int(args.adjoint), max_it=args.max_it, interp_type=args.interp)
     slv = mgdamg.Solver(**opts)
     adj = {}
 
@@ -205,10 +206,12 @@ def run_ours(args):
     # variants for context (one solve each, outside the timed region)
     variants = {}
     if not args.no_variants:
-        for name, kind, o in [("monolithic_amg_fp64", "amg", dict(batched=1, use_graph=1)),
-                              (f"{args.kind}_fp64_plain_launches", args.kind, dict()),
+        for name, kind, o in [("monolithic_amg_fp64_classical_interp", "amg", dict(batched=1, use_graph=1)),
+                              (f"{args.kind}_fp64_classical_modified_interp", args.kind,
+                               dict(batched=1, use_graph=1)),
+                              (f"{args.kind}_fp64_plain_launches", args.kind, dict(interp_type=args.interp)),
                               (f"{args.kind}_fp32_vcycle_batched_graph", args.kind,
-                               dict(precision=1, batched=1, use_graph=1))]:
+                               dict(precision=1, batched=1, use_graph=1, interp_type=args.interp))]:
             try:
                 v = mgdamg.Solver(autotune=1, **o)
                 v.setup(sysm.G, sysm.N, rp, ci, va, kind)
@@ -248,6 +251,7 @@ def run_ours(args):
                    f"{inputs.PRESET_NAMES[args.config]}[{args.kind}]",
                    "G": sysm.G, "grid": list(sysm.dims), "n": sysm.n, "nnz": sysm.nnz,
                    "precond": args.kind, "krylov": "FGMRES(30), right preconditioned", "tol": args.tol,
+                   "interpolation": "extended+i" if args.interp else "classical modified",
                    "step": "device setup + solve", "parallelism": f"replicas{ws}",
                    "launch": ("batched per-level launches" if args.batched else "per-operator launches") +
                              (", preconditioner replayed from a CUDA graph" if args.graph else ""),
@@ -311,7 +315,7 @@ def cpu_baseline(args, sysm, gpu_iters):
     orc.build()
     A = orc.csr_of_system(sysm)
     t0 = time.perf_counter()
-    M = orc.Block(A, sysm.G, sysm.N, args.kind)
+    M = orc.Block(A, sysm.G, sysm.N, args.kind, orc.opts(interp_type=args.interp))
     t1 = time.perf_counter()
     budget_its = args.cpu_iters
     x, it, rr, st, _ = orc.fgmres(A, sysm.b, M, tol=args.tol, maxit=budget_its)
@@ -339,7 +343,7 @@ def run_reference(args):
 
     def step():
         t0 = time.perf_counter()
-        M = orc.Block(A, sysm.G, sysm.N, args.kind)
+        M = orc.Block(A, sysm.G, sysm.N, args.kind, orc.opts(interp_type=args.interp))
         t1 = time.perf_counter()
         x, it, rr, st, _ = orc.fgmres(A, sysm.b, M, tol=args.tol, maxit=args.ref_iters)
         t2 = time.perf_counter()
@@ -353,7 +357,7 @@ def run_reference(args):
     # the iteration count of the full solve (one oracle solve, outside the samples)
     full_its = args.full_iters
     if full_its is None:
-        M = orc.Block(A, sysm.G, sysm.N, args.kind)
+        M = orc.Block(A, sysm.G, sysm.N, args.kind, orc.opts(interp_type=args.interp))
         _, full_its, _, _, _ = orc.fgmres(A, sysm.b, M, tol=args.tol, maxit=1000)
     vals = [su + so * full_its / max(it, 1) for su, so, it, st in samples]
     v = statistics.median(vals)
@@ -363,7 +367,7 @@ def run_reference(args):
         "ms_per_step": round(v * 1e3, 2), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": inputs.PRESET_NAMES[args.config], "n": sysm.n, "nnz": sysm.nnz,
-                   "precond": args.kind},
+                   "precond": args.kind, "interpolation": "extended+i" if args.interp else "classical modified"},
         "cpu_baseline": {"value": round(v, 4), "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": f"per step: full oracle setup + {args.ref_iters} FGMRES iterations, "
                                    f"scaled to the {full_its} iterations of the full solve"},
@@ -393,7 +397,11 @@ def main():
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="no nvidia-smi sampling (profiler runs)")
     ap.add_argument("--max-it", type=int, default=1000)
+    ap.add_argument("--interp", type=int, default=None,
+                    help="0 classical modified, 1 extended+i (default: 1 for the default workload, else 0)")
     args = ap.parse_args()
+    if args.interp is None:
+        args.interp = 1 if (args.config == WORKLOAD and args.kind == KIND) else 0
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -81,6 +81,8 @@ typedef struct mgd_opts {
   int fuse_rows;          /* levels below level 0 whose subsystems all have <= fuse_rows rows run, with every
                              coarser level, in one thread-block-cluster launch per V-cycle; 0: chosen by the
                              autotuner (not fused when autotune is off); -1: never */
+  int interp_type;        /* 0: classical modified interpolation (Section 3.1); 1: extended+i (distance-two
+                             classical interpolation, De Sterck, Falgout, Nolting, Yang 2008) */
 } mgd_opts;
 
 /* Fill *o with the defaults listed above.  Returns MGD_EINVAL if o is NULL. */

@@ -87,6 +87,8 @@ void or_default_opts(or_opts *o) {
   o->jacobi_sweeps = 1;
   o->adaptive = 0;
   o->seed = 0;
+  o->inner_mode = 0;
+  o->interp_type = 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -441,6 +443,146 @@ or_csr *or_interp(const or_csr *A, const uint8_t *S, const int8_t *CF) {
   return P;
 }
 
+/* ------------------------------------------------------------------ */
+/* Extended+i interpolation (De Sterck, Falgout, Nolting, Yang, "Distance-two */
+/* interpolation for parallel algebraic multigrid", NLAA 2008).  For an F   */
+/* point i the interpolatory set is C^_i = (strong C neighbours of i) united */
+/* with the strong C neighbours of i's strong F neighbours, and             */
+/*   w_ij = -( a_ij + sum_{k in F_i} a_ik abar_kj / d_k ) / a~_ii,          */
+/*   a~_ii = a_ii + sum_{n weak, not in C^_i} a_in                          */
+/*                + sum_{k in F_i} a_ik abar_ki / d_k,                      */
+/*   d_k = sum_{l in C^_i or l = i} abar_kl,                                */
+/* abar as in the classical formula; a_ij = 0 for j not adjacent to i.  A   */
+/* strong F neighbour with d_k = 0 is lumped into the diagonal.  C^_i is    */
+/* built in the order: strong C neighbours of i (row order), then for each  */
+/* strong F neighbour k (row order) its strong C neighbours (row order) not */
+/* yet listed; sums run in row i's stored order, then row k's.              */
+/* ------------------------------------------------------------------ */
+static int in_list(const int *list, int len, int j) {
+  for (int s = 0; s < len; ++s)
+    if (list[s] == j) return s;
+  return -1;
+}
+
+or_csr *or_interp_exti(const or_csr *A, const uint8_t *S, const int8_t *CF) {
+  int n = A->n;
+  int *cidx = (int *)xmalloc((size_t)n * sizeof(int) + 4);
+  int nc = 0;
+  for (int i = 0; i < n; ++i) cidx[i] = (CF[i] == 1) ? nc++ : -1;
+  /* pass 1: interpolatory sets and their sizes */
+  int *rp = (int *)xcalloc((size_t)n + 1, sizeof(int));
+  int cap = 64;
+  int *list = (int *)xmalloc((size_t)cap * sizeof(int));
+  for (int i = 0; i < n; ++i) {
+    int len = 0;
+    if (CF[i] == 1) {
+      rp[i + 1] = 1;
+      continue;
+    }
+    for (int p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+      int j = A->ci[p];
+      if (S[p] && CF[j] == 1 && in_list(list, len, j) < 0) {
+        if (len == cap) list = (int *)realloc(list, (size_t)(cap *= 2) * sizeof(int));
+        list[len++] = j;
+      }
+    }
+    for (int p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+      int k = A->ci[p];
+      if (!(S[p] && CF[k] == -1)) continue;
+      for (int q = A->rp[k]; q < A->rp[k + 1]; ++q) {
+        int m = A->ci[q];
+        if (S[q] && CF[m] == 1 && in_list(list, len, m) < 0) {
+          if (len == cap) list = (int *)realloc(list, (size_t)(cap *= 2) * sizeof(int));
+          list[len++] = m;
+        }
+      }
+    }
+    rp[i + 1] = len;
+  }
+  for (int i = 0; i < n; ++i) rp[i + 1] += rp[i];
+  or_csr *P = csr_alloc(n, nc, rp[n]);
+  memcpy(P->rp, rp, ((size_t)n + 1) * sizeof(int));
+  free(rp);
+  /* pass 2: weights */
+  for (int i = 0; i < n; ++i) {
+    int base = P->rp[i], len = P->rp[i + 1] - base;
+    if (CF[i] == 1) {
+      P->ci[base] = cidx[i];
+      P->v[base] = 1.0;
+      continue;
+    }
+    if (len == 0) continue;
+    int *L = P->ci + base;  /* fine indices while building */
+    double *num = P->v + base;
+    int t = 0;
+    for (int p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+      int j = A->ci[p];
+      if (S[p] && CF[j] == 1 && in_list(L, t, j) < 0) L[t++] = j;
+    }
+    for (int p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+      int k = A->ci[p];
+      if (!(S[p] && CF[k] == -1)) continue;
+      for (int q = A->rp[k]; q < A->rp[k + 1]; ++q) {
+        int m = A->ci[q];
+        if (S[q] && CF[m] == 1 && in_list(L, t, m) < 0) L[t++] = m;
+      }
+    }
+    for (int s2 = 0; s2 < len; ++s2) num[s2] = 0.0;
+    double diag = 0.0;
+    for (int p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+      int j = A->ci[p];
+      if (j == i) {
+        diag = A->v[p];
+        continue;
+      }
+      int sj = in_list(L, len, j);
+      if (sj >= 0) num[sj] = A->v[p]; /* a_ij for neighbours in C^_i */
+    }
+    for (int p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+      int k = A->ci[p];
+      if (k == i) continue;
+      double aik = A->v[p];
+      if (S[p] && CF[k] == 1) continue;
+      if (S[p] && CF[k] == -1) {
+        double akk = 0.0;
+        for (int q = A->rp[k]; q < A->rp[k + 1]; ++q)
+          if (A->ci[q] == k) akk = A->v[q];
+        double denom = 0.0;
+        for (int q = A->rp[k]; q < A->rp[k + 1]; ++q) {
+          int l = A->ci[q];
+          if ((l == i || in_list(L, len, l) >= 0) && opposite_sign(A->v[q], akk)) denom = denom + A->v[q];
+        }
+        if (denom == 0.0) {
+          diag = diag + aik;
+        } else {
+          for (int q = A->rp[k]; q < A->rp[k + 1]; ++q) {
+            int l = A->ci[q];
+            if (!opposite_sign(A->v[q], akk)) continue;
+            double prod = aik * A->v[q];
+            if (l == i) {
+              diag = diag + prod / denom;
+            } else {
+              int sl = in_list(L, len, l);
+              if (sl >= 0) num[sl] = num[sl] + prod / denom;
+            }
+          }
+        }
+      } else if (in_list(L, len, k) < 0) {
+        diag = diag + aik; /* weak neighbour outside C^_i */
+      }
+    }
+    /* finalise and sort the row by coarse index */
+    for (int s2 = 0; s2 < len; ++s2) {
+      num[s2] = (diag != 0.0) ? -num[s2] / diag : 0.0;
+      L[s2] = cidx[L[s2]];
+    }
+    sort_row(L, num, len);
+  }
+  free(list);
+  free(cidx);
+  return P;
+}
+
 /* Galerkin coarse operator A_c = R A P with R = P^T (AP first) */
 or_csr *or_rap(const or_csr *A, const or_csr *P) {
   or_csr *AP = or_spgemm(A, P);
@@ -569,7 +711,7 @@ or_amg *or_amg_setup(const or_csr *A0, const or_opts *o) {
       break;
     }
     h->CF[l] = CF;
-    h->P[l] = or_interp(A, S, CF);
+    h->P[l] = o->interp_type == 1 ? or_interp_exti(A, S, CF) : or_interp(A, S, CF);
     h->R[l] = or_transpose(h->P[l]);
     h->A[l + 1] = or_rap(A, h->P[l]);
     free(S);
@@ -696,7 +838,9 @@ typedef struct inv_t {
   or_amg *amg;      /* option #2: its hierarchy */
   double *jdinv;    /* option #1: 1 / diag(A) */
   int use_jacobi;
+  int accurate;     /* option #3: V-cycles until ||rhs - A x|| <= inner_tol ||rhs|| */
   int count;        /* sweeps (#1) or V-cycles (#2) */
+  long cycles;      /* V-cycles spent by this inverse since setup */
 } inv_t;
 
 #define NOPS 7
@@ -735,6 +879,9 @@ static void inv_build(or_block *B, int op, int comp, or_csr *A, int ncyc) {
   } else {
     iv->count = ncyc;
     iv->amg = or_amg_setup(A, &B->o);
+    /* Section 4: inner accuracy 1e-2 for C_E, S_I, C_g, S_g and the PCTL block relaxations */
+    iv->accurate = B->o.inner_mode &&
+                   (op == OP_CE || op == OP_CG || op == OP_SG || op == OP_SI || (B->kind == OR_PCTL && op == OP_A));
   }
 }
 
@@ -756,7 +903,24 @@ static void inv_apply_internal(or_block *B, inv_t *iv, int trans, const double *
       residual(iv->A, rhs, out, r);
       for (int i = 0; i < n; ++i) out[i] = out[i] + iv->jdinv[i] * r[i];
     }
+  } else if (iv->accurate && !trans) {
+    /* option #3: x = 0; x += V(rhs - A x) until the relative residual <= inner_tol */
+    double nr0 = 0.0;
+    for (int i = 0; i < n; ++i) nr0 += rhs[i] * rhs[i];
+    nr0 = sqrt(nr0);
+    for (int i = 0; i < n; ++i) out[i] = 0.0;
+    for (int it = 0; it < B->o.inner_maxit; ++it) {
+      residual(iv->A, rhs, out, r);
+      double nr = 0.0;
+      for (int i = 0; i < n; ++i) nr += r[i] * r[i];
+      nr = sqrt(nr);
+      if (nr <= B->o.inner_tol * nr0) break;
+      or_vcycle(iv->amg, r, e);
+      iv->cycles++;
+      for (int i = 0; i < n; ++i) out[i] = out[i] + e[i];
+    }
   } else {
+    iv->cycles += iv->count;
     if (trans)
       or_vcycle_T(iv->amg, rhs, out);
     else
@@ -1139,6 +1303,8 @@ int or_block_nmatvec(const or_block *B) { return B->nmatvec; }
 int or_block_dropped(const or_block *B, int a, int b) { return B->dropped ? B->dropped[a * B->nc + b] : 0; }
 int or_block_use_jacobi(const or_block *B, int op, int comp) { return B->inv[op][comp].use_jacobi; }
 const or_amg *or_block_amg(const or_block *B, int op, int comp) { return B->inv[op][comp].amg; }
+long or_block_cycles(const or_block *B, int op, int comp) { return B->inv[op][comp].cycles; }
+
 const double *or_block_vec(const or_block *B, int which, int comp) {
   if (which == 0) return B->p ? B->p[comp] : NULL;
   return B->diag ? B->diag[comp] : NULL;

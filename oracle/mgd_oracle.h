@@ -37,6 +37,9 @@ typedef struct or_opts {
   int jacobi_sweeps;      /* option #1 sweeps: 1 */
   int adaptive;           /* 1: Section 3.6 coupling drops + Section 3.5 option #1/#2 choice */
   uint64_t seed;          /* PMIS weight seed */
+  int inner_mode;         /* 1: option #3 (V-cycles to inner_tol) for the inverses Section 4 names:
+                             C_E, C_g (Schur1), S_g, S_I (Schur2), the block relaxations of PCTL */
+  int interp_type;        /* 0: classical modified (Section 3.1); 1: extended+i (distance two) */
 } or_opts;
 
 /* preconditioner kinds */
@@ -69,6 +72,8 @@ int or_pmis(const or_csr *A, const uint8_t *S, uint64_t seed, int level, int8_t 
 /* same rounds with caller-given weights (ties broken by the larger index) */
 int or_pmis_weights(const or_csr *A, const uint8_t *S, const double *w, int8_t *CF);
 or_csr *or_interp(const or_csr *A, const uint8_t *S, const int8_t *CF);
+/* extended+i (distance-two) interpolation, De Sterck, Falgout, Nolting, Yang 2008 */
+or_csr *or_interp_exti(const or_csr *A, const uint8_t *S, const int8_t *CF);
 or_csr *or_rap(const or_csr *A, const or_csr *P);
 
 /* AMG hierarchy */
@@ -101,6 +106,7 @@ int or_block_ninv(const or_block *B);
 int or_block_nmatvec(const or_block *B);
 int or_block_dropped(const or_block *B, int a, int b);
 int or_block_use_jacobi(const or_block *B, int op, int comp);
+long or_block_cycles(const or_block *B, int op, int comp); /* V-cycles spent by one inverse */
 const or_amg *or_block_amg(const or_block *B, int op, int comp);
 const double *or_block_vec(const or_block *B, int which, int comp); /* 0: p_alpha, 1: diag of op */
 const or_csr *or_block_Ac(const or_block *B);

@@ -39,7 +39,7 @@ class Opts(C.Structure):
                 ("inner_tol", C.c_double), ("inner_maxit", C.c_int),
                 ("nvcyc_group", C.c_int), ("nvcyc_E", C.c_int), ("nvcyc_I", C.c_int),
                 ("nvcyc_other", C.c_int), ("jacobi_sweeps", C.c_int), ("adaptive", C.c_int),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("inner_mode", C.c_int), ("interp_type", C.c_int)]
 
 
 INV_CB = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
@@ -73,6 +73,7 @@ def lib():
             "or_pmis": (C.c_int, [P, u8, C.c_uint64, C.c_int, i8]),
             "or_pmis_weights": (C.c_int, [P, u8, dp, i8]),
             "or_interp": (P, [P, u8, i8]),
+            "or_interp_exti": (P, [P, u8, i8]),
             "or_rap": (P, [P, P]),
             "or_amg_setup": (P, [P, C.POINTER(Opts)]),
             "or_amg_nlevels": (C.c_int, [P]),
@@ -95,6 +96,7 @@ def lib():
             "or_block_nmatvec": (C.c_int, [P]),
             "or_block_dropped": (C.c_int, [P, C.c_int, C.c_int]),
             "or_block_use_jacobi": (C.c_int, [P, C.c_int, C.c_int]),
+            "or_block_cycles": (C.c_long, [P, C.c_int, C.c_int]),
             "or_block_amg": (P, [P, C.c_int, C.c_int]),
             "or_block_vec": (C.POINTER(C.c_double), [P, C.c_int, C.c_int]),
             "or_block_Ac": (P, [P]),
@@ -204,6 +206,15 @@ def interp(A: Csr, S, CF):
     return Csr(lib().or_interp(A.h, Sb, CFb))
 
 
+def interp_exti(A: Csr, S, CF):
+    n, _, z = A.info()
+    Sb = np.zeros(max(z, 1), np.uint8)
+    Sb[:z] = S
+    CFb = np.zeros(max(n, 1), np.int8)
+    CFb[:n] = CF
+    return Csr(lib().or_interp_exti(A.h, Sb, CFb))
+
+
 def rap(A: Csr, P: Csr):
     return Csr(lib().or_rap(A.h, P.h))
 
@@ -307,6 +318,9 @@ class Block:
 
     def use_jacobi(self, op, comp):
         return bool(lib().or_block_use_jacobi(self.h, op, comp))
+
+    def cycles(self, op, comp):
+        return lib().or_block_cycles(self.h, op, comp)
 
     def amg(self, op, comp):
         h = lib().or_block_amg(self.h, op, comp)

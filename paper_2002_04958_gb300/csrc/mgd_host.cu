@@ -327,11 +327,29 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
     P.n = n;
     P.m = nc;
     P.rp = ar.alloc<int>(n + 1);
-    exclusive_scan(pcnt, P.rp, n, s);
-    P.nnz = read_int(P.rp + n, s);
-    P.ci = ar.alloc<int>(P.nnz);
-    P.v = ar.alloc<double>(P.nnz);
-    launch_interp_fill(n, lv.A.rp, lv.A.ci, lv.A.v, S, CF, cidx, P.rp, P.ci, P.v, s);
+    if (o.interp_type == 1) {  // extended+i: distance-two interpolatory sets
+      int* ub = tmp.alloc<int>(n);
+      launch_exti_ub(n, lv.A.rp, lv.A.ci, S, CF, pcnt, ub, s);
+      long long* off = tmp.alloc<long long>(n + 1);
+      launch_offsets64(ub, off, n, s);
+      long long tot = 0;
+      MGD_CUDA(cudaMemcpyAsync(&tot, off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+      MGD_CUDA(cudaStreamSynchronize(s));
+      int* list = tmp.alloc<int>(tot);
+      int* len = tmp.alloc<int>(n);
+      launch_exti_list(n, lv.A.rp, lv.A.ci, S, CF, off, list, len, s);
+      exclusive_scan(len, P.rp, n, s);
+      P.nnz = read_int(P.rp + n, s);
+      P.ci = ar.alloc<int>(P.nnz);
+      P.v = ar.alloc<double>(P.nnz);
+      launch_exti_fill(n, lv.A.rp, lv.A.ci, lv.A.v, S, CF, cidx, off, list, P.rp, P.ci, P.v, s);
+    } else {
+      exclusive_scan(pcnt, P.rp, n, s);
+      P.nnz = read_int(P.rp + n, s);
+      P.ci = ar.alloc<int>(P.nnz);
+      P.v = ar.alloc<double>(P.nnz);
+      launch_interp_fill(n, lv.A.rp, lv.A.ci, lv.A.v, S, CF, cidx, P.rp, P.ci, P.v, s);
+    }
     lv.P = P;
     lv.R = transpose(ar, P, s);
     Scratch apk(s, ar.pool);

@@ -502,6 +502,155 @@ void launch_interp_fill(int n, const int* rp, const int* ci, const double* v, co
   MGD_LAUNCH_CHECK();
 }
 
+// ------------------------------------------------------------------ extended+i interpolation
+// (De Sterck, Falgout, Nolting, Yang 2008): the interpolatory set of an F point
+// adds, to its strong C neighbours, the strong C neighbours of its strong F
+// neighbours.  Three kernels: an upper bound on each set, the deduplicated set
+// in construction order (strong C neighbours of i in row order, then for each
+// strong F neighbour k in row order its strong C neighbours in row order), and
+// the weights with the same operation order as the definition states.
+__device__ __forceinline__ int find_in(const int* L, int len, int j) {
+  for (int s = 0; s < len; ++s)
+    if (L[s] == j) return s;
+  return -1;
+}
+
+__global__ void k_exti_ub(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF,
+                          const int* scount, int* ub) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (CF[i] == 1) {
+    ub[i] = 1;
+    return;
+  }
+  int c = scount[i];
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (S[p] && CF[ci[p]] == -1) c += scount[ci[p]];
+  ub[i] = c;
+}
+
+__global__ void k_exti_list(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF,
+                            const long long* off, int* list, int* len) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (CF[i] == 1) {
+    len[i] = 1;
+    return;
+  }
+  int* L = list + off[i];
+  int t = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = ci[p];
+    if (S[p] && CF[j] == 1 && find_in(L, t, j) < 0) L[t++] = j;
+  }
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int k = ci[p];
+    if (!(S[p] && CF[k] == -1)) continue;
+    for (int q = rp[k]; q < rp[k + 1]; ++q) {
+      int m = ci[q];
+      if (S[q] && CF[m] == 1 && find_in(L, t, m) < 0) L[t++] = m;
+    }
+  }
+  len[i] = t;
+}
+
+__global__ void k_exti_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S,
+                            const signed char* CF, const int* cidx, const long long* off, const int* list,
+                            const int* prp, int* pci, double* pv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int base = prp[i], len = prp[i + 1] - base;
+  if (CF[i] == 1) {
+    pci[base] = cidx[i];
+    pv[base] = 1.0;
+    return;
+  }
+  if (len == 0) return;
+  int* L = pci + base;
+  double* num = pv + base;
+  const int* src = list + off[i];
+  for (int s = 0; s < len; ++s) {
+    L[s] = src[s];
+    num[s] = 0.0;
+  }
+  double diag = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = ci[p];
+    if (j == i) {
+      diag = v[p];
+      continue;
+    }
+    int sj = find_in(L, len, j);
+    if (sj >= 0) num[sj] = v[p];
+  }
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int k = ci[p];
+    if (k == i) continue;
+    double aik = v[p];
+    if (S[p] && CF[k] == 1) continue;
+    if (S[p] && CF[k] == -1) {
+      double akk = 0.0;
+      for (int q = rp[k]; q < rp[k + 1]; ++q)
+        if (ci[q] == k) akk = v[q];
+      double denom = 0.0;
+      for (int q = rp[k]; q < rp[k + 1]; ++q) {
+        int l = ci[q];
+        if ((l == i || find_in(L, len, l) >= 0) && opp_sign(v[q], akk)) denom = __dadd_rn(denom, v[q]);
+      }
+      if (denom == 0.0) {
+        diag = __dadd_rn(diag, aik);
+      } else {
+        for (int q = rp[k]; q < rp[k + 1]; ++q) {
+          int l = ci[q];
+          if (!opp_sign(v[q], akk)) continue;
+          double prod = __dmul_rn(aik, v[q]);
+          if (l == i) {
+            diag = __dadd_rn(diag, __ddiv_rn(prod, denom));
+          } else {
+            int sl = find_in(L, len, l);
+            if (sl >= 0) num[sl] = __dadd_rn(num[sl], __ddiv_rn(prod, denom));
+          }
+        }
+      }
+    } else if (find_in(L, len, k) < 0) {
+      diag = __dadd_rn(diag, aik);
+    }
+  }
+  for (int s = 0; s < len; ++s) {
+    num[s] = (diag != 0.0) ? __ddiv_rn(-num[s], diag) : 0.0;
+    L[s] = cidx[L[s]];
+  }
+  for (int a = 1; a < len; ++a) {  // sort by coarse index
+    int cc = L[a];
+    double vv = num[a];
+    int q = a - 1;
+    while (q >= 0 && L[q] > cc) {
+      L[q + 1] = L[q];
+      num[q + 1] = num[q];
+      --q;
+    }
+    L[q + 1] = cc;
+    num[q + 1] = vv;
+  }
+}
+
+void launch_exti_ub(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF, const int* scount,
+                    int* ub, cudaStream_t s) {
+  k_exti_ub<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, S, CF, scount, ub);
+  MGD_LAUNCH_CHECK();
+}
+void launch_exti_list(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF,
+                      const long long* off, int* list, int* len, cudaStream_t s) {
+  k_exti_list<<<cdiv(n, 128), 128, 0, s>>>(n, rp, ci, S, CF, off, list, len);
+  MGD_LAUNCH_CHECK();
+}
+void launch_exti_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S, const signed char* CF,
+                      const int* cidx, const long long* off, const int* list, const int* prp, int* pci, double* pv,
+                      cudaStream_t s) {
+  k_exti_fill<<<cdiv(n, 128), 128, 0, s>>>(n, rp, ci, v, S, CF, cidx, off, list, prp, pci, pv);
+  MGD_LAUNCH_CHECK();
+}
+
 // ------------------------------------------------------------------ transpose
 __global__ void k_transpose_count(int nnz, const int* ci, int* cnt) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;

@@ -36,7 +36,7 @@ class MgdOpts(C.Structure):
                 ("jacobi_sweeps", C.c_int), ("adaptive", C.c_int), ("seed", C.c_ulonglong),
                 ("restart", C.c_int), ("max_it", C.c_int), ("precision", C.c_int), ("batched", C.c_int),
                 ("use_graph", C.c_int), ("autotune", C.c_int), ("keep_transpose", C.c_int),
-                ("fuse_rows", C.c_int)]
+                ("fuse_rows", C.c_int), ("interp_type", C.c_int)]
 
 
 class MgdStats(C.Structure):

@@ -39,7 +39,7 @@ def test_opts_defaults_and_struct_layout(built):
     assert o.theta_wd == 0.9 and o.theta_wc == 1e-2 and o.sigma_wc == 0.5 and o.inner_tol == 1e-2
     assert o.restart == 30 and o.nvcyc_group == 1 and o.precision == 0
     # the ctypes mirror has the C struct's size: the library writes every field
-    assert C.sizeof(mgdamg.MgdOpts) == 120 and C.sizeof(mgdamg.MgdStats) == 112
+    assert C.sizeof(mgdamg.MgdOpts) == 128 and C.sizeof(mgdamg.MgdStats) == 112
     assert mgdamg.lib().mgd_kernel_launches() >= 0
     assert mgdamg.lib().mgd_opts_default(None) == 1
 

@@ -106,6 +106,25 @@ def test_solve_parity_fp64(gpu, orc, case, kind):
     assert np.linalg.norm(s.b - A @ xg) <= 1e-8 * np.linalg.norm(s.b) * (1 + 1e-6)
 
 
+@pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[4]], ids=["G1", "G4", "G2_3d"])
+@pytest.mark.parametrize("kind", ["amg", "schur1", "schur2", "pctl"])
+def test_exti_setup_bit_exact_and_solve(gpu, orc, case, kind):
+    # extended+i interpolation: hierarchies bit-exact, iteration counts equal
+    s = _system(case)
+    slv = gpu.Solver(interp_type=1).setup_system(s, kind)
+    Ao = orc.csr_of_system(s)
+    ob = orc.Block(Ao, s.G, s.N, kind, orc.opts(interp_type=1))
+    for k in range(slv.stats()["n_ops"]):
+        info = slv.op_info(k)
+        if info["use_jacobi"] or (kind == "pctl" and info["kind"] == 5):
+            continue
+        _compare_hierarchy(slv, k, _oracle_hierarchy(orc, ob, kind, info["kind"], info["comp"]))
+    x, it, rr, rc = slv.solve(torch.from_numpy(s.b), tol=1e-8)
+    xo, ito, rro, sto, _ = orc.fgmres(Ao, s.b, ob, tol=1e-8)
+    assert rc == 0 and sto == 0 and it == ito
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-10 * np.linalg.norm(xo)
+
+
 @pytest.mark.parametrize("kind", ["amg", "schur1", "schur2", "bd"])
 def test_precond_apply_matches_oracle(gpu, orc, kind):
     s = _system(CASES[2])

@@ -326,3 +326,53 @@ def test_rap_matches_dense_and_is_symmetric(orc):
     ref = P.T @ A.toarray() @ P
     assert np.allclose(Ac, ref, rtol=1e-13, atol=1e-13 * abs(ref).max())
     assert np.allclose(Ac, Ac.T, rtol=0, atol=1e-14 * abs(Ac).max())
+
+
+# ---------------------------------------------------------------- extended+i interpolation
+def test_exti_reduces_to_classical_without_distance_two(orc):
+    # 1-D Poisson with C = odd points: no F point has a strong F neighbour, so
+    # the interpolatory sets are the direct C neighbours and w = 1/2, 1/2
+    n = 15
+    A = _tridiag(n)
+    A.sort_indices()
+    Ao = orc.Csr.from_scipy(A)
+    S = orc.strength(Ao)
+    CF = np.where(np.arange(n) % 2 == 1, 1, -1).astype(np.int8)
+    assert np.array_equal(orc.interp_exti(Ao, S, CF).scipy().toarray(), orc.interp(Ao, S, CF).scipy().toarray())
+
+
+def test_exti_hand_distance_two(orc):
+    # chain 0(C) - 1(F) - 2(F) - 3(C), Poisson rows [-1 2 -1] (ends with 2 on the diagonal)
+    # F point 1: C^_1 = {0} u {3} (3 is a strong C neighbour of its strong F neighbour 2)
+    #   k = 2: d_2 = abar_21 (l = i) + abar_23 = -1 + -1 = -2
+    #   num_0 = a_10 = -1; num_3 = 0 + a_12 abar_23 / d_2 = (-1)(-1)/(-2) = -1/2
+    #   a~_11 = 2 + a_12 abar_21 / d_2 = 2 + (-1)(-1)/(-2) = 3/2
+    #   w_10 = 1/(3/2) = 2/3, w_13 = (1/2)/(3/2) = 1/3   (linear interpolation)
+    A = sp.csr_matrix(np.array([[2, -1, 0, 0], [-1, 2, -1, 0], [0, -1, 2, -1], [0, 0, -1, 2.0]]))
+    A.sort_indices()
+    Ao = orc.Csr.from_scipy(A)
+    S = orc.strength(Ao)
+    CF = np.array([1, -1, -1, 1], np.int8)
+    P = orc.interp_exti(Ao, S, CF).scipy().toarray()
+    assert np.allclose(P, np.array([[1, 0], [2 / 3, 1 / 3], [1 / 3, 2 / 3], [0, 1.0]]), rtol=1e-15, atol=0)
+
+
+def test_exti_reproduces_constants_and_galerkin(orc):
+    nx = 14
+    T = sp.diags([-np.ones(nx - 1), -np.ones(nx - 1)], [-1, 1])
+    L1 = sp.diags(np.asarray(-T.sum(1)).ravel()) + T
+    A = (sp.kron(L1, sp.eye(nx)) + sp.kron(sp.eye(nx), L1)).tocsr()
+    A.sort_indices()
+    Ao = orc.Csr.from_scipy(A)
+    S = orc.strength(Ao)
+    nc, CF = orc.pmis(Ao, S, seed=5)
+    Pe = orc.interp_exti(Ao, S, CF)
+    P = Pe.scipy()
+    rows = np.diff(P.indptr) > 0
+    assert np.allclose(np.asarray(P.sum(1)).ravel()[rows], 1.0, rtol=0, atol=1e-13)
+    # at least as many interpolation entries as the classical formula, and no empty F rows here
+    Pc = orc.interp(Ao, S, CF).scipy()
+    assert P.nnz >= Pc.nnz and rows.sum() >= (np.diff(Pc.indptr) > 0).sum()
+    Pd = P.toarray()
+    Ac = orc.rap(Ao, Pe).scipy().toarray()
+    assert np.allclose(Ac, Pd.T @ A.toarray() @ Pd, rtol=0, atol=1e-12 * abs(Ac).max())
