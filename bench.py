@@ -122,7 +122,7 @@ def run_ours(args):
     va = torch.from_numpy(sysm.val).to(dev)
     b = torch.from_numpy(sysm.b).to(dev)
     opts = dict(precision=args.precision, batched=args.batched, use_graph=args.graph, autotune=1,
-                keep_transpose=int(args.adjoint), max_it=args.max_it, interp_type=args.interp)
+                keep_transpose=int(args.adjoint), max_it=args.max_it, interp_type=args.interp, pdl=args.pdl)
     slv = mgdamg.Solver(**opts)
     adj = {}
 
@@ -397,6 +397,7 @@ def main():
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="no nvidia-smi sampling (profiler runs)")
     ap.add_argument("--max-it", type=int, default=1000)
+    ap.add_argument("--pdl", type=int, default=1, help="programmatic dependent launch of solve kernels")
     ap.add_argument("--interp", type=int, default=None,
                     help="0 classical modified, 1 extended+i (default: 1 for the default workload, else 0)")
     args = ap.parse_args()

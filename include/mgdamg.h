@@ -83,6 +83,8 @@ typedef struct mgd_opts {
                              autotuner (not fused when autotune is off); -1: never */
   int interp_type;        /* 0: classical modified interpolation (Section 3.1); 1: extended+i (distance-two
                              classical interpolation, De Sterck, Falgout, Nolting, Yang 2008) */
+  int pdl;                /* 1: solve kernels use programmatic dependent launch (each waits on its predecessor
+                             in-kernel, so launch latency overlaps the previous kernel); 0: plain launches */
 } mgd_opts;
 
 /* Fill *o with the defaults listed above.  Returns MGD_EINVAL if o is NULL. */
@@ -169,6 +171,15 @@ int mgd_level_export(mgd_ctx *c, int op, int level, int *h_rp, int *h_ci, double
 int mgd_block_vector(mgd_ctx *c, int which, int comp, int comp2, double *h_out);
 /* 1 if coupling D_{a,b} was dropped by the Section 3.6 rule. */
 int mgd_coupling_dropped(mgd_ctx *c, int a, int b);
+
+/* Host wall time (ms) of the phases of the last mgd_setup, h_ms[0..n-1]:
+ * 0 strength, 1 PMIS, 2 interpolation, 3 transpose, 4 A P, 5 R (A P),
+ * 6 level finalisation (diagonals, layouts, copies), 7 coarsest inverse --
+ * these eight summed over every hierarchy (built concurrently, so they can
+ * exceed the wall time) -- then 8 validation, 9 block extraction, 10 all
+ * hierarchies (wall), 11 PCTL vectors and coarse operator, 12 launch program,
+ * batches and autotuning, 13 Krylov storage and graph capture. */
+int mgd_setup_phases(mgd_ctx *c, double *h_ms, int n);
 
 /* Launch plan of the V-cycle batches: *nbatches batches (independent V-cycles
  * launched together); for batch `batch` and level `level`, the number of

@@ -23,6 +23,7 @@ namespace mgd {
 
 long long g_kernel_launches = 0;
 thread_local cudaMemPool_t tl_pool = nullptr;
+thread_local bool tl_pdl = false;
 thread_local cudaStream_t tl_stream = nullptr;
 
 enum OpKind { OP_A = 0, OP_CE = 1, OP_CG = 2, OP_SG = 3, OP_SI = 4, OP_AC = 5, OP_MONO = 6 };
@@ -177,12 +178,44 @@ struct Hier {
   int nlev() const { return (int)L.size(); }
 };
 
+// host wall time per setup phase, summed over all hierarchy builds (worker
+// threads add concurrently, so the hierarchy phases can sum past wall time)
+enum SetupPhase {
+  SP_STRENGTH = 0, SP_PMIS, SP_INTERP, SP_TRANSPOSE, SP_AP, SP_RAP, SP_FINALIZE, SP_COARSE,
+  SP_VALIDATE, SP_BLOCKS, SP_HIERARCHIES, SP_PCTL, SP_PROGRAM, SP_KRYLOV, SP_COUNT = 16
+};
+struct PhaseClock {
+  std::mutex mu;
+  double ms[SP_COUNT] = {0};
+  void add(int ph, double v) {
+    std::lock_guard<std::mutex> lk(mu);
+    ms[ph] += v;
+  }
+  void reset() {
+    std::lock_guard<std::mutex> lk(mu);
+    for (double& x : ms) x = 0;
+  }
+};
+struct PhaseTimer {
+  PhaseClock* clk;
+  int ph;
+  std::chrono::steady_clock::time_point t0;
+  PhaseTimer(PhaseClock* c, int p) : clk(c), ph(p), t0(std::chrono::steady_clock::now()) {}
+  void stop() {
+    if (!clk) return;
+    clk->add(ph, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+    clk = nullptr;
+  }
+  ~PhaseTimer() { stop(); }
+};
+
 struct SetupCtx {
   Arena* arena;
   cudaStream_t s;
   const mgd_opts* o;
   bool mixed;
   bool keepT;
+  PhaseClock* clk;
 };
 
 static Csr csr_alloc(Arena& a, int n, int m, int nnz) {
@@ -293,6 +326,7 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
     int n = lv.A.n;
     if (n <= o.max_coarse || l == o.max_levels - 1) break;
     Scratch tmp(s);
+    PhaseTimer pt_str(sc.clk, SP_STRENGTH);
     uint8_t* S = tmp.alloc<uint8_t>(lv.A.nnz);
     launch_strength(n, lv.A.rp, lv.A.ci, lv.A.v, o.theta_str, S, s);
     int* cnt = tmp.alloc<int>(n);
@@ -305,15 +339,22 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
     int* cur = tmp.alloc<int>(n);
     MGD_CUDA(cudaMemsetAsync(cur, 0, sizeof(int) * n, s));
     launch_fill_st(n, lv.A.rp, lv.A.ci, S, strp, cur, stci, s);
+    pt_str.stop();
+    PhaseTimer pt_pmis(sc.clk, SP_PMIS);
     double* w = tmp.alloc<double>(n);
     signed char* CF = ar.alloc<signed char>(n);
     launch_pmis_init(n, lv.A.rp, S, cnt, o.seed, l, w, CF, s);
     uint8_t* newc = tmp.alloc<uint8_t>(n);
     int* und = tmp.alloc<int>(1);
-    for (int round = 0; round < n + 1; ++round) {
+    // rounds are idempotent once every point is decided, so the undecided
+    // count is read back only every second round
+    for (int round = 0; round < n + 1; round += 2) {
+      launch_pmis_round(n, lv.A.rp, lv.A.ci, S, strp, stci, w, CF, newc, und, s);
       launch_pmis_round(n, lv.A.rp, lv.A.ci, S, strp, stci, w, CF, newc, und, s);
       if (read_int(und, s) == 0) break;
     }
+    pt_pmis.stop();
+    PhaseTimer pt_int(sc.clk, SP_INTERP);
     int* pcnt = tmp.alloc<int>(n);
     int* isc = tmp.alloc<int>(n);
     launch_interp_count(n, lv.A.rp, lv.A.ci, S, CF, pcnt, isc, s);
@@ -351,14 +392,22 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
       launch_interp_fill(n, lv.A.rp, lv.A.ci, lv.A.v, S, CF, cidx, P.rp, P.ci, P.v, s);
     }
     lv.P = P;
+    pt_int.stop();
+    PhaseTimer pt_tr(sc.clk, SP_TRANSPOSE);
     lv.R = transpose(ar, P, s);
+    pt_tr.stop();
+    PhaseTimer pt_ap(sc.clk, SP_AP);
     Scratch apk(s, ar.pool);
     Csr AP = spgemm(ar, lv.A, P, s, &apk);
+    pt_ap.stop();
+    PhaseTimer pt_rap(sc.clk, SP_RAP);
     Csr Ac = spgemm(ar, lv.R, AP, s);
+    pt_rap.stop();
     h.L.emplace_back();
     h.L.back().A = Ac;
   }
   // finalize levels
+  PhaseTimer pt_fin(sc.clk, SP_FINALIZE);
   for (int l = 0; l < h.nlev(); ++l) {
     Level& lv = h.L[l];
     int n = lv.A.n;
@@ -402,6 +451,9 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
     MGD_CUDA(cudaMemsetAsync(lv.xt, 0, es * n, s));
     MGD_CUDA(cudaMemsetAsync(lv.r, 0, es * n, s));
   }
+  MGD_CUDA(cudaStreamSynchronize(s));
+  pt_fin.stop();
+  PhaseTimer pt_co(sc.clk, SP_COARSE);
   Level& last = h.L.back();
   if (last.A.n <= o.max_coarse) {
     int n = last.A.n;
@@ -811,6 +863,7 @@ struct mgd_ctx {
   long long graph_kernels = 0;
   mgd_stats st;
   int n_jacobi = 0;
+  mgd::PhaseClock phases;
 };
 
 namespace mgd {
@@ -904,7 +957,7 @@ static void finalize_op(mgd_ctx* c, InvOp& op, cudaStream_t st) {
     op.b = c->ar.alloc<char>(es * op.n, true, st);
     op.x = c->ar.alloc<char>(es * op.n, true, st);
   } else {
-    SetupCtx sc{&c->ar, st, &c->o, mixed(c), c->o.keep_transpose != 0};
+    SetupCtx sc{&c->ar, st, &c->o, mixed(c), c->o.keep_transpose != 0, &c->phases};
     build_hierarchy(sc, op.h, op.A);
     op.b = op.h.L[0].b;
     op.x = op.h.L[0].x;
@@ -1491,6 +1544,7 @@ static int guarded(mgd_ctx* c, F&& f) {
     if (dev != c->device) MGD_CUDA(cudaSetDevice(c->device));
     tl_pool = c->ar.pool;
     tl_stream = nullptr;
+    tl_pdl = c->o.pdl != 0;
     int r = f();
     if (dev != c->device) cudaSetDevice(dev);
     return r;
@@ -1566,6 +1620,8 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
   int G = c->G, N = c->N, n = c->n, nnz = c->nnz, nc = G + 2;
   const mgd_opts& o = c->o;
   c->ar.stream = s;
+  c->phases.reset();
+  PhaseTimer pt_val(&c->phases, SP_VALIDATE);
   // validation
   {
     Scratch sc(s);
@@ -1596,6 +1652,8 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
     c->AT = transpose(c->ar, c->A, s);
     c->ATsell = build_sell(c->ar, c->AT, false, s);
   }
+  pt_val.stop();
+  PhaseTimer pt_blk(&c->phases, SP_BLOCKS);
   c->wEs = c->ar.alloc<double>(N, true);
   c->wIs = c->ar.alloc<double>(N, true);
   c->rfull = c->ar.alloc<double>(n, true);
@@ -1709,8 +1767,13 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
     bd.d_dtab = (double**)upload_vec(c, bd.d);
   }
   // hierarchies / Jacobi data
+  MGD_CUDA(cudaStreamSynchronize(s));
+  pt_blk.stop();
+  PhaseTimer pt_h(&c->phases, SP_HIERARCHIES);
   if (mixed(c)) finalize_ops_parallel<float>(c, 0, c->ops.size());
   else finalize_ops_parallel<double>(c, 0, c->ops.size());
+  pt_h.stop();
+  PhaseTimer pt_pctl(&c->phases, SP_PCTL);
   for (auto& op : c->ops)
     if (op.jacobi) c->n_jacobi++;
   if (c->kind == MGD_PCTL) {
@@ -1809,6 +1872,8 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
     if (c->ops[oAc].jacobi) c->n_jacobi++;
   }
   // program, batches, graph
+  pt_pctl.stop();
+  PhaseTimer pt_prog(&c->phases, SP_PROGRAM);
   if (mixed(c)) {
     build_program<float>(c);
     build_batches<float>(c);
@@ -1817,6 +1882,9 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
     build_batches<double>(c);
   }
   // FGMRES storage
+  MGD_CUDA(cudaStreamSynchronize(s));
+  pt_prog.stop();
+  PhaseTimer pt_kry(&c->phases, SP_KRYLOV);
   c->m = std::max(1, std::min(o.restart, 30));
   c->V = c->ar.alloc<double>((size_t)(c->m + 1) * n, true);
   c->Z = c->ar.alloc<double>((size_t)c->m * n, true);
@@ -1854,6 +1922,7 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
   }
   capture_graph(c);
   MGD_CUDA(cudaStreamSynchronize(s));
+  pt_kry.stop();
   // stats
   memset(&c->st, 0, sizeof(c->st));
   mgd_stats& st = c->st;
@@ -2051,6 +2120,9 @@ int mgd_opts_default(mgd_opts* o) {
   o->use_graph = 0;
   o->autotune = 1;
   o->keep_transpose = 0;
+  o->fuse_rows = 0;
+  o->interp_type = 0;
+  o->pdl = 1;
   return MGD_OK;
 }
 
@@ -2325,6 +2397,13 @@ int mgd_plan_info(mgd_ctx* c, int batch, int level, int* nbatches, int* depth, i
     return MGD_OK;
   };
   return m ? fill(c->vb32[batch]) : fill(c->vb64[batch]);
+}
+
+int mgd_setup_phases(mgd_ctx* c, double* h_ms, int n) {
+  if (!c || !h_ms || n < 0) return MGD_EINVAL;
+  std::lock_guard<std::mutex> lk(c->phases.mu);
+  for (int k = 0; k < n && k < SP_COUNT; ++k) h_ms[k] = c->phases.ms[k];
+  return MGD_OK;
 }
 
 long long mgd_kernel_launches(void) { return __atomic_load_n(&g_kernel_launches, __ATOMIC_RELAXED); }

@@ -35,6 +35,35 @@ extern long long g_kernel_launches;
 
 constexpr int kThreads = 256;
 
+// Programmatic dependent launch: solve kernels are launched with the
+// programmatic-stream-serialisation attribute; each waits for its predecessor
+// grid (griddepcontrol.wait) before touching memory and then lets its own
+// successor start launching, so launch latency overlaps the previous kernel.
+// Without the attribute both instructions are no-ops.
+#define MGD_PDL_ENTRY()                                         \
+  do {                                                          \
+    asm volatile("griddepcontrol.wait;" ::: "memory");          \
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); \
+  } while (0)
+
+extern thread_local bool tl_pdl;
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = tl_pdl ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+  if (e != cudaSuccess) throw Error{7, std::string("kernel launch: ") + cudaGetErrorString(e)};
+}
+
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // ------------------------------------------------------------------ memory

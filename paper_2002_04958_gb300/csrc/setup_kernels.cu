@@ -13,37 +13,6 @@ namespace mgd {
 
 // ------------------------------------------------------------------ scan
 template <typename I>
-__global__ void k_scan_block(const int* in, I* out, I* bsum, int n) {
-  // 256 threads x 4 items per block
-  __shared__ I sh[kThreads];
-  int base = blockIdx.x * kThreads * 4;
-  I v[4];
-  I tsum = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    int i = base + threadIdx.x * 4 + k;
-    v[k] = (i < n && in) ? (I)in[i] : 0;
-    tsum += v[k];
-  }
-  sh[threadIdx.x] = tsum;
-  __syncthreads();
-  for (int off = 1; off < kThreads; off <<= 1) {
-    I t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
-    __syncthreads();
-    sh[threadIdx.x] += t;
-    __syncthreads();
-  }
-  I run = sh[threadIdx.x] - tsum;  // exclusive prefix of this thread
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    int i = base + threadIdx.x * 4 + k;
-    if (i < n) out[i] = run;
-    run += v[k];
-  }
-  if (threadIdx.x == kThreads - 1) bsum[blockIdx.x] = sh[kThreads - 1];
-}
-
-template <typename I>
 __global__ void k_scan_block_i(const I* in, I* out, I* bsum, int n) {
   __shared__ I sh[kThreads];
   int base = blockIdx.x * kThreads * 4;
@@ -725,58 +694,121 @@ void launch_spgemm_ub(int n, const int* xrp, const int* xci, const int* yrp, int
   MGD_LAUNCH_CHECK();
 }
 
-__global__ void k_spgemm_expand(int n, const int* xrp, const int* xci, const double* xv, const int* yrp,
-                                const int* yci, const double* yv, const long long* off, int* tc, double* tv,
-                                int* cnt) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  long long b = off[i];
-  long long t = b;
+// One warp per output row, in shared memory for rows with at most
+// kWarpProducts products: products are expanded in order (k along row i of X,
+// then row k of Y), ranked by a stable counting sort on the column (ties keep
+// their expansion order), and each run of equal columns is summed left to
+// right by one lane.  Longer rows run the same three steps (expand, stable
+// insertion sort, run sums) on one lane in global memory.
+constexpr int kWarpProducts = 256;
+constexpr int kSpgWarps = 4;
+
+__global__ void __launch_bounds__(32 * kSpgWarps) k_spgemm_warp(int n, const int* xrp, const int* xci,
+                                                                const double* xv, const int* yrp, const int* yci,
+                                                                const double* yv, const long long* off, int* tc,
+                                                                double* tv, int* cnt) {
+  __shared__ int s_col[kSpgWarps][kWarpProducts];
+  __shared__ double s_val[kSpgWarps][kWarpProducts];
+  __shared__ int s_scol[kSpgWarps][kWarpProducts];
+  __shared__ double s_sval[kSpgWarps][kWarpProducts];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kSpgWarps + warp;
+  if (i >= n) return;  // whole warp
+  const long long b = off[i];
+  const int L = (int)(off[i + 1] - b);
+  if (L > kWarpProducts) {
+    if (lane != 0) return;
+    long long t = b;
+    for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
+      int k = xci[p];
+      double x = xv[p];
+      for (int q = yrp[k]; q < yrp[k + 1]; ++q) {
+        tc[t] = yci[q];
+        tv[t] = __dmul_rn(x, yv[q]);
+        ++t;
+      }
+    }
+    long long e = t;
+    for (long long a = b + 1; a < e; ++a) {
+      int cc = tc[a];
+      double vv = tv[a];
+      long long q = a - 1;
+      while (q >= b && tc[q] > cc) {
+        tc[q + 1] = tc[q];
+        tv[q + 1] = tv[q];
+        --q;
+      }
+      tc[q + 1] = cc;
+      tv[q + 1] = vv;
+    }
+    long long w = b;
+    for (long long a = b; a < e;) {
+      int cc = tc[a];
+      double acc = tv[a];
+      long long q = a + 1;
+      while (q < e && tc[q] == cc) {
+        acc = __dadd_rn(acc, tv[q]);
+        ++q;
+      }
+      tc[w] = cc;
+      tv[w] = acc;
+      ++w;
+      a = q;
+    }
+    cnt[i] = (int)(w - b);
+    return;
+  }
+  int* col = s_col[warp];
+  double* val = s_val[warp];
+  int* scol = s_scol[warp];
+  double* sval = s_sval[warp];
+  int p0 = 0;
   for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
     int k = xci[p];
     double x = xv[p];
-    for (int q = yrp[k]; q < yrp[k + 1]; ++q) {
-      tc[t] = yci[q];
-      tv[t] = __dmul_rn(x, yv[q]);
-      ++t;
+    int yb = yrp[k], len = yrp[k + 1] - yb;
+    for (int q = lane; q < len; q += 32) {
+      col[p0 + q] = yci[yb + q];
+      val[p0 + q] = __dmul_rn(x, yv[yb + q]);
     }
+    p0 += len;
   }
-  long long e = t;
-  // stable insertion sort by column
-  for (long long a = b + 1; a < e; ++a) {
-    int cc = tc[a];
-    double vv = tv[a];
-    long long q = a - 1;
-    while (q >= b && tc[q] > cc) {
-      tc[q + 1] = tc[q];
-      tv[q + 1] = tv[q];
-      --q;
+  __syncwarp();
+  for (int p = lane; p < L; p += 32) {  // stable rank by column
+    int c = col[p], r = 0;
+    for (int t = 0; t < L; ++t) {
+      int ct = col[t];
+      r += (ct < c) || (ct == c && t < p);
     }
-    tc[q + 1] = cc;
-    tv[q + 1] = vv;
+    scol[r] = c;
+    sval[r] = val[p];
   }
-  // sum runs of equal columns left to right, compacting in place
-  long long w = b;
-  for (long long a = b; a < e;) {
-    int cc = tc[a];
-    double acc = tv[a];
-    long long q = a + 1;
-    while (q < e && tc[q] == cc) {
-      acc = __dadd_rn(acc, tv[q]);
-      ++q;
+  __syncwarp();
+  int base = 0;  // unique columns before this chunk
+  for (int c0 = 0; c0 < L; c0 += 32) {
+    int p = c0 + lane;
+    bool start = p < L && (p == 0 || scol[p] != scol[p - 1]);
+    unsigned m = __ballot_sync(0xffffffffu, start);
+    if (start) {
+      int u = base + __popc(m & ((1u << lane) - 1u));
+      double acc = sval[p];
+      int q = p + 1;
+      while (q < L && scol[q] == scol[p]) {
+        acc = __dadd_rn(acc, sval[q]);
+        ++q;
+      }
+      tc[b + u] = scol[p];
+      tv[b + u] = acc;
     }
-    tc[w] = cc;
-    tv[w] = acc;
-    ++w;
-    a = q;
+    base += __popc(m);
   }
-  cnt[i] = (int)(w - b);
+  if (lane == 0) cnt[i] = base;
 }
 
 void launch_spgemm_expand(int n, const int* xrp, const int* xci, const double* xv, const int* yrp,
                           const int* yci, const double* yv, const long long* off, int* tc, double* tv, int* cnt,
                           cudaStream_t s) {
-  k_spgemm_expand<<<cdiv(n, 128), 128, 0, s>>>(n, xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt);
+  k_spgemm_warp<<<cdiv(n, kSpgWarps), 32 * kSpgWarps, 0, s>>>(n, xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt);
   MGD_LAUNCH_CHECK();
 }
 

@@ -17,6 +17,7 @@ __device__ __forceinline__ double* resolve(const PRef& r, const IOSlots* io) {
 // dst = (T)(a + sum_t s_t d_t (.) w_t)
 template <typename T>
 __global__ void k_produce(const ProduceDesc<T>* __restrict__ ds, int N, const IOSlots* __restrict__ io) {
+  MGD_PDL_ENTRY();
   const ProduceDesc<T>* d = ds + blockIdx.y;
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -35,6 +36,7 @@ __global__ void k_produce(const ProduceDesc<T>* __restrict__ ds, int N, const IO
 // dst = base + s * x
 template <typename T>
 __global__ void k_consume(const ConsumeDesc<T>* __restrict__ ds, int N, const IOSlots* __restrict__ io) {
+  MGD_PDL_ENTRY();
   const ConsumeDesc<T>* d = ds + blockIdx.y;
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -46,6 +48,7 @@ __global__ void k_consume(const ConsumeDesc<T>* __restrict__ ds, int N, const IO
 
 template <typename T>
 __global__ void k_jacobi(const JacDesc<T>* __restrict__ ds, int N) {
+  MGD_PDL_ENTRY();
   const JacDesc<T>* d = ds + blockIdx.y;
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < N) d->x[k] = d->dinv[k] * d->b[k];
@@ -54,19 +57,19 @@ __global__ void k_jacobi(const JacDesc<T>* __restrict__ ds, int N) {
 template <typename T>
 void launch_produce(const ProduceDesc<T>* d, int nd, int N, const IOSlots* io, cudaStream_t s) {
   if (nd <= 0) return;
-  k_produce<T><<<dim3(cdiv(N, kThreads), nd), kThreads, 0, s>>>(d, N, io);
+  launch_k(k_produce<T>, dim3(dim3(cdiv(N, kThreads), nd)), dim3(kThreads), 0, s, d, N, io);
   MGD_LAUNCH_CHECK();
 }
 template <typename T>
 void launch_consume(const ConsumeDesc<T>* d, int nd, int N, const IOSlots* io, cudaStream_t s) {
   if (nd <= 0) return;
-  k_consume<T><<<dim3(cdiv(N, kThreads), nd), kThreads, 0, s>>>(d, N, io);
+  launch_k(k_consume<T>, dim3(dim3(cdiv(N, kThreads), nd)), dim3(kThreads), 0, s, d, N, io);
   MGD_LAUNCH_CHECK();
 }
 template <typename T>
 void launch_jacobi(const JacDesc<T>* d, int nd, int N, cudaStream_t s) {
   if (nd <= 0) return;
-  k_jacobi<T><<<dim3(cdiv(N, kThreads), nd), kThreads, 0, s>>>(d, N);
+  launch_k(k_jacobi<T>, dim3(dim3(cdiv(N, kThreads), nd)), dim3(kThreads), 0, s, d, N);
   MGD_LAUNCH_CHECK();
 }
 template void launch_produce<double>(const ProduceDesc<double>*, int, int, const IOSlots*, cudaStream_t);
@@ -83,6 +86,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(int n, const int* __restrict_
                                                    const int* __restrict__ sci, const T* __restrict__ sv,
                                                    const T* __restrict__ b, const T* __restrict__ x,
                                                    T* __restrict__ y) {
+  MGD_PDL_ENTRY();
   constexpr int TPR = FmtTraits<FMT>::tpr;
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int row = (int)(g / TPR), lane = (int)(g % TPR);
@@ -100,15 +104,15 @@ static void spmv_dispatch(int fmt, int n, const int* rp, const int* ci, const T*
   if (fmt == FMT_SELL && !sptr) fmt = FMT_CSR4;
   auto g = [&](int tpr) { return cdiv((long long)n * tpr + 32, kThreads); };
   switch (fmt) {
-    case FMT_SELL: k_spmv<T, FMT_SELL, MODE><<<g(1), kThreads, 0, s>>>(n, rp, ci, v, sptr, sci, sv, b, x, y); break;
-    case FMT_CSR1: k_spmv<T, FMT_CSR1, MODE><<<g(1), kThreads, 0, s>>>(n, rp, ci, v, sptr, sci, sv, b, x, y); break;
-    case FMT_CSR2: k_spmv<T, FMT_CSR2, MODE><<<g(2), kThreads, 0, s>>>(n, rp, ci, v, sptr, sci, sv, b, x, y); break;
-    case FMT_CSR4: k_spmv<T, FMT_CSR4, MODE><<<g(4), kThreads, 0, s>>>(n, rp, ci, v, sptr, sci, sv, b, x, y); break;
-    case FMT_CSR8: k_spmv<T, FMT_CSR8, MODE><<<g(8), kThreads, 0, s>>>(n, rp, ci, v, sptr, sci, sv, b, x, y); break;
+    case FMT_SELL: launch_k(k_spmv<T, FMT_SELL, MODE>, dim3(g(1)), dim3(kThreads), 0, s, n, rp, ci, v, sptr, sci, sv, b, x, y); break;
+    case FMT_CSR1: launch_k(k_spmv<T, FMT_CSR1, MODE>, dim3(g(1)), dim3(kThreads), 0, s, n, rp, ci, v, sptr, sci, sv, b, x, y); break;
+    case FMT_CSR2: launch_k(k_spmv<T, FMT_CSR2, MODE>, dim3(g(2)), dim3(kThreads), 0, s, n, rp, ci, v, sptr, sci, sv, b, x, y); break;
+    case FMT_CSR4: launch_k(k_spmv<T, FMT_CSR4, MODE>, dim3(g(4)), dim3(kThreads), 0, s, n, rp, ci, v, sptr, sci, sv, b, x, y); break;
+    case FMT_CSR8: launch_k(k_spmv<T, FMT_CSR8, MODE>, dim3(g(8)), dim3(kThreads), 0, s, n, rp, ci, v, sptr, sci, sv, b, x, y); break;
     case FMT_CSR16:
-      k_spmv<T, FMT_CSR16, MODE><<<g(16), kThreads, 0, s>>>(n, rp, ci, v, sptr, sci, sv, b, x, y);
+      launch_k(k_spmv<T, FMT_CSR16, MODE>, dim3(g(16)), dim3(kThreads), 0, s, n, rp, ci, v, sptr, sci, sv, b, x, y);
       break;
-    default: k_spmv<T, FMT_CSR32, MODE><<<g(32), kThreads, 0, s>>>(n, rp, ci, v, sptr, sci, sv, b, x, y); break;
+    default: launch_k(k_spmv<T, FMT_CSR32, MODE>, dim3(g(32)), dim3(kThreads), 0, s, n, rp, ci, v, sptr, sci, sv, b, x, y); break;
   }
   MGD_LAUNCH_CHECK();
 }
@@ -135,52 +139,57 @@ void launch_resid_f64(int fmt, int n, const int* rp, const int* ci, const double
 
 template <typename T>
 __global__ void k_axpy(int n, T* y, const T* x) {
+  MGD_PDL_ENTRY();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] += x[i];
 }
 template <typename T>
 void launch_axpy(int n, T* y, const T* x, cudaStream_t s) {
   if (n <= 0) return;
-  k_axpy<T><<<cdiv(n, kThreads), kThreads, 0, s>>>(n, y, x);
+  launch_k(k_axpy<T>, dim3(cdiv(n, kThreads)), dim3(kThreads), 0, s, n, y, x);
   MGD_LAUNCH_CHECK();
 }
 template void launch_axpy<double>(int, double*, const double*, cudaStream_t);
 template void launch_axpy<float>(int, float*, const float*, cudaStream_t);
 
 __global__ void k_set_io(IOSlots* io, const double* v, double* z) {
+  MGD_PDL_ENTRY();
   io->v = v;
   io->z = z;
 }
 void launch_set_io(IOSlots* io, const double* v, double* z, cudaStream_t s) {
-  k_set_io<<<1, 1, 0, s>>>(io, v, z);
+  launch_k(k_set_io, dim3(1), dim3(1), 0, s, io, v, z);
   MGD_LAUNCH_CHECK();
 }
 
 __global__ void k_cast_df(int n, const double* a, float* b) {
+  MGD_PDL_ENTRY();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
 }
 __global__ void k_cast_fd(int n, const float* a, double* b) {
+  MGD_PDL_ENTRY();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (double)a[i];
 }
 __global__ void k_copy(int n, const double* a, double* b) {
+  MGD_PDL_ENTRY();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = a[i];
 }
 void launch_cast_f64_f32(int n, const double* a, float* b, cudaStream_t s) {
   if (n <= 0) return;
-  k_cast_df<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, a, b);
+  launch_k(k_cast_df, dim3(cdiv(n, kThreads)), dim3(kThreads), 0, s, n, a, b);
   MGD_LAUNCH_CHECK();
 }
 void launch_cast_f32_f64(int n, const float* a, double* b, cudaStream_t s) {
   if (n <= 0) return;
-  k_cast_fd<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, a, b);
+  launch_k(k_cast_fd, dim3(cdiv(n, kThreads)), dim3(kThreads), 0, s, n, a, b);
   MGD_LAUNCH_CHECK();
 }
 void launch_copy_f64(int n, const double* a, double* b, cudaStream_t s) {
   if (n <= 0) return;
-  k_copy<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, a, b);
+  launch_k(k_copy, dim3(cdiv(n, kThreads)), dim3(kThreads), 0, s, n, a, b);
   MGD_LAUNCH_CHECK();
 }
 
@@ -189,6 +198,7 @@ constexpr int kMaxV = 32;
 
 // out[t] = sum_b partial[b * kMaxV + t]  (fixed order: deterministic)
 __global__ void k_reduce_partials(const double* __restrict__ partial, int nblocks, int nv, double* __restrict__ out) {
+  MGD_PDL_ENTRY();
   int t = blockIdx.x;
   if (t >= nv) return;
   __shared__ double sh[kThreads];
@@ -215,6 +225,7 @@ static int dot_blocks(int n) { return std::min(kDotBlocks, std::max(1, cdiv(n, k
 __global__ void __launch_bounds__(kThreads) k_dot_partial(int n, const double* __restrict__ a,
                                                           const double* __restrict__ b,
                                                           double* __restrict__ partial) {
+  MGD_PDL_ENTRY();
   double s = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     s += a[i] * b[i];
@@ -249,6 +260,7 @@ __global__ void __launch_bounds__(kThreads) k_mgs_step(int n, const double* __re
                                                        const double* __restrict__ vnext, double* __restrict__ w,
                                                        const double* __restrict__ pin, int nb,
                                                        double* __restrict__ pout, double* __restrict__ hout) {
+  MGD_PDL_ENTRY();
   const double h = block_sum_partials(pin, nb);
   if (blockIdx.x == 0 && threadIdx.x == 0) *hout = h;
   double s = 0.0;
@@ -270,6 +282,7 @@ __global__ void __launch_bounds__(kThreads) k_mgs_step(int n, const double* __re
 }
 
 __global__ void k_sum_partials(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  MGD_PDL_ENTRY();
   double r = block_sum_partials(partial, nb);
   if (threadIdx.x == 0) *out = r;
 }
@@ -280,17 +293,17 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int nb, doubl
 void launch_mgs(int n, const double* V, long long ldv, int nv, double* w, double* h, double* nrm2, double* pa,
                 double* pb, cudaStream_t s) {
   int nb = std::min(kDotBlocks, std::max(1, cdiv(n, kThreads)));
-  k_dot_partial<<<nb, kThreads, 0, s>>>(n, V, w, pa);
+  launch_k(k_dot_partial, dim3(nb), dim3(kThreads), 0, s, n, V, w, pa);
   MGD_LAUNCH_CHECK();
   double* pin = pa;
   double* pout = pb;
   for (int i = 0; i < nv; ++i) {
     const double* vnext = i + 1 < nv ? V + (long long)(i + 1) * ldv : nullptr;
-    k_mgs_step<<<nb, kThreads, 0, s>>>(n, V + (long long)i * ldv, vnext, w, pin, nb, pout, h + i);
+    launch_k(k_mgs_step, dim3(nb), dim3(kThreads), 0, s, n, V + (long long)i * ldv, vnext, w, pin, nb, pout, h + i);
     MGD_LAUNCH_CHECK();
     std::swap(pin, pout);
   }
-  k_sum_partials<<<1, kThreads, 0, s>>>(pin, nb, nrm2);
+  launch_k(k_sum_partials, dim3(1), dim3(kThreads), 0, s, pin, nb, nrm2);
   MGD_LAUNCH_CHECK();
 }
 
@@ -298,6 +311,7 @@ void launch_mgs(int n, const double* V, long long ldv, int nv, double* w, double
 // division is a long instruction sequence on this part)
 __global__ void k_scale_by_norm(int n, const double* __restrict__ w, const double* __restrict__ nrm2,
                                 double* __restrict__ v) {
+  MGD_PDL_ENTRY();
   __shared__ double s_inv;
   if (threadIdx.x == 0) {
     double h = sqrt(*nrm2);
@@ -308,12 +322,13 @@ __global__ void k_scale_by_norm(int n, const double* __restrict__ w, const doubl
   if (i < n) v[i] = w[i] * s_inv;
 }
 void launch_scale_by_norm(int n, const double* w, const double* nrm2, double* v, cudaStream_t s) {
-  k_scale_by_norm<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, w, nrm2, v);
+  launch_k(k_scale_by_norm, dim3(cdiv(n, kThreads)), dim3(kThreads), 0, s, n, w, nrm2, v);
   MGD_LAUNCH_CHECK();
 }
 
 __global__ void k_vcomb(int n, const double* __restrict__ Z, long long ldz, int nv, const double* __restrict__ y,
                         double* __restrict__ x) {
+  MGD_PDL_ENTRY();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double s = x[i];
@@ -322,12 +337,13 @@ __global__ void k_vcomb(int n, const double* __restrict__ Z, long long ldz, int 
 }
 void launch_vcomb(int n, const double* Z, long long ldz, int nv, const double* y, double* x, cudaStream_t s) {
   if (nv <= 0) return;
-  k_vcomb<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, Z, ldz, nv, y, x);
+  launch_k(k_vcomb, dim3(cdiv(n, kThreads)), dim3(kThreads), 0, s, n, Z, ldz, nv, y, x);
   MGD_LAUNCH_CHECK();
 }
 
 __global__ void __launch_bounds__(kThreads) k_norm2_partial(int n, const double* __restrict__ x,
                                                             double* __restrict__ partial) {
+  MGD_PDL_ENTRY();
   double s = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     s += x[i] * x[i];
@@ -344,9 +360,9 @@ __global__ void __launch_bounds__(kThreads) k_norm2_partial(int n, const double*
 }
 void launch_norm2(int n, const double* x, double* partial, double* out, cudaStream_t s) {
   int nb = dot_blocks(n);
-  k_norm2_partial<<<nb, kThreads, 0, s>>>(n, x, partial);
+  launch_k(k_norm2_partial, dim3(nb), dim3(kThreads), 0, s, n, x, partial);
   MGD_LAUNCH_CHECK();
-  k_reduce_partials<<<1, kThreads, 0, s>>>(partial, nb, 1, out);
+  launch_k(k_reduce_partials, dim3(1), dim3(kThreads), 0, s, partial, nb, 1, out);
   MGD_LAUNCH_CHECK();
 }
 
@@ -354,6 +370,7 @@ void launch_norm2(int n, const double* x, double* partial, double* out, cudaStre
 __global__ void k_block_resid(int N, int nc, const int* const* __restrict__ brp, const int* const* __restrict__ bci,
                               const double* const* __restrict__ bv, const double* const* __restrict__ dtab,
                               const IOSlots* __restrict__ io, double* __restrict__ r) {
+  MGD_PDL_ENTRY();
   int a = blockIdx.y;
   const double* w = io->z;  // current preconditioner output (the block-relaxed w)
   int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -372,24 +389,26 @@ __global__ void k_block_resid(int N, int nc, const int* const* __restrict__ brp,
 }
 void launch_block_resid(int N, int nc, const int* const* brp, const int* const* bci, const double* const* bv,
                         const double* const* dtab, const IOSlots* io, double* r, cudaStream_t s) {
-  k_block_resid<<<dim3(cdiv(N, kThreads), nc), kThreads, 0, s>>>(N, nc, brp, bci, bv, dtab, io, r);
+  launch_k(k_block_resid, dim3(dim3(cdiv(N, kThreads), nc)), dim3(kThreads), 0, s, N, nc, brp, bci, bv, dtab, io, r);
   MGD_LAUNCH_CHECK();
 }
 
 __global__ void k_saxpy_vec(int n, double a, const double* x, double* y) {
+  MGD_PDL_ENTRY();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] += a * x[i];
 }
 void launch_saxpy_vec(int n, double a, const double* x, double* y, cudaStream_t s) {
-  k_saxpy_vec<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, a, x, y);
+  launch_k(k_saxpy_vec, dim3(cdiv(n, kThreads)), dim3(kThreads), 0, s, n, a, x, y);
   MGD_LAUNCH_CHECK();
 }
 __global__ void k_lincomb(int n, double a, const double* x, double b, const double* y, double* out) {
+  MGD_PDL_ENTRY();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = a * x[i] + b * y[i];
 }
 void launch_lincomb(int n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s) {
-  k_lincomb<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, a, x, b, y, out);
+  launch_k(k_lincomb, dim3(cdiv(n, kThreads)), dim3(kThreads), 0, s, n, a, x, b, y, out);
   MGD_LAUNCH_CHECK();
 }
 

@@ -20,6 +20,7 @@ namespace mgd {
 // the column-scaled copy of A so that each nonzero costs one multiply-add
 template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_pre(const LDesc<T>* __restrict__ descs) {
+  MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
   constexpr int TPR = FmtTraits<FMT>::tpr;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -40,6 +41,7 @@ __global__ void __launch_bounds__(kThreads) k_pre(const LDesc<T>* __restrict__ d
 // POST: x = xt + D^-1 (b - A xt)
 template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_post(const LDesc<T>* __restrict__ descs) {
+  MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
   constexpr int TPR = FmtTraits<FMT>::tpr;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -55,6 +57,7 @@ __global__ void __launch_bounds__(kThreads) k_post(const LDesc<T>* __restrict__ 
 // RESTRICT: bc = R r ; PROLONG: xt += P xc  (CSR, TPR threads per row)
 template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_restrict(const LDesc<T>* __restrict__ descs) {
+  MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
   constexpr int TPR = FmtTraits<FMT>::tpr;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -69,6 +72,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const LDesc<T>* __restric
 
 template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_prolong(const LDesc<T>* __restrict__ descs) {
+  MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
   constexpr int TPR = FmtTraits<FMT>::tpr;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -84,6 +88,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LDesc<T>* __restrict
 // stalled coarsest level, first l1-Jacobi sweep from zero: xt = D^-1 b
 template <typename T>
 __global__ void k_jac1(const LDesc<T>* __restrict__ descs) {
+  MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < d->n) d->xt[i] = d->dinv[i] * d->b[i];
@@ -92,6 +97,7 @@ __global__ void k_jac1(const LDesc<T>* __restrict__ descs) {
 // coarsest level: x = A_L^{-1} b with the dense FP64 inverse (one CTA per subsystem)
 template <typename T>
 __global__ void k_coarse(const LDesc<T>* __restrict__ descs) {
+  MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
   extern __shared__ double sb[];
   int n = d->cn;
@@ -112,13 +118,13 @@ __global__ void k_coarse(const LDesc<T>* __restrict__ descs) {
   do {                                                                                         \
     auto g_ = [&](int tpr) { return dim3(cdiv((long long)(maxrows) * tpr + 32, kThreads), (ny)); }; \
     switch (fmt) {                                                                             \
-      case FMT_SELL: K<T, FMT_SELL><<<g_(1), kThreads, 0, s>>>(descs); break;                  \
-      case FMT_CSR1: K<T, FMT_CSR1><<<g_(1), kThreads, 0, s>>>(descs); break;                  \
-      case FMT_CSR2: K<T, FMT_CSR2><<<g_(2), kThreads, 0, s>>>(descs); break;                  \
-      case FMT_CSR4: K<T, FMT_CSR4><<<g_(4), kThreads, 0, s>>>(descs); break;                  \
-      case FMT_CSR8: K<T, FMT_CSR8><<<g_(8), kThreads, 0, s>>>(descs); break;                  \
-      case FMT_CSR16: K<T, FMT_CSR16><<<g_(16), kThreads, 0, s>>>(descs); break;               \
-      default: K<T, FMT_CSR32><<<g_(32), kThreads, 0, s>>>(descs); break;                      \
+      case FMT_SELL: launch_k(K<T, FMT_SELL>, dim3(g_(1)), dim3(kThreads), 0, s, descs); break;                  \
+      case FMT_CSR1: launch_k(K<T, FMT_CSR1>, dim3(g_(1)), dim3(kThreads), 0, s, descs); break;                  \
+      case FMT_CSR2: launch_k(K<T, FMT_CSR2>, dim3(g_(2)), dim3(kThreads), 0, s, descs); break;                  \
+      case FMT_CSR4: launch_k(K<T, FMT_CSR4>, dim3(g_(4)), dim3(kThreads), 0, s, descs); break;                  \
+      case FMT_CSR8: launch_k(K<T, FMT_CSR8>, dim3(g_(8)), dim3(kThreads), 0, s, descs); break;                  \
+      case FMT_CSR16: launch_k(K<T, FMT_CSR16>, dim3(g_(16)), dim3(kThreads), 0, s, descs); break;               \
+      default: launch_k(K<T, FMT_CSR32>, dim3(g_(32)), dim3(kThreads), 0, s, descs); break;                      \
     }                                                                                          \
   } while (0)
 
@@ -131,9 +137,9 @@ void launch_phase(int phase, int fmtA, int fmtRP, const LDesc<T>* d_descs, int n
     case PH_POST: MGD_DISPATCH_FMT(k_post, fmtA, maxrows, ndesc, s, d_descs); break;
     case PH_RESTRICT: MGD_DISPATCH_FMT(k_restrict, rp, maxrows, ndesc, s, d_descs); break;
     case PH_PROLONG: MGD_DISPATCH_FMT(k_prolong, rp, maxrows, ndesc, s, d_descs); break;
-    case PH_JAC1: k_jac1<T><<<dim3(cdiv(maxrows, kThreads), ndesc), kThreads, 0, s>>>(d_descs); break;
+    case PH_JAC1: launch_k(k_jac1<T>, dim3(dim3(cdiv(maxrows, kThreads), ndesc)), dim3(kThreads), 0, s, d_descs); break;
     case PH_COARSE:
-      k_coarse<T><<<dim3(1, ndesc), kThreads, sizeof(double) * maxrows, s>>>(d_descs);
+      launch_k(k_coarse<T>, dim3(dim3(1, ndesc)), dim3(kThreads), sizeof(double) * maxrows, s, d_descs);
       break;
   }
   MGD_LAUNCH_CHECK();
@@ -176,6 +182,7 @@ __device__ __forceinline__ T tail_row(const int* __restrict__ rp, const int* __r
 
 template <typename T>
 __global__ void __launch_bounds__(kTailThreads) k_vtail(const TailSub<T>* __restrict__ subs) {
+  MGD_PDL_ENTRY();
   cg::cluster_group cl = cg::this_cluster();
   const int cs = (int)cl.num_blocks();
   const TailSub<T> S = subs[blockIdx.x / cs];

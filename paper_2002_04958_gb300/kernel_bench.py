@@ -31,6 +31,7 @@ def main():
     ap.add_argument("--applies", type=int, default=5)
     ap.add_argument("--timing", type=int, default=1, help="0: no CUDA events (for profiler runs)")
     ap.add_argument("--solve", action="store_true", help="also time one full solve by kernel class")
+    ap.add_argument("--interp", type=int, default=0)
     args = ap.parse_args()
 
     import torch
@@ -40,7 +41,7 @@ def main():
     build()
     s = inputs.preset(args.config)
     slv = mgdamg.Solver(precision=args.precision, batched=args.batched, use_graph=args.graph,
-                        autotune=0 if args.no_autotune else 1)
+                        autotune=0 if args.no_autotune else 1, interp_type=args.interp)
     slv.setup_system(s, args.kind)
     v = torch.from_numpy(s.b).cuda()
     if args.timing:
@@ -86,6 +87,12 @@ def main():
                         "idle_ms": round(wall - busy, 3), "classes": cls}
         slv.profile(0)
     st = slv.stats()
+    out["setup_ms"] = round(st["setup_ms"], 3)
+    out["setup_phases_ms"] = slv.setup_phases()
+    # a second setup of the same system (autotune decisions cached)
+    slv.setup_system(s, args.kind)
+    out["setup2_ms"] = round(slv.stats()["setup_ms"], 3)
+    out["setup2_phases_ms"] = slv.setup_phases()
     out["plan"] = slv.plan()
     out["vcycle_bytes_per_apply"] = st["vcycle_bytes"]
     out["levels"] = st["max_levels_used"]

@@ -25,6 +25,7 @@ ENTRY_POINTS = ["mgd_opts_default", "mgd_create", "mgd_setup", "mgd_update_value
                 "mgd_solve_transpose", "mgd_grad_values", "mgd_precond_apply", "mgd_get_stats", "mgd_get_history",
                 "mgd_op_info", "mgd_level_info", "mgd_level_export", "mgd_block_vector", "mgd_coupling_dropped",
                 "mgd_profile_enable", "mgd_profile_read", "mgd_kernel_launches", "mgd_last_error", "mgd_destroy", "mgd_plan_info",
+                "mgd_setup_phases",
                 "mgd_relres_noalloc"]
 
 
@@ -36,7 +37,7 @@ class MgdOpts(C.Structure):
                 ("jacobi_sweeps", C.c_int), ("adaptive", C.c_int), ("seed", C.c_ulonglong),
                 ("restart", C.c_int), ("max_it", C.c_int), ("precision", C.c_int), ("batched", C.c_int),
                 ("use_graph", C.c_int), ("autotune", C.c_int), ("keep_transpose", C.c_int),
-                ("fuse_rows", C.c_int), ("interp_type", C.c_int)]
+                ("fuse_rows", C.c_int), ("interp_type", C.c_int), ("pdl", C.c_int)]
 
 
 class MgdStats(C.Structure):
@@ -85,6 +86,7 @@ def lib():
             "mgd_kernel_launches": (C.c_longlong, []),
             "mgd_relres_noalloc": (I, [I, P, P, P, P, P, P, P]),
             "mgd_plan_info": (I, [P, I, I, pI, pI, pI, pI, pI, pI, pI, pI]),
+            "mgd_setup_phases": (I, [P, P, I]),
             "mgd_last_error": (C.c_char_p, [P]),
             "mgd_destroy": (None, [P]),
         }
@@ -268,6 +270,14 @@ class Solver:
         if nnzp:
             out.update(cf=cf[:n], prp=prp, pci=pci[:nnzp], pv=pv[:nnzp])
         return out
+
+    SETUP_PHASES = ["strength", "pmis", "interp", "transpose", "AP", "RAP", "finalize", "coarse_inverse",
+                    "validate", "blocks", "hierarchies_wall", "pctl", "program_autotune", "krylov_graph"]
+
+    def setup_phases(self):
+        ms = np.zeros(16)
+        self._check(lib().mgd_setup_phases(self.h, ms.ctypes.data_as(C.c_void_p), 16))
+        return {k: round(float(v), 3) for k, v in zip(self.SETUP_PHASES, ms)}
 
     def plan(self):
         """Autotuned launch plan: one list of per-level dicts per V-cycle batch."""

@@ -157,7 +157,7 @@ def test_batched_and_graph_identical(gpu, kind):
     ref = gpu.Solver(autotune=0).setup_system(s, kind)
     xr, itr, _, _ = ref.solve(b)
     for opts in [dict(batched=1), dict(use_graph=1), dict(batched=1, use_graph=1),
-                 dict(batched=1, use_graph=1, precision=0)]:
+                 dict(batched=1, use_graph=1, pdl=0), dict(pdl=0)]:
         slv = gpu.Solver(autotune=0, **opts).setup_system(s, kind)
         x, it, _, _ = slv.solve(b)
         assert it == itr
