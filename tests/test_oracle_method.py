@@ -364,3 +364,64 @@ def test_exti_fgmres_converges_to_dense_solution(orc):
         x, it, rr, st, _ = orc.fgmres(Ao, s.b, M, tol=1e-13, maxit=2000)
         xs = np.linalg.solve(s.scipy().toarray(), s.b)
         assert st == 0 and np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+
+
+# ---------------------------------------------------------------- option #3 inside the preconditioner
+ACCURATE_OPS = {"schur1": {1, 2}, "schur2": {3, 4}, "pctl": {0}}  # C_E, C_g | S_g, S_I | A_a (Section 4)
+
+
+@pytest.mark.parametrize("kind", ["schur1", "schur2", "pctl"])
+def test_option3_tight_tolerance_gives_exact_inverses(orc, kind):
+    # Section 3.5 option #3 with the inner tolerance driven to rounding level:
+    # the listed inverses become exact, every other inverse stays one V-cycle
+    s = I.make_system(3, (16, 13), multigroup=True)   # N = 208 > 100: multilevel hierarchies
+    Ao = orc.csr_of_system(s)
+    M = orc.Block(Ao, s.G, s.N, kind, orc.opts(inner_mode=1, inner_tol=1e-14, inner_maxit=5000))
+    assert M.amg(min(ACCURATE_OPS[kind] - {1}), 0).nlevels >= 2  # a group operator is multilevel
+
+    def cb(op, comp, rhs):
+        h = M.amg(op, comp)
+        if op in ACCURATE_OPS[kind]:  # the operator the method inverts (Section 3.4's diagonal Schur forms)
+            return np.linalg.solve(h.A(0).scipy().toarray(), rhs)
+        return h.vcycle(rhs)
+    v = np.random.default_rng(7).standard_normal(s.n)
+    z = M.apply(v)
+    zr = M.apply(v, cb)
+    assert np.linalg.norm(z - zr) <= 1e-9 * np.linalg.norm(zr)
+    # option #2 (one V-cycle) is far from it: the comparison is not vacuous
+    z2 = orc.Block(Ao, s.G, s.N, kind).apply(v)
+    assert np.linalg.norm(z2 - zr) >= 1e-3 * np.linalg.norm(zr)
+
+
+def test_option3_cycle_counts_are_the_first_to_reach_tolerance(orc):
+    # Schur2, stage 2: S_g z_g = v_g - D_gE w_E with w_E = A_E^{-1} v_E (Eq. 3.2).
+    # The stationary iteration x += V(rhs - S_g x) from x = 0, written here
+    # with scipy matrix-vector products, must stop at the same cycle count as
+    # the oracle and at the first iterate within the 1e-2 inner tolerance
+    s = I.make_system(3, (12, 10), multigroup=True)
+    Ao = orc.csr_of_system(s)
+    tol = 1e-2
+    M = orc.Block(Ao, s.G, s.N, "schur2", orc.opts(inner_mode=1, inner_tol=tol))
+    v = np.random.default_rng(11).standard_normal(s.n)
+    M.apply(v)
+    A, blk = _blocks(s)
+    N, G = s.N, s.G
+    E = G
+    wE = M.amg(0, E).vcycle(v[E * N:(E + 1) * N])
+    for g in range(G):
+        h = M.amg(3, g)
+        S = h.A(0).scipy()
+        rhs = v[g * N:(g + 1) * N] - np.diag(blk(g, E)) * wE
+        x = np.zeros(N)
+        k = 0
+        prev = np.inf
+        while k < 100:
+            nr = np.linalg.norm(rhs - S @ x)
+            if nr <= tol * np.linalg.norm(rhs):
+                break
+            assert nr < prev      # a convergent V-cycle iteration
+            prev = nr
+            x = x + h.vcycle(rhs - S @ x)
+            k += 1
+        assert 1 < k < 100
+        assert M.cycles(3, g) == k, (g, M.cycles(3, g), k)
