@@ -62,8 +62,9 @@ typedef struct mgd_opts {
   double theta_wd;        /* Definition 2 threshold: 0.9 */
   double theta_wc;        /* Definition 1 threshold: 1e-2 */
   double sigma_wc;        /* Section 3.6 switch criterion: 0.5 */
-  double inner_tol;       /* option #3 accuracy for the PCTL p_a: 1e-2 (Section 4) */
-  int inner_maxit;        /* option #3 cycle cap: 100 */
+  double inner_tol;       /* option #3 accuracy (Sections 3.4-3.5, Section 4: 1e-2) for the PCTL p_a and, when
+                             inner_mode, for the inverses listed there */
+  int inner_maxit;        /* option #3 cycle cap: 100 (1 .. 100000) */
   int nvcyc_group;        /* option #2 V-cycles per inverse of a group operator: 1 */
   int nvcyc_E;            /* ... of an E operator: 1 */
   int nvcyc_I;            /* ... of an I operator: 1 */
@@ -85,6 +86,11 @@ typedef struct mgd_opts {
                              classical interpolation, De Sterck, Falgout, Nolting, Yang 2008) */
   int pdl;                /* 1: solve kernels use programmatic dependent launch (each waits on its predecessor
                              in-kernel, so launch latency overlaps the previous kernel); 0: plain launches */
+  int inner_mode;         /* 1: option #3 (Section 3.5) inside the preconditioner for the Schur-type inverses
+                             C_E, C_g (Schur1), S_g, S_I (Schur2) and the PCTL block inverses A_a: x = 0, then
+                             x += V(rhs - A x) until ||rhs - A x|| <= inner_tol ||rhs|| or inner_maxit cycles.
+                             The loop runs on the device (a conditional CUDA graph node when use_graph); the
+                             transposed apply keeps the fixed cycle counts.  0: option #2 (default) */
 } mgd_opts;
 
 /* Fill *o with the defaults listed above.  Returns MGD_EINVAL if o is NULL. */
@@ -159,6 +165,11 @@ int mgd_get_history(mgd_ctx *c, double *h_hist, int cap, int *count);
  * list, see mgd_op_info) for the parity tests. */
 int mgd_op_info(mgd_ctx *c, int op, int *kind, int *comp, int *nlevels, int *use_jacobi, int *coarse_lu);
 int mgd_level_info(mgd_ctx *c, int op, int level, int *n, int *nnz, int *nnzP, int *ncoarse);
+/* *cycles = V-cycles (option #2/#3) applied by the inverse of operator `op`
+ * since its setup, forward and transposed applies together (0 for an
+ * option #1 Jacobi inverse).  Synchronises the context's stream (the option #3 counts
+ * live on the device).  MGD_EINVAL for a bad op or NULL cycles. */
+int mgd_op_cycles(mgd_ctx *c, int op, long long *cycles);
 /* Copy level `level` of operator `op` to host buffers (any may be NULL):
  * A_l as h_rp[n+1], h_ci[nnz], h_v[nnz]; C/F splitting h_cf[n] (1 = C,
  * -1 = F; absent on the coarsest level); P_l as h_prp[n+1], h_pci[nnzP],

@@ -38,6 +38,7 @@ struct Profiler {
   bool on = false;
   unsigned mask = 0;       // classes to record
   bool capturing = false;  // inside stream capture: record graph event nodes
+  bool suppress = false;   // inside a conditional node's body: no event nodes allowed
   struct Pair {
     int cls;
     cudaEvent_t a, b;
@@ -66,7 +67,7 @@ struct Profiler {
     else MGD_CUDA(cudaEventRecord(e, s));
   }
   int begin(cudaStream_t s, int cls) {
-    if (!on || !(mask & (1u << cls))) {
+    if (!on || suppress || !(mask & (1u << cls))) {
       next_detail = -1;
       return -1;
     }
@@ -175,6 +176,7 @@ struct Hier {
   double* cinv = nullptr;
   double* cinvT = nullptr;
   int cn = 0;
+  int* active = nullptr;  // device flag of a device-controlled inverse (nullptr: none)
   int nlev() const { return (int)L.size(); }
 };
 
@@ -545,6 +547,7 @@ static LDesc<T> make_desc(Hier& h, int l, bool trans) {
   d.r = (T*)lv.r;
   d.cinv = trans ? h.cinvT : h.cinv;
   d.cn = h.cn;
+  d.active = trans ? nullptr : h.active;
   return d;
 }
 
@@ -789,6 +792,7 @@ struct InvOp {
   int kind, comp;
   Csr A;               // operator (FP64)
   bool jacobi = false; // option #1
+  bool accurate = false;  // option #3 in the forward apply (inner_mode)
   int count = 1;       // sweeps (#1) or V-cycles (#2)
   Hier h;
   double* jd = nullptr;  // 1/diag(A)
@@ -811,6 +815,14 @@ struct Step {
   std::vector<int> ops;   // INVERT
   int batch = -1;         // index into batches when batched
   double bytes = 0;
+  // INVERT with a device-controlled loop (option #3 or several cycles)
+  bool loop = false;
+  void* inner = nullptr;       // InnerDesc<T>[nloop] (device)
+  InnerCtl* ctl = nullptr;     // device loop state
+  long long* total = nullptr;  // == ctl->total (device), per loop op
+  int* any = nullptr;          // == ctl->any (device)
+  std::vector<int> loop_ops;   // op ids in InnerDesc order
+  int maxn = 0, guard = 0;
 };
 
 struct BlockData {
@@ -860,7 +872,10 @@ struct mgd_ctx {
   mgd::Profiler prof;
   cudaGraphExec_t graph = nullptr;
   bool graph_ok = false;
+  bool capturing = false;            // run_program is being recorded into c->graph
+  cudaStream_t s_body = nullptr;     // stream that records conditional-node bodies
   long long graph_kernels = 0;
+  long long napply = 0, napplyT = 0; // preconditioner applies since setup (forward, transposed)
   mgd_stats st;
   int n_jacobi = 0;
   mgd::PhaseClock phases;
@@ -962,7 +977,7 @@ static void finalize_op(mgd_ctx* c, InvOp& op, cudaStream_t st) {
     op.b = op.h.L[0].b;
     op.x = op.h.L[0].x;
   }
-  if (op.count > 1) {
+  if (op.count > 1 || op.accurate) {
     op.bsave = c->ar.alloc<char>(es * op.n, true, st);
     op.xacc = c->ar.alloc<char>(es * op.n, true, st);
   }
@@ -1045,6 +1060,10 @@ static int add_op(mgd_ctx* c, int kind, int comp, Csr A) {
   op.jacobi = c->o.adaptive && kind != OP_MONO && gamma_wd(c, A) == 0.0;
   op.count = op.jacobi ? c->o.jacobi_sweeps : cycles_for(c->o, kind, comp, c->G);
   if (op.count < 1) op.count = 1;
+  // Section 4: the Schur-type inverses, and the PCTL block inverses, to the inner accuracy
+  op.accurate = c->o.inner_mode && !op.jacobi &&
+                (kind == OP_CE || kind == OP_CG || kind == OP_SG || kind == OP_SI ||
+                 (c->kind == MGD_PCTL && kind == OP_A));
   c->ops.push_back(op);
   return (int)c->ops.size() - 1;
 }
@@ -1089,6 +1108,69 @@ static void apply_jacobi_ops(mgd_ctx* c, const std::vector<int>& ids, bool trans
   }
 }
 
+// The device-controlled loop of one INVERT step.  Eager: the host reads the
+// control kernel's "some operator active" flag after every trip.  Under graph
+// capture: a conditional while node whose body (V-cycle, update, residual,
+// control) is recorded on a second stream; the control kernel sets the node's
+// condition, so a replay runs exactly the trips the eager loop would.
+template <typename T>
+static void run_inner_loop(mgd_ctx* c, const Step& st, VBatch<T>& B) {
+  const InnerDesc<T>* d = (const InnerDesc<T>*)st.inner;
+  const int nd = (int)st.loop_ops.size();
+  const cudaGraphConditionalHandle none = 0;
+  launch_inner_begin<T>(d, nd, st.maxn, st.ctl, c->s);
+  if (!c->capturing) {
+    launch_inner_ctl<T>(d, nd, st.ctl, 1, 0, none, c->s);
+    for (int trip = 0; trip < st.guard && read_int(st.any, c->s); ++trip) {
+      run_vbatch<T>(B, false, c->s, c->prof);
+      launch_inner_update<T>(d, nd, st.maxn, c->s);
+      launch_inner_resid<T>(d, nd, st.maxn, st.ctl, c->s);
+      launch_inner_ctl<T>(d, nd, st.ctl, 0, 0, none, c->s);
+    }
+    launch_inner_end<T>(d, nd, st.maxn, c->s);
+    return;
+  }
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  MGD_CUDA(cudaStreamGetCaptureInfo(c->s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle h;
+  MGD_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+  launch_inner_ctl<T>(d, nd, st.ctl, 1, 1, h, c->s);
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  MGD_CUDA(cudaStreamGetCaptureInfo(c->s, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  MGD_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  MGD_CUDA(cudaStreamUpdateCaptureDependencies(c->s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  // body nodes: kernels only (no event nodes, no programmatic edges)
+  const bool pdl = tl_pdl;
+  tl_pdl = false;
+  c->prof.suppress = true;
+  MGD_CUDA(cudaStreamBeginCaptureToGraph(c->s_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaGraph_t recorded = nullptr;
+  try {
+    run_vbatch<T>(B, false, c->s_body, c->prof);
+    launch_inner_update<T>(d, nd, st.maxn, c->s_body);
+    launch_inner_resid<T>(d, nd, st.maxn, st.ctl, c->s_body);
+    launch_inner_ctl<T>(d, nd, st.ctl, 0, 1, h, c->s_body);
+  } catch (...) {
+    cudaStreamEndCapture(c->s_body, &recorded);
+    c->prof.suppress = false;
+    tl_pdl = pdl;
+    throw;
+  }
+  c->prof.suppress = false;
+  MGD_CUDA(cudaStreamEndCapture(c->s_body, &recorded));
+  launch_inner_end<T>(d, nd, st.maxn, c->s);  // after the conditional node: a plain edge
+  tl_pdl = pdl;
+}
+
 template <typename T>
 static void run_invert(mgd_ctx* c, const Step& st, bool trans) {
   std::vector<int> jac, vc;
@@ -1096,6 +1178,10 @@ static void run_invert(mgd_ctx* c, const Step& st, bool trans) {
   apply_jacobi_ops<T>(c, jac, trans);
   if (vc.empty()) return;
   auto& B = batches<T>(c)[st.batch];
+  if (!trans && st.loop) {
+    run_inner_loop<T>(c, st, B);
+    return;
+  }
   int maxcount = 1;
   for (int id : vc) maxcount = std::max(maxcount, c->ops[id].count);
   if (maxcount == 1) {
@@ -1426,6 +1512,77 @@ static std::vector<long long> tune_key(const VBatch<T>& vb, bool trans, int fuse
 }
 
 // group INVERT steps into batches (one batch per step when batched, else one per op)
+// INVERT steps whose V-cycle operators need the device-controlled loop
+// (option #3, or more than one cycle): a flag per hierarchy (read by the
+// V-cycle kernels, so it must exist before the plans are built), the loop
+// descriptors and the loop state.
+template <typename T>
+static void setup_loops(mgd_ctx* c) {
+  static const int kOne = 1;
+  for (Step& st : c->steps) {
+    if (st.type != Step::INVERT || st.batch < 0) continue;
+    std::vector<int> vc;
+    bool need = false;
+    for (int id : st.ops) {
+      const InvOp& op = c->ops[id];
+      if (op.jacobi) continue;
+      vc.push_back(id);
+      need = need || op.accurate || op.count > 1;
+    }
+    if (!need) continue;
+    std::vector<InnerDesc<T>> ds;
+    int maxn = 0, guard = std::max(1, c->o.inner_maxit);
+    for (int id : vc) {
+      InvOp& op = c->ops[id];
+      const size_t es = sizeof(T);
+      if (!op.h.active) {
+        op.h.active = c->ar.alloc<int>(1);
+        MGD_CUDA(cudaMemcpyAsync(op.h.active, &kOne, sizeof(int), cudaMemcpyHostToDevice, c->s));
+      }
+      if (!op.bsave) op.bsave = c->ar.alloc<char>(es * op.n, true, c->s);
+      if (!op.xacc) op.xacc = c->ar.alloc<char>(es * op.n, true, c->s);
+      Level& l0 = op.h.L[0];
+      InnerDesc<T> d;
+      memset(&d, 0, sizeof(d));
+      d.rp = l0.A.rp;
+      d.ci = l0.A.ci;
+      d.v = pick<T>(l0.A.v, l0.v32);
+      d.b = (T*)op.b;
+      d.x = (T*)op.x;
+      d.rhs = (T*)op.bsave;
+      d.xacc = (T*)op.xacc;
+      d.n = op.n;
+      d.accurate = op.accurate ? 1 : 0;
+      d.count = op.count;
+      d.active = op.h.active;
+      ds.push_back(d);
+      maxn = std::max(maxn, op.n);
+      guard = std::max(guard, op.count);
+    }
+    const int nd = (int)ds.size();
+    InnerCtl h;
+    memset(&h, 0, sizeof(h));
+    h.nops = nd;
+    h.maxit = std::max(1, c->o.inner_maxit);
+    h.guard = guard;
+    h.tol = c->o.inner_tol;
+    h.part = c->ar.alloc<double>((size_t)nd * kInnerParts, true, c->s);
+    h.nr0 = c->ar.alloc<double>(nd, true, c->s);
+    h.cycles = c->ar.alloc<int>(nd, true, c->s);
+    h.total = c->ar.alloc<long long>(nd, true, c->s);
+    h.trips = c->ar.alloc<int>(1, true, c->s);
+    h.any = c->ar.alloc<int>(1, true, c->s);
+    st.loop = true;
+    st.loop_ops = vc;
+    st.maxn = maxn;
+    st.guard = guard;
+    st.total = h.total;
+    st.any = h.any;
+    st.inner = upload_vec(c, ds);
+    st.ctl = (InnerCtl*)upload_vec(c, std::vector<InnerCtl>{h});
+  }
+}
+
 template <typename T>
 static void build_batches(mgd_ctx* c) {
   auto& B = batches<T>(c);
@@ -1468,6 +1625,7 @@ static void build_batches(mgd_ctx* c) {
     }
   }
   c->steps = out;
+  setup_loops<T>(c);
   for (auto& vb : B) {
     build_plan<T>(c->ar, vb, false, c->s);
     if (c->o.keep_transpose) build_plan<T>(c->ar, vb, true, c->s);
@@ -1556,6 +1714,7 @@ static int guarded(mgd_ctx* c, F&& f) {
 }
 
 static void precond_apply(mgd_ctx* c, const double* v, double* z, bool trans) {
+  (trans ? c->napplyT : c->napply)++;
   launch_set_io(c->io, v, z, c->s);
   if (!trans && c->graph_ok) {
     MGD_CUDA(cudaGraphLaunch(c->graph, c->s));
@@ -1578,6 +1737,8 @@ static void capture_graph(mgd_ctx* c) {
   c->prof.drop_graph_pairs();
   long long k0 = __atomic_load_n(&g_kernel_launches, __ATOMIC_RELAXED);
   c->prof.capturing = true;
+  c->capturing = true;
+  if (!c->s_body) MGD_CUDA(cudaStreamCreateWithFlags(&c->s_body, cudaStreamNonBlocking));
   MGD_CUDA(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
   try {
     if (mixed(c)) run_program<float>(c, false);
@@ -1585,9 +1746,11 @@ static void capture_graph(mgd_ctx* c) {
   } catch (...) {
     cudaStreamEndCapture(c->s, &g);
     c->prof.capturing = false;
+    c->capturing = false;
     throw;
   }
   c->prof.capturing = false;
+  c->capturing = false;
   MGD_CUDA(cudaStreamEndCapture(c->s, &g));
   // kernels recorded into the graph (the counter counted them at capture)
   long long k1 = __atomic_load_n(&g_kernel_launches, __ATOMIC_RELAXED);
@@ -1610,6 +1773,7 @@ static void free_setup(mgd_ctx* c) {
   c->vb32.clear();
   c->bd = BlockData();
   c->ready = false;
+  c->napply = c->napplyT = 0;
   if (c->hpin) cudaFreeHost(c->hpin);
   c->hpin = nullptr;
 }
@@ -1827,8 +1991,6 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
           } else {
             run_vbatch<float>(vb32, false, s, c->prof);
           }
-          double* e = rhs + 0;  // reuse: e is added into p below
-          (void)e;
           Scratch t2(s);
           double* ed = t2.alloc<double>(N);
           launch_cast_f32_f64(N, (const float*)op.x, ed, s);
@@ -2123,6 +2285,7 @@ int mgd_opts_default(mgd_opts* o) {
   o->fuse_rows = 0;
   o->interp_type = 0;
   o->pdl = 1;
+  o->inner_mode = 0;
   return MGD_OK;
 }
 
@@ -2133,8 +2296,11 @@ int mgd_create(mgd_ctx** out, const mgd_opts* o, void* stream) {
   if (!c) return MGD_ENOMEM;
   if (o) c->o = *o;
   else mgd_opts_default(&c->o);
-  if (c->o.max_coarse < 1 || c->o.max_coarse > 4096 || c->o.max_levels < 1 || c->o.restart < 1 ||
-      c->o.restart > 30 || c->o.precision < 0 || c->o.precision > 1) {
+  const mgd_opts& q = c->o;
+  if (q.max_coarse < 1 || q.max_coarse > 4096 || q.max_levels < 1 || q.restart < 1 || q.restart > 30 ||
+      q.precision < 0 || q.precision > 1 || q.inner_mode < 0 || q.inner_mode > 1 || q.inner_maxit < 1 ||
+      q.inner_maxit > 100000 || !(q.inner_tol >= 0.0) || q.nvcyc_group > 1000 || q.nvcyc_E > 1000 ||
+      q.nvcyc_I > 1000 || q.nvcyc_other > 1000 || q.jacobi_sweeps > 1000) {
     delete c;
     return MGD_EINVAL;
   }
@@ -2294,6 +2460,33 @@ int mgd_level_info(mgd_ctx* c, int op, int level, int* n, int* nnz, int* nnzP, i
   return MGD_OK;
 }
 
+int mgd_op_cycles(mgd_ctx* c, int op, long long* cycles) {
+  return guarded(c, [&]() -> int {
+    if (!c->ready || op < 0 || op >= (int)c->ops.size() || !cycles) throw Error{MGD_EINVAL, "bad operator"};
+    const InvOp& o = c->ops[op];
+    long long n = 0;
+    if (!o.jacobi) {
+      for (const Step& st : c->steps) {
+        if (st.type != Step::INVERT) continue;
+        if (std::find(st.ops.begin(), st.ops.end(), op) == st.ops.end()) continue;
+        n += (long long)o.count * c->napplyT;  // the transposed apply runs the fixed count
+        auto it = std::find(st.loop_ops.begin(), st.loop_ops.end(), op);
+        if (st.loop && it != st.loop_ops.end()) {
+          long long t = 0;
+          MGD_CUDA(cudaMemcpyAsync(&t, st.total + (it - st.loop_ops.begin()), sizeof(t), cudaMemcpyDeviceToHost,
+                                   c->s));
+          MGD_CUDA(cudaStreamSynchronize(c->s));
+          n += t;
+        } else {
+          n += (long long)o.count * c->napply;
+        }
+      }
+    }
+    *cycles = n;
+    return MGD_OK;
+  });
+}
+
 int mgd_level_export(mgd_ctx* c, int op, int level, int* h_rp, int* h_ci, double* h_v, signed char* h_cf,
                      int* h_prp, int* h_pci, double* h_pv) {
   return guarded(c, [&]() -> int {
@@ -2411,6 +2604,7 @@ long long mgd_kernel_launches(void) { return __atomic_load_n(&g_kernel_launches,
 void mgd_destroy(mgd_ctx* c) {
   if (!c) return;
   free_setup(c);
+  if (c->s_body) cudaStreamDestroy(c->s_body);
   if (c->hpin) cudaFreeHost(c->hpin);
   c->pool.destroy();
   delete c;

@@ -205,7 +205,18 @@ struct LDesc {
   // coarsest level: dense inverse (FP64, row-major cn x cn)
   const double* cinv;
   int cn;
+  // option #3 / multi-cycle loops: the subsystem's flag (nullptr: always
+  // run); a V-cycle kernel skips a subsystem whose flag is 0
+  const int* active;
 };
+
+// the V-cycle kernels' first statement after the dependency wait: leave a
+// subsystem that its inner loop has already finished (uniform per CTA)
+#define MGD_SKIP_INACTIVE(d) \
+  do {                        \
+    const int* a_ = (d)->active; \
+    if (a_ && *a_ == 0) return; \
+  } while (0)
 
 // One subsystem's share of the fused coarse-level kernel: its level
 // descriptors from the first fused level to its coarsest level.
@@ -251,6 +262,37 @@ struct JacDesc {      // option #1: x = dinv (.) b
   T* x;
   const T* b;
   const T* dinv;
+};
+
+// One operator of a device-controlled inverse (Section 3.5): option #3
+// (x = 0; x += V(rhs - A x) until ||rhs - A x|| <= tol ||rhs||, at most
+// maxit cycles) or a fixed number of cycles (x = V rhs; x += V(rhs - A x)).
+// The V-cycle reads b and writes x (the hierarchy's level-0 vectors).
+template <typename T>
+struct InnerDesc {
+  const int* rp;   // level-0 operator, CSR
+  const int* ci;
+  const T* v;
+  T* b;            // V-cycle input: the residual
+  T* x;            // V-cycle output: the correction (the solution after the loop)
+  T* rhs;          // the right-hand side, saved
+  T* xacc;         // accumulated solution
+  int n;
+  int accurate;    // 1: option #3, 0: `count` cycles
+  int count;
+  int* active;     // read by the V-cycle kernels of this operator's hierarchy
+};
+// loop state of one INVERT step (device memory)
+constexpr int kInnerParts = 608;  // partial-norm blocks per operator (4 per SM)
+struct InnerCtl {
+  int nops, maxit, guard;  // guard: hard cap on loop trips (>= every op's cap)
+  double tol;
+  double* part;            // nops x kInnerParts partial sums of squares
+  double* nr0;             // ||rhs|| per op
+  int* cycles;             // cycles of the current apply, per op
+  long long* total;        // cycles since setup, per op
+  int* trips;              // loop trips of the current apply
+  int* any;                // 1 while some op is active (read by the host loop)
 };
 
 // ------------------------------------------------------------------ setup launchers (setup_kernels.cu)
@@ -338,6 +380,24 @@ void launch_residual(int fmt, int n, const int* rp, const int* ci, const T* v, c
                      const T* sv, const T* b, const T* x, T* r, cudaStream_t s);
 template <typename T>
 void launch_axpy(int n, T* y, const T* x, cudaStream_t s);  // y += x
+
+// device-controlled inverse loop (one INVERT step, nd operators):
+//   begin: rhs = b, xacc = 0, partial ||b||^2; ctl(first)
+//   loop while any active: V-cycle; update (xacc += x); resid (b = rhs - A xacc,
+//   partial ||b||^2); ctl
+//   end: x = xacc, b = rhs, active = 1
+// ctl sets the conditional node's value when use_cond (graph replay)
+template <typename T>
+void launch_inner_begin(const InnerDesc<T>* d, int nd, int maxn, const InnerCtl* ctl, cudaStream_t s);
+template <typename T>
+void launch_inner_update(const InnerDesc<T>* d, int nd, int maxn, cudaStream_t s);
+template <typename T>
+void launch_inner_resid(const InnerDesc<T>* d, int nd, int maxn, const InnerCtl* ctl, cudaStream_t s);
+template <typename T>
+void launch_inner_ctl(const InnerDesc<T>* d, int nd, const InnerCtl* ctl, int first, int use_cond,
+                      cudaGraphConditionalHandle cond, cudaStream_t s);
+template <typename T>
+void launch_inner_end(const InnerDesc<T>* d, int nd, int maxn, cudaStream_t s);
 
 void launch_spmv_f64(int fmt, int n, const int* rp, const int* ci, const double* v, const int* sptr,
                      const int* sci, const double* sv, const double* x, double* y, cudaStream_t s);

@@ -413,3 +413,185 @@ void launch_lincomb(int n, double a, const double* x, double b, const double* y,
 }
 
 }  // namespace mgd
+
+// ---------------------------------------------------------------- device-controlled inverses (Section 3.5)
+// Option #3 runs V-cycles on the residual until ||rhs - A x|| <= tol ||rhs||;
+// a fixed count > 1 runs the same recurrence a set number of times.  Each
+// trip: V-cycle (inactive operators skip it), xacc += x, b = rhs - A xacc with
+// partial sums of b^2 in a fixed block order, then one control kernel that
+// turns the partial sums into norms, advances the per-operator cycle counts
+// and decides which operators stay active.  The host never reads a norm: the
+// control kernel also sets the value of the graph's conditional while node.
+namespace mgd {
+
+__device__ __forceinline__ void inner_block_partial(double acc, double* out) {
+  __shared__ double sh[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[k];
+    *out = t;
+  }
+}
+
+// rhs = b, xacc = 0, partial sums of b^2
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_inner_begin(const InnerDesc<T>* __restrict__ ds,
+                                                          const InnerCtl* __restrict__ ctl) {
+  MGD_PDL_ENTRY();
+  const InnerDesc<T>* d = ds + blockIdx.y;
+  const int n = d->n;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    T bi = d->b[i];
+    d->rhs[i] = bi;
+    d->xacc[i] = T(0);
+    acc += (double)bi * (double)bi;
+  }
+  inner_block_partial(acc, ctl->part + (size_t)blockIdx.y * kInnerParts + blockIdx.x);
+}
+
+// xacc += x for the active operators
+template <typename T>
+__global__ void k_inner_update(const InnerDesc<T>* __restrict__ ds) {
+  MGD_PDL_ENTRY();
+  const InnerDesc<T>* d = ds + blockIdx.y;
+  if (*d->active == 0) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d->n) d->xacc[i] = d->xacc[i] + d->x[i];
+}
+
+// b = rhs - A xacc (groups of 4 lanes per row; every thread runs the same
+// number of row steps) and partial sums of b^2, for the active operators
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_inner_resid(const InnerDesc<T>* __restrict__ ds,
+                                                          const InnerCtl* __restrict__ ctl) {
+  MGD_PDL_ENTRY();
+  const InnerDesc<T>* d = ds + blockIdx.y;
+  if (*d->active == 0) return;
+  constexpr int TPR = 4;
+  const int n = d->n;
+  const int lane = threadIdx.x % TPR;
+  const long long stride = (long long)gridDim.x * blockDim.x / TPR;
+  const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / TPR;
+  const long long steps = (n + stride - 1) / stride;
+  double acc = 0.0;
+  for (long long st = 0; st < steps; ++st) {
+    long long row = g + st * stride;
+    bool ok = row < n;
+    T s = T(0);
+    if (ok) {
+      int e = d->rp[row + 1];
+      for (int p = d->rp[row] + lane; p < e; p += TPR) s += d->v[p] * d->xacc[d->ci[p]];
+    }
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (ok && lane == 0) {
+      T r = d->rhs[row] - s;
+      d->b[row] = r;
+      acc += (double)r * (double)r;
+    }
+  }
+  inner_block_partial(acc, ctl->part + (size_t)blockIdx.y * kInnerParts + blockIdx.x);
+}
+
+// norms from the partial sums (one warp per operator, fixed order), cycle
+// counts, activity; thread 0 publishes "some operator active" to the host
+// flag and, under graph replay, to the conditional node
+template <typename T>
+__global__ void k_inner_ctl(const InnerDesc<T>* __restrict__ ds, int nd, const InnerCtl* __restrict__ ctl, int first,
+                            int use_cond, cudaGraphConditionalHandle cond) {
+  MGD_PDL_ENTRY();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int mine = 0;
+  for (int o = warp; o < nd; o += blockDim.x >> 5) {
+    const InnerDesc<T>* d = ds + o;
+    double sum = 0.0;
+    for (int p = lane; p < kInnerParts; p += 32) sum += ctl->part[(size_t)o * kInnerParts + p];
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, k);
+    if (lane == 0) {
+      double nr = sqrt(sum);
+      int act;
+      if (first) {
+        ctl->nr0[o] = nr;
+        ctl->cycles[o] = 0;
+        act = d->accurate ? !(nr <= ctl->tol * nr) : (d->count > 0);
+      } else if (*d->active) {
+        int c = ++ctl->cycles[o];
+        ctl->total[o] += 1;
+        act = d->accurate ? (!(nr <= ctl->tol * ctl->nr0[o]) && c < ctl->maxit) : (c < d->count);
+      } else {
+        act = 0;
+      }
+      *d->active = act;
+      mine |= act;
+    }
+  }
+  int any = __syncthreads_or(mine);
+  if (threadIdx.x == 0) {
+    int t = first ? 0 : *ctl->trips + 1;
+    *ctl->trips = t;
+    if (t >= ctl->guard) any = 0;  // hard cap: every operator's own cap is below it
+    *ctl->any = any;
+    if (use_cond) cudaGraphSetConditional(cond, any ? 1u : 0u);
+  }
+}
+
+// x = xacc, b = rhs, active = 1
+template <typename T>
+__global__ void k_inner_end(const InnerDesc<T>* __restrict__ ds) {
+  MGD_PDL_ENTRY();
+  const InnerDesc<T>* d = ds + blockIdx.y;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d->n) {
+    d->x[i] = d->xacc[i];
+    d->b[i] = d->rhs[i];
+  }
+  if (i == 0) *d->active = 1;
+}
+
+template <typename T>
+void launch_inner_begin(const InnerDesc<T>* d, int nd, int maxn, const InnerCtl* ctl, cudaStream_t s) {
+  (void)maxn;
+  launch_k(k_inner_begin<T>, dim3(kInnerParts, nd), dim3(kThreads), 0, s, d, ctl);
+  MGD_LAUNCH_CHECK();
+}
+template <typename T>
+void launch_inner_update(const InnerDesc<T>* d, int nd, int maxn, cudaStream_t s) {
+  launch_k(k_inner_update<T>, dim3(cdiv(maxn, kThreads), nd), dim3(kThreads), 0, s, d);
+  MGD_LAUNCH_CHECK();
+}
+template <typename T>
+void launch_inner_resid(const InnerDesc<T>* d, int nd, int maxn, const InnerCtl* ctl, cudaStream_t s) {
+  (void)maxn;
+  launch_k(k_inner_resid<T>, dim3(kInnerParts, nd), dim3(kThreads), 0, s, d, ctl);
+  MGD_LAUNCH_CHECK();
+}
+template <typename T>
+void launch_inner_ctl(const InnerDesc<T>* d, int nd, const InnerCtl* ctl, int first, int use_cond,
+                      cudaGraphConditionalHandle cond, cudaStream_t s) {
+  launch_k(k_inner_ctl<T>, dim3(1), dim3(kThreads), 0, s, d, nd, ctl, first, use_cond, cond);
+  MGD_LAUNCH_CHECK();
+}
+template <typename T>
+void launch_inner_end(const InnerDesc<T>* d, int nd, int maxn, cudaStream_t s) {
+  launch_k(k_inner_end<T>, dim3(cdiv(std::max(maxn, 1), kThreads), nd), dim3(kThreads), 0, s, d);
+  MGD_LAUNCH_CHECK();
+}
+
+#define MGD_INNER_INST(T)                                                                                      \
+  template void launch_inner_begin<T>(const InnerDesc<T>*, int, int, const InnerCtl*, cudaStream_t);          \
+  template void launch_inner_update<T>(const InnerDesc<T>*, int, int, cudaStream_t);                          \
+  template void launch_inner_resid<T>(const InnerDesc<T>*, int, int, const InnerCtl*, cudaStream_t);          \
+  template void launch_inner_ctl<T>(const InnerDesc<T>*, int, const InnerCtl*, int, int,                      \
+                                    cudaGraphConditionalHandle, cudaStream_t);                                 \
+  template void launch_inner_end<T>(const InnerDesc<T>*, int, int, cudaStream_t);
+MGD_INNER_INST(double)
+MGD_INNER_INST(float)
+#undef MGD_INNER_INST
+
+}  // namespace mgd

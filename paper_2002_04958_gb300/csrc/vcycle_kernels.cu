@@ -22,6 +22,7 @@ template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_pre(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
+  MGD_SKIP_INACTIVE(d);
   constexpr int TPR = FmtTraits<FMT>::tpr;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   int row = g / TPR, lane = g % TPR;
@@ -43,6 +44,7 @@ template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_post(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
+  MGD_SKIP_INACTIVE(d);
   constexpr int TPR = FmtTraits<FMT>::tpr;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   int row = g / TPR, lane = g % TPR;
@@ -59,6 +61,7 @@ template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_restrict(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
+  MGD_SKIP_INACTIVE(d);
   constexpr int TPR = FmtTraits<FMT>::tpr;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   int row = g / TPR, lane = g % TPR;
@@ -74,6 +77,7 @@ template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_prolong(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
+  MGD_SKIP_INACTIVE(d);
   constexpr int TPR = FmtTraits<FMT>::tpr;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   int row = g / TPR, lane = g % TPR;
@@ -90,6 +94,7 @@ template <typename T>
 __global__ void k_jac1(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
+  MGD_SKIP_INACTIVE(d);
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < d->n) d->xt[i] = d->dinv[i] * d->b[i];
 }
@@ -99,6 +104,7 @@ template <typename T>
 __global__ void k_coarse(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
+  MGD_SKIP_INACTIVE(d);
   extern __shared__ double sb[];
   int n = d->cn;
   for (int j = threadIdx.x; j < n; j += blockDim.x) sb[j] = (double)d->b[j];
@@ -186,6 +192,7 @@ __global__ void __launch_bounds__(kTailThreads) k_vtail(const TailSub<T>* __rest
   cg::cluster_group cl = cg::this_cluster();
   const int cs = (int)cl.num_blocks();
   const TailSub<T> S = subs[blockIdx.x / cs];
+  MGD_SKIP_INACTIVE(S.lev);  // the same flag for every CTA of the cluster
   const int rank = (int)cl.block_rank();
   const int lane = threadIdx.x % kTailTpr;
   const int gwarp = rank * (kTailThreads / 32) + (int)(threadIdx.x >> 5);

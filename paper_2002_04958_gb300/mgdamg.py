@@ -25,7 +25,7 @@ ENTRY_POINTS = ["mgd_opts_default", "mgd_create", "mgd_setup", "mgd_update_value
                 "mgd_solve_transpose", "mgd_grad_values", "mgd_precond_apply", "mgd_get_stats", "mgd_get_history",
                 "mgd_op_info", "mgd_level_info", "mgd_level_export", "mgd_block_vector", "mgd_coupling_dropped",
                 "mgd_profile_enable", "mgd_profile_read", "mgd_kernel_launches", "mgd_last_error", "mgd_destroy", "mgd_plan_info",
-                "mgd_setup_phases",
+                "mgd_setup_phases", "mgd_op_cycles",
                 "mgd_relres_noalloc"]
 
 
@@ -37,7 +37,7 @@ class MgdOpts(C.Structure):
                 ("jacobi_sweeps", C.c_int), ("adaptive", C.c_int), ("seed", C.c_ulonglong),
                 ("restart", C.c_int), ("max_it", C.c_int), ("precision", C.c_int), ("batched", C.c_int),
                 ("use_graph", C.c_int), ("autotune", C.c_int), ("keep_transpose", C.c_int),
-                ("fuse_rows", C.c_int), ("interp_type", C.c_int), ("pdl", C.c_int)]
+                ("fuse_rows", C.c_int), ("interp_type", C.c_int), ("pdl", C.c_int), ("inner_mode", C.c_int)]
 
 
 class MgdStats(C.Structure):
@@ -78,6 +78,7 @@ def lib():
             "mgd_get_history": (I, [P, P, I, pI]),
             "mgd_op_info": (I, [P, I, pI, pI, pI, pI, pI]),
             "mgd_level_info": (I, [P, I, I, pI, pI, pI, pI]),
+            "mgd_op_cycles": (I, [P, I, pLL]),
             "mgd_level_export": (I, [P, I, I, P, P, P, P, P, P, P]),
             "mgd_block_vector": (I, [P, I, I, I, P]),
             "mgd_coupling_dropped": (I, [P, I, I]),
@@ -250,6 +251,12 @@ class Solver:
         v = [C.c_int() for _ in range(5)]
         self._check(lib().mgd_op_info(self.h, op, *[C.byref(x) for x in v]))
         return dict(zip(["kind", "comp", "nlevels", "use_jacobi", "coarse_lu"], [x.value for x in v]))
+
+    def op_cycles(self, op):
+        """V-cycles applied by operator op's inverse since setup (forward and transposed applies)."""
+        v = C.c_longlong()
+        self._check(lib().mgd_op_cycles(self.h, op, C.byref(v)))
+        return v.value
 
     def level(self, op, l):
         """Host copies of level l of operator op: A (rp, ci, v), CF, P (rp, ci, v)."""

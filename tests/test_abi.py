@@ -38,8 +38,9 @@ def test_opts_defaults_and_struct_layout(built):
     assert o.theta_str == 0.25 and o.max_coarse == 100 and o.max_levels == 25
     assert o.theta_wd == 0.9 and o.theta_wc == 1e-2 and o.sigma_wc == 0.5 and o.inner_tol == 1e-2
     assert o.restart == 30 and o.nvcyc_group == 1 and o.precision == 0
+    assert o.inner_mode == 0 and o.inner_maxit == 100
     # the ctypes mirror has the C struct's size: the library writes every field
-    assert C.sizeof(mgdamg.MgdOpts) == 128 and C.sizeof(mgdamg.MgdStats) == 112
+    assert C.sizeof(mgdamg.MgdOpts) == 136 and C.sizeof(mgdamg.MgdStats) == 112
     assert mgdamg.lib().mgd_kernel_launches() >= 0
     assert mgdamg.lib().mgd_opts_default(None) == 1
 
@@ -51,3 +52,31 @@ def test_no_cpu_fallback(built):
         pytest.skip("GPU present")
     with pytest.raises(RuntimeError):
         mgdamg.Solver()
+
+
+def test_struct_layout_matches_c_compiler(tmp_path):
+    """Sizes and field offsets of the ctypes mirrors, as gcc lays out the header's structs."""
+    import shutil
+    import subprocess
+    from paper_2002_04958_gb300 import mgdamg
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in mgdamg.MgdOpts._fields_]
+    sfields = [f for f, _ in mgdamg.MgdStats._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mgdamg.h"', 'int main(void) {',
+             '  printf("%zu %zu\\n", sizeof(mgd_opts), sizeof(mgd_stats));']
+    lines += [f'  printf("%zu\\n", offsetof(mgd_opts, {f}));' for f in fields]
+    lines += [f'  printf("%zu\\n", offsetof(mgd_stats, {f}));' for f in sfields]
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    vals = [int(v) for v in out]
+    assert vals[0] == C.sizeof(mgdamg.MgdOpts) and vals[1] == C.sizeof(mgdamg.MgdStats)
+    offs = vals[2:]
+    for k, f in enumerate(fields):
+        assert offs[k] == getattr(mgdamg.MgdOpts, f).offset, f
+    for k, f in enumerate(sfields):
+        assert offs[len(fields) + k] == getattr(mgdamg.MgdStats, f).offset, f
