@@ -272,6 +272,9 @@ PRESETS = {
     2: dict(G=20, dims=(256, 256), multigroup=True, inclusion=False),
     3: dict(G=20, dims=(96, 96, 96), multigroup=True, inclusion=False),
     4: dict(G=4, dims=(256, 256), multigroup=True, inclusion=False),
+    # Eq. 2.1 as printed: the electron energy diffuses too (E gets a stencil)
+    5: dict(G=1, dims=(1024, 1024), multigroup=False, inclusion=True, diffuse_E=True),
+    6: dict(G=20, dims=(256, 256), multigroup=True, inclusion=False, diffuse_E=True),
 }
 
 PRESET_NAMES = {
@@ -280,6 +283,8 @@ PRESET_NAMES = {
     2: "G20_256x256_blockdiag_fp32vcycle",
     3: "G20_96x96x96_Schur2_fp32vcycle",
     4: "G4_256x256_adjoint",
+    5: "G1_3T_1024x1024_inclusion_diffuseE_Schur1",
+    6: "G20_256x256_diffuseE_Schur2_cycles311",
 }
 
 
@@ -288,4 +293,4 @@ def preset(i, dims=None, seed=0):
     if dims is not None:
         p["dims"] = tuple(dims)
     return make_system(p["G"], p["dims"], seed=seed, multigroup=p["multigroup"],
-                       inclusion=p["inclusion"], name=PRESET_NAMES[i])
+                       inclusion=p["inclusion"], diffuse_E=p.get("diffuse_E", False), name=PRESET_NAMES[i])

@@ -32,6 +32,7 @@ def main():
     ap.add_argument("--timing", type=int, default=1, help="0: no CUDA events (for profiler runs)")
     ap.add_argument("--solve", action="store_true", help="also time one full solve by kernel class")
     ap.add_argument("--interp", type=int, default=0)
+    ap.add_argument("--inner", type=int, default=0, help="1: option #3 inverses")
     args = ap.parse_args()
 
     import torch
@@ -41,7 +42,8 @@ def main():
     build()
     s = inputs.preset(args.config)
     slv = mgdamg.Solver(precision=args.precision, batched=args.batched, use_graph=args.graph,
-                        autotune=0 if args.no_autotune else 1, interp_type=args.interp)
+                        autotune=0 if args.no_autotune else 1, interp_type=args.interp,
+                        inner_mode=args.inner)
     slv.setup_system(s, args.kind)
     v = torch.from_numpy(s.b).cuda()
     if args.timing:

@@ -258,6 +258,10 @@ class Solver:
         self._check(lib().mgd_op_cycles(self.h, op, C.byref(v)))
         return v.value
 
+    def total_cycles(self):
+        """V-cycles applied by every inverse since setup."""
+        return sum(self.op_cycles(k) for k in range(self.stats()["n_ops"]))
+
     def level(self, op, l):
         """Host copies of level l of operator op: A (rp, ci, v), CF, P (rp, ci, v)."""
         n, nnz, nnzp, ncoarse = (C.c_int() for _ in range(4))

@@ -77,6 +77,26 @@ def test_generator_block_structure(G, dims, mg):
         assert np.all(np.diff(c) > 0)
 
 
+@pytest.mark.parametrize("preset", [5, 6])
+def test_generator_diffuse_e_structure(preset):
+    # Eq. 2.1 as printed: E diffuses with the groups' stencil; every other rule unchanged
+    s = I.preset(preset, dims=(7, 6))
+    G, N = s.G, s.N
+    faces = sum(N // d * (d - 1) for d in (7, 6))
+    assert s.nnz == (G + 2) * (N + 2 * faces) + 2 * N * (G + 1)
+    A = s.scipy().toarray()
+    E = G
+    AE = A[E * N:(E + 1) * N, E * N:(E + 1) * N]
+    A0 = A[:N, :N]
+    assert np.array_equal(AE != 0, A0 != 0)
+    assert np.array_equal(AE, AE.T)
+    d = np.diag(A)
+    assert np.all(d - (np.abs(A).sum(1) - d) >= 1.0 - 1e-12 * d.max())
+    t = I.preset(preset - 4, dims=(7, 6))   # the same system without E diffusion
+    assert np.array_equal(np.delete(A, np.s_[E * N:(E + 1) * N], 0),
+                          np.delete(t.scipy().toarray(), np.s_[E * N:(E + 1) * N], 0))
+
+
 def test_generator_tpfa_values_by_hand():
     # 2x1 grid, one group: cell diffusion k0, k1 -> face T = 2 k0 k1 / (k0+k1),
     # boundary faces 2k (three per cell in 2D with ny=1: left/right ends + bottom + top)
