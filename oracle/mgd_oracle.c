@@ -89,6 +89,7 @@ void or_default_opts(or_opts *o) {
   o->seed = 0;
   o->inner_mode = 0;
   o->interp_type = 0;
+  o->smoother = 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -341,6 +342,59 @@ int or_pmis(const or_csr *A, const uint8_t *S, uint64_t seed, int level, int8_t 
 
 int or_pmis_weights(const or_csr *A, const uint8_t *S, const double *w, int8_t *CF) {
   return pmis_core(A, S, w, 0, 0, CF);
+}
+
+/* Jones-Plassmann colouring (the Gauss-Seidel order of the smoother) of the
+   symmetrised graph: i and j are neighbours when a_ij or a_ji is stored.
+   Rounds over the uncoloured points, all taken simultaneously from the
+   colours of the previous round. */
+static int colour_taken(const or_csr *A, const or_csr *AT, int i, const int *colour, int c) {
+  for (int p = A->rp[i]; p < A->rp[i + 1]; ++p)
+    if (A->ci[p] != i && colour[A->ci[p]] == c) return 1;
+  for (int p = AT->rp[i]; p < AT->rp[i + 1]; ++p)
+    if (AT->ci[p] != i && colour[AT->ci[p]] == c) return 1;
+  return 0;
+}
+
+static int colour_beaten(const or_csr *M, int i, const int *colour, const double *w) {
+  for (int p = M->rp[i]; p < M->rp[i + 1]; ++p) {
+    int j = M->ci[p];
+    if (j == i || colour[j] >= 0) continue;
+    if (w[j] > w[i] || (w[j] == w[i] && j > i)) return 1;
+  }
+  return 0;
+}
+
+int or_colour(const or_csr *A, uint64_t seed, int level, int *colour) {
+  int n = A->n;
+  or_csr *AT = or_transpose(A);
+  double *w = (double *)xmalloc((size_t)n * sizeof(double) + 8);
+  int *next = (int *)xmalloc((size_t)n * sizeof(int) + 8);
+  for (int i = 0; i < n; ++i) {
+    w[i] = or_uniform(seed, 2000ULL + (uint64_t)level, (uint64_t)i);
+    colour[i] = -1;
+  }
+  int left = n, ncol = 0;
+  while (left > 0) {
+    for (int i = 0; i < n; ++i) {
+      next[i] = colour[i];
+      if (colour[i] >= 0) continue;
+      if (colour_beaten(A, i, colour, w) || colour_beaten(AT, i, colour, w)) continue;
+      int c = 0;  /* the smallest colour that no coloured neighbour has */
+      while (colour_taken(A, AT, i, colour, c)) ++c;
+      next[i] = c;
+    }
+    left = 0;
+    for (int i = 0; i < n; ++i) {
+      colour[i] = next[i];
+      if (colour[i] < 0) ++left;
+      else if (colour[i] + 1 > ncol) ncol = colour[i] + 1;
+    }
+  }
+  or_csr_free(AT);
+  free(w);
+  free(next);
+  return ncol;
 }
 
 /* ------------------------------------------------------------------ */
@@ -668,6 +722,10 @@ struct or_amg {
   int coarse_lu;      /* 1: dense LU at the coarsest level, 0: two l1-Jacobi sweeps */
   double *lu;
   int *piv;
+  int smoother;       /* 0: l1-Jacobi; 1: Gauss-Seidel in C/F colour order */
+  int **key;          /* smoother 1: sweep index per point (levels with a C/F split) */
+  int *nkeys;
+  double **gdinv;     /* smoother 1: 1 / a_ii */
 };
 
 static double *l1_dinv(const or_csr *A) {
@@ -678,6 +736,34 @@ static double *l1_dinv(const or_csr *A) {
     d[i] = 1.0 / s;
   }
   return d;
+}
+
+/* Section 3.1's symmetric C/F relaxation order for level l: sweep keys
+   C(colour 0), C(colour 1), ..., F(colour 0), F(colour 1), ..., with empty
+   classes dropped; and the Gauss-Seidel diagonal 1 / a_ii */
+static void gs_order(or_amg *h, int l, const or_csr *A, const int8_t *CF, uint64_t seed) {
+  int n = A->n;
+  int *col = (int *)xmalloc((size_t)n * sizeof(int) + 8);
+  int ncol = or_colour(A, seed, l, col);
+  int nraw = 2 * ncol;
+  int *cnt = (int *)xcalloc((size_t)nraw + 1, sizeof(int));
+  for (int i = 0; i < n; ++i) cnt[(CF[i] == 1 ? 0 : ncol) + col[i]]++;
+  int *map = (int *)xmalloc((size_t)nraw * sizeof(int) + 8);
+  int nk = 0;
+  for (int k = 0; k < nraw; ++k) map[k] = cnt[k] > 0 ? nk++ : -1;
+  h->key[l] = (int *)xmalloc((size_t)n * sizeof(int) + 8);
+  for (int i = 0; i < n; ++i) h->key[l][i] = map[(CF[i] == 1 ? 0 : ncol) + col[i]];
+  h->nkeys[l] = nk;
+  h->gdinv[l] = (double *)xmalloc((size_t)n * sizeof(double) + 8);
+  for (int i = 0; i < n; ++i) {
+    double d = 1.0;
+    for (int p = A->rp[i]; p < A->rp[i + 1]; ++p)
+      if (A->ci[p] == i) d = A->v[p];
+    h->gdinv[l][i] = 1.0 / d;
+  }
+  free(col);
+  free(cnt);
+  free(map);
 }
 
 or_amg *or_amg_setup(const or_csr *A0, const or_opts *o) {
@@ -692,6 +778,10 @@ or_amg *or_amg_setup(const or_csr *A0, const or_opts *o) {
   h->w1 = (double **)xcalloc((size_t)cap, sizeof(double *));
   h->w2 = (double **)xcalloc((size_t)cap, sizeof(double *));
   h->w3 = (double **)xcalloc((size_t)cap, sizeof(double *));
+  h->key = (int **)xcalloc((size_t)cap, sizeof(int *));
+  h->nkeys = (int *)xcalloc((size_t)cap, sizeof(int));
+  h->gdinv = (double **)xcalloc((size_t)cap, sizeof(double *));
+  h->smoother = o->smoother;
   h->A[0] = csr_copy(A0);
   int l = 0;
   for (;;) {
@@ -711,6 +801,7 @@ or_amg *or_amg_setup(const or_csr *A0, const or_opts *o) {
       break;
     }
     h->CF[l] = CF;
+    if (o->smoother == 1) gs_order(h, l, A, CF, o->seed);
     h->P[l] = o->interp_type == 1 ? or_interp_exti(A, S, CF) : or_interp(A, S, CF);
     h->R[l] = or_transpose(h->P[l]);
     h->A[l + 1] = or_rap(A, h->P[l]);
@@ -736,6 +827,10 @@ const or_csr *or_amg_A(const or_amg *h, int l) { return h->A[l]; }
 const or_csr *or_amg_P(const or_amg *h, int l) { return l < h->L - 1 ? h->P[l] : NULL; }
 const int8_t *or_amg_CF(const or_amg *h, int l) { return l < h->L - 1 ? h->CF[l] : NULL; }
 int or_amg_coarse_is_lu(const or_amg *h) { return h->coarse_lu; }
+const int *or_amg_key(const or_amg *h, int l, int *nkeys) {
+  if (nkeys) *nkeys = (l < h->L - 1 && h->key[l]) ? h->nkeys[l] : 0;
+  return l < h->L - 1 ? h->key[l] : NULL;
+}
 
 void or_amg_free(or_amg *h) {
   if (!h) return;
@@ -749,7 +844,12 @@ void or_amg_free(or_amg *h) {
     free(h->w1[l]);
     free(h->w2[l]);
     free(h->w3[l]);
+    free(h->key[l]);
+    free(h->gdinv[l]);
   }
+  free(h->key);
+  free(h->nkeys);
+  free(h->gdinv);
   free(h->A);
   free(h->P);
   free(h->R);
@@ -762,6 +862,18 @@ void or_amg_free(or_amg *h) {
   free(h->lu);
   free(h->piv);
   free(h);
+}
+
+/* one Gauss-Seidel sweep over the points with sweep index k: no two of them
+   are coupled (a colour class of the symmetrised graph), so each is updated
+   from the current values of all other points: x_i += (b_i - sum_j a_ij x_j) / a_ii */
+static void gs_sweep(const or_csr *A, const int *key, int k, const double *gdinv, const double *b, double *x) {
+  for (int i = 0; i < A->n; ++i) {
+    if (key[i] != k) continue;
+    double s = 0.0;
+    for (int p = A->rp[i]; p < A->rp[i + 1]; ++p) s += A->v[p] * x[A->ci[p]];
+    x[i] = x[i] + (b[i] - s) * gdinv[i];
+  }
 }
 
 /* one V(1,1) cycle with zero initial guess on level l.
@@ -789,6 +901,22 @@ static void vcycle_level(const or_amg *h, int l, int trans, const double *b, dou
   double *bc = h->w2[l + 1];
   double *xc = h->w1[l + 1];
   const or_csr *P = h->P[l], *R = h->R[l];
+  if (h->smoother == 1) {
+    /* down: Gauss-Seidel sweeps in key order (C points, then F points) from zero */
+    for (int i = 0; i < n; ++i) x[i] = 0.0;
+    for (int k = 0; k < h->nkeys[l]; ++k) gs_sweep(A, h->key[l], k, h->gdinv[l], b, x);
+    residual(A, b, x, r);
+    or_spmv(R, r, bc);
+    vcycle_level(h, l + 1, trans, bc, xc);
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int p = P->rp[i]; p < P->rp[i + 1]; ++p) s += P->v[p] * xc[P->ci[p]];
+      x[i] = x[i] + s;
+    }
+    /* up: the opposite traversal (F points, then C points) */
+    for (int k = h->nkeys[l] - 1; k >= 0; --k) gs_sweep(A, h->key[l], k, h->gdinv[l], b, x);
+    return;
+  }
   for (int i = 0; i < n; ++i) x[i] = d[i] * b[i];     /* pre-smoothing from zero */
   residual(A, b, x, r);                               /* r = b - A x */
   or_spmv(R, r, bc);                                  /* restriction */

@@ -40,6 +40,8 @@ typedef struct or_opts {
   int inner_mode;         /* 1: option #3 (V-cycles to inner_tol) for the inverses Section 4 names:
                              C_E, C_g (Schur1), S_g, S_I (Schur2), the block relaxations of PCTL */
   int interp_type;        /* 0: classical modified (Section 3.1); 1: extended+i (distance two) */
+  int smoother;           /* 0: l1-Jacobi; 1: Gauss-Seidel in C/F order (Section 3.1's hybrid GS), read
+                             as multicolour GS: C colours then F colours on the way down, the reverse up */
 } or_opts;
 
 /* preconditioner kinds */
@@ -69,6 +71,12 @@ or_csr *or_spgemm(const or_csr *X, const or_csr *Y);
 /* AMG setup building blocks (Section 3.1) */
 void or_strength(const or_csr *A, double theta, uint8_t *S);
 int or_pmis(const or_csr *A, const uint8_t *S, uint64_t seed, int level, int8_t *CF);
+/* Colouring of the symmetrised graph of A (i ~ j when a_ij or a_ji is stored)
+   by Jones-Plassmann rounds with weights u_i = or_uniform(seed, 2000 + level, i): each round every
+   uncoloured point whose weight beats all uncoloured neighbours (ties: larger
+   index) takes the smallest colour no coloured neighbour has.  Returns the
+   number of colours. */
+int or_colour(const or_csr *A, uint64_t seed, int level, int *colour);
 /* same rounds with caller-given weights (ties broken by the larger index) */
 int or_pmis_weights(const or_csr *A, const uint8_t *S, const double *w, int8_t *CF);
 or_csr *or_interp(const or_csr *A, const uint8_t *S, const int8_t *CF);
@@ -83,6 +91,10 @@ int or_amg_nlevels(const or_amg *h);
 const or_csr *or_amg_A(const or_amg *h, int l);
 const or_csr *or_amg_P(const or_amg *h, int l);
 const int8_t *or_amg_CF(const or_amg *h, int l);
+/* Gauss-Seidel sweep index of each point of level l (smoother 1; NULL otherwise
+   and on the coarsest level): C points by colour, then F points by colour,
+   empty classes skipped; *nkeys = number of sweeps */
+const int *or_amg_key(const or_amg *h, int l, int *nkeys);
 int or_amg_coarse_is_lu(const or_amg *h);
 void or_vcycle(const or_amg *h, const double *b, double *x);
 void or_vcycle_T(const or_amg *h, const double *b, double *x);

@@ -39,7 +39,8 @@ class Opts(C.Structure):
                 ("inner_tol", C.c_double), ("inner_maxit", C.c_int),
                 ("nvcyc_group", C.c_int), ("nvcyc_E", C.c_int), ("nvcyc_I", C.c_int),
                 ("nvcyc_other", C.c_int), ("jacobi_sweeps", C.c_int), ("adaptive", C.c_int),
-                ("seed", C.c_uint64), ("inner_mode", C.c_int), ("interp_type", C.c_int)]
+                ("seed", C.c_uint64), ("inner_mode", C.c_int), ("interp_type", C.c_int),
+                ("smoother", C.c_int)]
 
 
 INV_CB = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
@@ -72,6 +73,8 @@ def lib():
             "or_strength": (None, [P, C.c_double, u8]),
             "or_pmis": (C.c_int, [P, u8, C.c_uint64, C.c_int, i8]),
             "or_pmis_weights": (C.c_int, [P, u8, dp, i8]),
+            "or_colour": (C.c_int, [P, C.c_uint64, C.c_int, ip]),
+            "or_amg_key": (C.POINTER(C.c_int), [P, C.c_int, C.POINTER(C.c_int)]),
             "or_interp": (P, [P, u8, i8]),
             "or_interp_exti": (P, [P, u8, i8]),
             "or_rap": (P, [P, P]),
@@ -186,6 +189,14 @@ def pmis(A: Csr, S, seed=0, level=0):
     return nc, CF[:n]
 
 
+def colour(A: Csr, seed=0, level=0):
+    """Jones-Plassmann colouring of the symmetrised graph of A: (ncolours, colour[n])."""
+    n = A.info()[0]
+    col = np.zeros(max(n, 1), np.int32)
+    nc = lib().or_colour(A.h, seed, level, col)
+    return nc, col[:n]
+
+
 def pmis_weights(A: Csr, S, w):
     n, _, z = A.info()
     CF = np.zeros(max(n, 1), np.int8)
@@ -265,6 +276,15 @@ class Amg:
     @property
     def coarse_is_lu(self):
         return bool(lib().or_amg_coarse_is_lu(self.h))
+
+    def key(self, l):
+        """Gauss-Seidel sweep index per point of level l (smoother 1), and the number of sweeps."""
+        nk = C.c_int()
+        p = lib().or_amg_key(self.h, l, C.byref(nk))
+        if not p:
+            return None, 0
+        n = self.A(l).info()[0]
+        return np.ctypeslib.as_array(p, shape=(n,)).copy(), nk.value
 
     def vcycle(self, b, transpose=False):
         b = np.ascontiguousarray(b, np.float64)

@@ -5,6 +5,7 @@ import os
 
 import numpy as np
 import pytest
+import scipy.linalg as sla
 import scipy.sparse as sp
 
 from paper_2002_04958_gb300 import inputs as I
@@ -396,3 +397,108 @@ def test_exti_reproduces_constants_and_galerkin(orc):
     Pd = P.toarray()
     Ac = orc.rap(Ao, Pe).scipy().toarray()
     assert np.allclose(Ac, Pd.T @ A.toarray() @ Pd, rtol=0, atol=1e-12 * abs(Ac).max())
+
+
+# ---------------------------------------------------------------- Gauss-Seidel order (smoother 1)
+def _greedy_by_weight(adj, w):
+    """Sequential greedy colouring, points taken by decreasing weight (ties: larger
+    index first): the colouring Jones-Plassmann rounds produce on a symmetric graph."""
+    n = len(adj)
+    order = sorted(range(n), key=lambda i: (w[i], i), reverse=True)
+    col = [-1] * n
+    for i in order:
+        used = {col[j] for j in adj[i] if col[j] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        col[i] = c
+    return col
+
+
+@pytest.mark.parametrize("n,density,sym,seed", [(60, 0.05, True, 1), (150, 0.03, True, 2), (120, 0.04, False, 3),
+                                                (40, 0.5, True, 4)])
+def test_colouring_is_greedy_by_weight_and_proper(orc, n, density, sym, seed):
+    rng = np.random.default_rng(seed)
+    M = sp.random(n, n, density=density, random_state=rng, format="csr")
+    if sym:
+        M = M + M.T
+    M = (M + sp.eye(n)).tocsr()
+    M.sort_indices()
+    level = seed % 3
+    nc, col = orc.colour(orc.Csr.from_scipy(M), seed=7, level=level)
+    Ms = ((M + M.T) != 0).tolil()
+    adj = [[j for j in Ms.rows[i] if j != i] for i in range(n)]
+    w = I.uniform(7, 2000 + level, n)
+    assert list(col) == _greedy_by_weight(adj, w)
+    assert nc == col.max() + 1
+    for i in range(n):
+        assert all(col[i] != col[j] for j in adj[i])
+
+
+def _dense_m_matrix(n, seed):
+    rng = np.random.default_rng(seed)
+    B = -rng.uniform(0.5, 1.0, (n, n))
+    A = (B + B.T) / 2
+    np.fill_diagonal(A, 0.0)
+    np.fill_diagonal(A, -A.sum(1) + 1.0)
+    return A
+
+
+def test_gs_vcycle_is_triangular_solves_on_a_complete_graph(orc):
+    # every point its own colour: the C/F-ordered multicolour sweeps become
+    # plain forward (down) and backward (up) Gauss-Seidel in the sweep order
+    n = 130
+    A = _dense_m_matrix(n, 5)
+    As = sp.csr_matrix(A)
+    As.sort_indices()
+    h = orc.Amg(orc.Csr.from_scipy(As), orc.opts(smoother=1, max_levels=2))
+    assert h.nlevels == 2 and h.coarse_is_lu
+    key, nk = h.key(0)
+    CF = h.CF(0)
+    assert nk == n and sorted(key) == list(range(n))
+    assert key[CF == 1].max() < key[CF == -1].min()        # C points are swept first
+    perm = np.argsort(key)
+    Ap = A[np.ix_(perm, perm)]
+    b = np.random.default_rng(6).standard_normal(n)
+    x = np.zeros(n)
+    x[perm] = sla.solve_triangular(np.tril(Ap), b[perm], lower=True)
+    r = b - A @ x
+    P = h.P(0).scipy().toarray()
+    Ac = h.A(1).scipy().toarray()
+    x = x + P @ np.linalg.solve(Ac, P.T @ r)
+    rp = (b - A @ x)[perm]
+    x[perm] = x[perm] + sla.solve_triangular(np.triu(Ap), rp, lower=False)
+    assert np.allclose(h.vcycle(b), x, rtol=1e-12, atol=1e-12 * abs(x).max())
+
+
+def test_gs_vcycle_symmetric_and_adjoint(orc):
+    # mirrored sweep orders make the cycle symmetric on a symmetric operator;
+    # the transposed cycle is the adjoint on a nonsymmetric one
+    rng = np.random.default_rng(9)
+    T = sp.diags([-np.ones(29), 2 * np.ones(30), -np.ones(29)], [-1, 0, 1])
+    A = (sp.kron(T, sp.eye(30)) + sp.kron(sp.eye(30), T)).tocsr()
+    A.sort_indices()
+    h = orc.Amg(orc.Csr.from_scipy(A), orc.opts(smoother=1, max_coarse=20))
+    assert h.nlevels >= 3
+    u, v = rng.standard_normal(900), rng.standard_normal(900)
+    assert abs(h.vcycle(u) @ v - u @ h.vcycle(v)) <= 1e-13 * np.linalg.norm(u) * np.linalg.norm(v) * 10
+    s = I.make_system(2, (12, 10), multigroup=True)
+    hm = orc.Amg(orc.csr_of_system(s), orc.opts(smoother=1, max_coarse=20))
+    u, v = rng.standard_normal(s.n), rng.standard_normal(s.n)
+    lhs, rhs = hm.vcycle(u) @ v, u @ hm.vcycle(v, transpose=True)
+    assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(u) * np.linalg.norm(v) * 10
+    assert abs(hm.vcycle(u) @ v - u @ hm.vcycle(v)) > 1e-8 * np.linalg.norm(u) * np.linalg.norm(v)
+
+
+def test_gs_keys_on_a_hierarchy(orc):
+    s = I.make_system(1, (24, 20), inclusion=True)
+    h = orc.Amg(orc.csr_of_system(s), orc.opts(smoother=1))
+    for l in range(h.nlevels - 1):
+        key, nk = h.key(l)
+        CF = h.CF(l)
+        assert set(key) == set(range(nk))                   # no empty sweep
+        assert key[CF == 1].max() < key[CF == -1].min()
+        A = h.A(l).scipy().tocoo()
+        off = A.row != A.col
+        assert np.all(key[A.row[off]] != key[A.col[off]])    # a sweep's points are uncoupled
+    assert h.key(h.nlevels - 1)[0] is None

@@ -71,6 +71,23 @@ def test_two_grid_factor_poisson(orc):
     hm = orc.Amg(Ao, orc.opts())
     rhom = _conv_factor(hm, A)
     assert rho2 <= rhom + 1e-12 < 0.9
+    # Gauss-Seidel in C/F order (Section 3.1's smoother): measured 0.500 two-grid, 0.575 V-cycle
+    g2 = _conv_factor(orc.Amg(Ao, orc.opts(smoother=1, max_levels=2, max_coarse=1000)), A)
+    gm = _conv_factor(orc.Amg(Ao, orc.opts(smoother=1)), A)
+    assert g2 < 0.55 and g2 < rho2 - 0.05 and gm < rhom - 0.05, (g2, gm)
+
+
+def test_gs_smoother_rescues_monolithic_amg(orc):
+    # the coupled one-group system: l1-Jacobi V-cycles barely precondition it,
+    # C/F Gauss-Seidel ones do (measured 199 vs 29 FGMRES iterations)
+    s = I.make_system(1, (64, 64), inclusion=True)
+    Ao = orc.csr_of_system(s)
+    its = []
+    for sm in (0, 1):
+        _, it, _, st, _ = orc.fgmres(Ao, s.b, orc.Block(Ao, s.G, s.N, "amg", orc.opts(smoother=sm)), tol=1e-8)
+        assert st == 0
+        its.append(it)
+    assert its[1] * 3 < its[0], its
 
 
 def test_hierarchy_galerkin_and_sizes(orc):
