@@ -124,7 +124,8 @@ def run_ours(args):
     ncyc = [int(t) for t in args.nvcyc.split(",")]
     opts = dict(precision=args.precision, batched=args.batched, use_graph=args.graph, autotune=1,
                 keep_transpose=int(args.adjoint), max_it=args.max_it, interp_type=args.interp, pdl=args.pdl,
-                inner_mode=args.inner, nvcyc_group=ncyc[0], nvcyc_E=ncyc[1], nvcyc_I=ncyc[2])
+                inner_mode=args.inner, nvcyc_group=ncyc[0], nvcyc_E=ncyc[1], nvcyc_I=ncyc[2],
+                smoother=args.smoother)
     slv = mgdamg.Solver(**opts)
     adj = {}
 
@@ -218,7 +219,11 @@ def run_ours(args):
                               (f"{args.kind}_fp64_option3_inner_1e-2", args.kind,
                                dict(inner_mode=1, batched=1, use_graph=1, interp_type=args.interp)),
                               (f"{args.kind}_fp64_vcycles_3_1_1", args.kind,
-                               dict(nvcyc_group=3, batched=1, use_graph=1, interp_type=args.interp))]:
+                               dict(nvcyc_group=3, batched=1, use_graph=1, interp_type=args.interp)),
+                              (f"{args.kind}_fp64_cf_gauss_seidel", args.kind,
+                               dict(smoother=1, batched=1, use_graph=1, interp_type=args.interp)),
+                              ("monolithic_amg_fp64_cf_gauss_seidel", "amg",
+                               dict(smoother=1, batched=1, use_graph=1, interp_type=args.interp))]:
             try:
                 v = mgdamg.Solver(autotune=1, **o)
                 v.setup(sysm.G, sysm.N, rp, ci, va, kind)
@@ -261,6 +266,7 @@ def run_ours(args):
                    "interpolation": "extended+i" if args.interp else "classical modified",
                    "inverses": ("option #3: V-cycles to 1e-2 for the Schur-type inverses" if args.inner else
                                 "option #2: V-cycles per group/E/I inverse " + args.nvcyc.replace(",", "/")),
+                   "smoother": "Gauss-Seidel in C/F order (multicolour)" if args.smoother else "l1-Jacobi",
                    "step": "device setup + solve", "parallelism": f"replicas{ws}",
                    "launch": ("batched per-level launches" if args.batched else "per-operator launches") +
                              (", preconditioner replayed from a CUDA graph" if args.graph else ""),
@@ -305,7 +311,8 @@ def _l2_note(sysm):
 def _oracle_opts(args):
     """The oracle's options for the preconditioner the GPU arm runs."""
     g, e, i = (int(t) for t in args.nvcyc.split(","))
-    return dict(interp_type=args.interp, inner_mode=args.inner, nvcyc_group=g, nvcyc_E=e, nvcyc_I=i)
+    return dict(interp_type=args.interp, inner_mode=args.inner, nvcyc_group=g, nvcyc_E=e, nvcyc_I=i,
+                smoother=args.smoother)
 
 
 def _traffic_from_profiles():
@@ -422,6 +429,7 @@ def main():
     ap.add_argument("--max-it", type=int, default=1000)
     ap.add_argument("--pdl", type=int, default=1, help="programmatic dependent launch of solve kernels")
     ap.add_argument("--inner", type=int, default=0, help="1: option #3 inverses (V-cycles to 1e-2)")
+    ap.add_argument("--smoother", type=int, default=0, help="0 l1-Jacobi, 1 Gauss-Seidel in C/F order")
     ap.add_argument("--nvcyc", default="1,1,1", help="V-cycles per group, E and I inverse")
     ap.add_argument("--interp", type=int, default=None,
                     help="0 classical modified, 1 extended+i (default: 1 for the default workload, else 0)")

@@ -91,6 +91,12 @@ typedef struct mgd_opts {
                              x += V(rhs - A x) until ||rhs - A x|| <= inner_tol ||rhs|| or inner_maxit cycles.
                              The loop runs on the device (a conditional CUDA graph node when use_graph); the
                              transposed apply keeps the fixed cycle counts.  0: option #2 (default) */
+  int smoother;           /* 0: l1-Jacobi pre- and post-smoothing (default); 1: Section 3.1's Gauss-Seidel in
+                             C/F order as multicolour Gauss-Seidel: the points of each level are coloured by
+                             Jones-Plassmann rounds on the symmetrised graph of A_l (weights from the seeded
+                             counter generator, stream 2000 + level); pre-smoothing sweeps the C colours then
+                             the F colours, post-smoothing the same classes in the opposite order; each sweep
+                             updates x_i += (b_i - (A x)_i) / a_ii for its (mutually uncoupled) points */
 } mgd_opts;
 
 /* Fill *o with the defaults listed above.  Returns MGD_EINVAL if o is NULL. */
@@ -170,6 +176,10 @@ int mgd_level_info(mgd_ctx *c, int op, int level, int *n, int *nnz, int *nnzP, i
  * option #1 Jacobi inverse).  Synchronises the context's stream (the option #3 counts
  * live on the device).  MGD_EINVAL for a bad op or NULL cycles. */
 int mgd_op_cycles(mgd_ctx *c, int op, long long *cycles);
+/* Gauss-Seidel order of level `level` of operator `op` (smoother 1): *nkeys =
+ * number of sweeps; h_key[n] (host, may be NULL) = sweep index of each point.
+ * *nkeys = 0 on the coarsest level or with the l1-Jacobi smoother. */
+int mgd_level_keys(mgd_ctx *c, int op, int level, int *nkeys, int *h_key);
 /* Copy level `level` of operator `op` to host buffers (any may be NULL):
  * A_l as h_rp[n+1], h_ci[nnz], h_v[nnz]; C/F splitting h_cf[n] (1 = C,
  * -1 = F; absent on the coarsest level); P_l as h_prp[n+1], h_pci[nnzP],

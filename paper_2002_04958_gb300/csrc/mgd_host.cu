@@ -168,6 +168,14 @@ struct Level {
   signed char* CF = nullptr;
   int nc = 0;
   void *b = nullptr, *x = nullptr, *xt = nullptr, *r = nullptr;
+  // Gauss-Seidel order (smoother 1, levels with a C/F split)
+  int nk = 0;
+  int* key = nullptr;
+  int* perm = nullptr;
+  int* koff = nullptr;
+  std::vector<int> koff_h;
+  double* gdinv = nullptr;
+  float* gdinv32 = nullptr;
 };
 
 struct Hier {
@@ -184,7 +192,7 @@ struct Hier {
 // threads add concurrently, so the hierarchy phases can sum past wall time)
 enum SetupPhase {
   SP_STRENGTH = 0, SP_PMIS, SP_INTERP, SP_TRANSPOSE, SP_AP, SP_RAP, SP_FINALIZE, SP_COARSE,
-  SP_VALIDATE, SP_BLOCKS, SP_HIERARCHIES, SP_PCTL, SP_PROGRAM, SP_KRYLOV, SP_COUNT = 16
+  SP_VALIDATE, SP_BLOCKS, SP_HIERARCHIES, SP_PCTL, SP_PROGRAM, SP_KRYLOV, SP_COLOUR, SP_COUNT = 16
 };
 struct PhaseClock {
   std::mutex mu;
@@ -313,6 +321,68 @@ static float* cast32(Arena& a, const double* x, int n, cudaStream_t s) {
   return y;
 }
 
+// Gauss-Seidel order of a level (Section 3.1's C/F relaxation): colouring of
+// the symmetrised graph, then sweep classes C(colour 0..), F(colour 0..) with
+// the empty ones dropped, each class's rows listed in increasing order.
+static void gs_order(Arena& ar, Level& lv, int level, unsigned long long seed, cudaStream_t s) {
+  const int n = lv.A.n;
+  Scratch tmp(s);
+  // pattern of A^T, scratch only (rows unsorted: the colouring does not need order)
+  const int nnz = lv.A.nnz;
+  int* tcnt = tmp.alloc<int>(n);
+  MGD_CUDA(cudaMemsetAsync(tcnt, 0, sizeof(int) * std::max(n, 1), s));
+  launch_transpose_count(nnz, lv.A.ci, tcnt, s);
+  int* trp = tmp.alloc<int>(n + 1);
+  exclusive_scan(tcnt, trp, n, s);
+  int* tci = tmp.alloc<int>(nnz);
+  double* tv = tmp.alloc<double>(nnz);
+  int* tcur = tmp.alloc<int>(n);
+  MGD_CUDA(cudaMemsetAsync(tcur, 0, sizeof(int) * std::max(n, 1), s));
+  launch_transpose_fill(n, lv.A.rp, lv.A.ci, lv.A.v, trp, tcur, tci, tv, s);
+  Csr AT;
+  AT.rp = trp;
+  AT.ci = tci;
+  double* w = tmp.alloc<double>(n);
+  int* col = tmp.alloc<int>(n);
+  int* nxt = tmp.alloc<int>(n);
+  int* left = tmp.alloc<int>(1);
+  launch_colour_init(n, seed, level, w, col, s);
+  // rounds are idempotent once every point is coloured: check every second round
+  for (int round = 0; round < n + 1; round += 2) {
+    MGD_CUDA(cudaMemsetAsync(left, 0, sizeof(int), s));
+    launch_colour_round(n, lv.A.rp, lv.A.ci, AT.rp, AT.ci, w, col, nxt, left, s);
+    MGD_CUDA(cudaMemsetAsync(left, 0, sizeof(int), s));
+    launch_colour_round(n, lv.A.rp, lv.A.ci, AT.rp, AT.ci, w, nxt, col, left, s);
+    if (read_int(left, s) == 0) break;
+  }
+  int* mx = tmp.alloc<int>(1);
+  MGD_CUDA(cudaMemsetAsync(mx, 0, sizeof(int), s));
+  launch_colour_max(n, col, mx, s);
+  const int ncol = read_int(mx, s) + 1;
+  int* cnt = tmp.alloc<int>(2 * ncol);
+  MGD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * ncol, s));
+  launch_key_count(n, col, lv.CF, ncol, cnt, s);
+  std::vector<int> hc(2 * ncol), map(2 * ncol, -1);
+  MGD_CUDA(cudaMemcpyAsync(hc.data(), cnt, sizeof(int) * 2 * ncol, cudaMemcpyDeviceToHost, s));
+  MGD_CUDA(cudaStreamSynchronize(s));
+  lv.koff_h.assign(1, 0);
+  for (int k = 0; k < 2 * ncol; ++k)
+    if (hc[k] > 0) {
+      map[k] = (int)lv.koff_h.size() - 1;
+      lv.koff_h.push_back(lv.koff_h.back() + hc[k]);
+    }
+  lv.nk = (int)lv.koff_h.size() - 1;
+  int* dmap = tmp.alloc<int>(2 * ncol);
+  MGD_CUDA(cudaMemcpyAsync(dmap, map.data(), sizeof(int) * 2 * ncol, cudaMemcpyHostToDevice, s));
+  lv.koff = ar.alloc<int>(lv.nk + 1);
+  MGD_CUDA(cudaMemcpyAsync(lv.koff, lv.koff_h.data(), sizeof(int) * (lv.nk + 1), cudaMemcpyHostToDevice, s));
+  lv.key = ar.alloc<int>(n);
+  launch_key_assign(n, col, lv.CF, ncol, dmap, lv.key, s);
+  lv.perm = ar.alloc<int>(n);
+  launch_key_perm(n, lv.nk, lv.key, lv.koff, lv.perm, s);
+  MGD_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope
+}
+
 // Section 3.1 setup: strength -> PMIS -> interpolation -> R = P^T -> A_c = R (A P),
 // level by level until the coarsest criterion; then smoother diagonals,
 // kernel layouts, FP32 copies and the coarsest dense inverse.
@@ -366,6 +436,10 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
     if (nc == 0 || nc == n) break;  // coarsening stalled: this level is the coarsest
     lv.CF = CF;
     lv.nc = nc;
+    if (o.smoother == 1) {
+      PhaseTimer pt_col(sc.clk, SP_COLOUR);
+      gs_order(ar, lv, l, o.seed, s);
+    }
     Csr P;
     P.n = n;
     P.m = nc;
@@ -415,14 +489,24 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
     int n = lv.A.n;
     lv.dinv = ar.alloc<double>(n);
     launch_l1_dinv(n, lv.A.rp, lv.A.v, lv.dinv, s);
+    if (lv.nk > 0) {
+      lv.gdinv = ar.alloc<double>(n);
+      launch_diag_inv(n, lv.A.rp, lv.A.ci, lv.A.v, lv.gdinv, s);
+      if (sc.mixed) lv.gdinv32 = cast32(ar, lv.gdinv, n, s);
+    }
     lv.sell = build_sell(ar, lv.A, sc.mixed, s);
-    lv.vpre = ar.alloc<double>(lv.A.nnz);
-    launch_colscale(lv.A.nnz, lv.A.ci, lv.A.v, lv.dinv, lv.vpre, s);
-    lv.sell.vpre = ar.alloc<double>(lv.sell.nstored);
-    launch_colscale(lv.sell.nstored, lv.sell.ci, lv.sell.v, lv.dinv, lv.sell.vpre, s);
+    const bool jac = lv.nk == 0;  // A D^-1 feeds only the l1-Jacobi pre-smoothing
+    if (jac) {
+      lv.vpre = ar.alloc<double>(lv.A.nnz);
+      launch_colscale(lv.A.nnz, lv.A.ci, lv.A.v, lv.dinv, lv.vpre, s);
+      lv.sell.vpre = ar.alloc<double>(lv.sell.nstored);
+      launch_colscale(lv.sell.nstored, lv.sell.ci, lv.sell.v, lv.dinv, lv.sell.vpre, s);
+    }
     if (sc.mixed) {
-      lv.vpre32 = cast32(ar, lv.vpre, lv.A.nnz, s);
-      lv.sell.vpre32 = cast32(ar, lv.sell.vpre, (int)lv.sell.nstored, s);
+      if (jac) {
+        lv.vpre32 = cast32(ar, lv.vpre, lv.A.nnz, s);
+        lv.sell.vpre32 = cast32(ar, lv.sell.vpre, (int)lv.sell.nstored, s);
+      }
       lv.v32 = cast32(ar, lv.A.v, lv.A.nnz, s);
       lv.dinv32 = cast32(ar, lv.dinv, n, s);
       if (l < h.nlev() - 1) {
@@ -433,20 +517,25 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
     if (sc.keepT) {
       lv.AT = transpose(ar, lv.A, s);
       lv.sellT = build_sell(ar, lv.AT, sc.mixed, s);
-      lv.atvpre = ar.alloc<double>(lv.AT.nnz);
-      launch_colscale(lv.AT.nnz, lv.AT.ci, lv.AT.v, lv.dinv, lv.atvpre, s);
-      lv.sellT.vpre = ar.alloc<double>(lv.sellT.nstored);
-      launch_colscale(lv.sellT.nstored, lv.sellT.ci, lv.sellT.v, lv.dinv, lv.sellT.vpre, s);
+      if (jac) {
+        lv.atvpre = ar.alloc<double>(lv.AT.nnz);
+        launch_colscale(lv.AT.nnz, lv.AT.ci, lv.AT.v, lv.dinv, lv.atvpre, s);
+        lv.sellT.vpre = ar.alloc<double>(lv.sellT.nstored);
+        launch_colscale(lv.sellT.nstored, lv.sellT.ci, lv.sellT.v, lv.dinv, lv.sellT.vpre, s);
+      }
       if (sc.mixed) {
         lv.atv32 = cast32(ar, lv.AT.v, lv.AT.nnz, s);
-        lv.atvpre32 = cast32(ar, lv.atvpre, lv.AT.nnz, s);
-        lv.sellT.vpre32 = cast32(ar, lv.sellT.vpre, (int)lv.sellT.nstored, s);
+        if (jac) {
+          lv.atvpre32 = cast32(ar, lv.atvpre, lv.AT.nnz, s);
+          lv.sellT.vpre32 = cast32(ar, lv.sellT.vpre, (int)lv.sellT.nstored, s);
+        }
       }
     }
     size_t es = sc.mixed ? sizeof(float) : sizeof(double);
     lv.b = ar.alloc<char>(es * n);
-    lv.x = ar.alloc<char>(es * n);
     lv.xt = ar.alloc<char>(es * n);
+    // Gauss-Seidel levels smooth in place: the level's output is xt itself
+    lv.x = lv.nk > 0 ? lv.xt : ar.alloc<char>(es * n);
     lv.r = ar.alloc<char>(es * n);
     MGD_CUDA(cudaMemsetAsync(lv.b, 0, es * n, s));
     MGD_CUDA(cudaMemsetAsync(lv.x, 0, es * n, s));
@@ -489,6 +578,10 @@ struct VBatch {
     int fmtA = FMT_SELL, fmtR = FMT_CSR4, fmtP = FMT_CSR1;
     double bytes_pre = 0, bytes_post = 0, bytes_restrict = 0, bytes_prolong = 0, bytes_coarse = 0, bytes_jac = 0;
     double bytes_post_cj = 0;  // post-smoothing of the stalled coarsest levels
+    // Gauss-Seidel levels: sweep steps and, per step, the largest class over the subsystems
+    bool gs = false;
+    int nkmax = 0, tprGS = 4;
+    std::vector<int> seg_pre, seg_post;
   };
   std::vector<LP> plan, planT;
   double bytes_total = 0;
@@ -548,6 +641,11 @@ static LDesc<T> make_desc(Hier& h, int l, bool trans) {
   d.cinv = trans ? h.cinvT : h.cinv;
   d.cn = h.cn;
   d.active = trans ? nullptr : h.active;
+  d.nk = lv.nk;
+  d.key = lv.key;
+  d.perm = lv.perm;
+  d.koff = lv.koff;
+  d.gdinv = pick<T>(lv.gdinv, lv.gdinv32);
   return d;
 }
 
@@ -573,8 +671,27 @@ static void build_plan(Arena& ar, VBatch<T>& vb, bool trans, cudaStream_t s) {
         down.push_back(d);
         lp.maxn = std::max<int>(lp.maxn, (int)n);
         lp.maxnc = std::max(lp.maxnc, lv.nc);
-        lp.bytes_pre += sp_bytes(nnz, n, sv) + 4.0 * sv * n;
-        lp.bytes_post += sp_bytes(nnz, n, sv) + 4.0 * sv * n;
+        if (lv.nk > 0) {
+          // first sweep (key, b, 1/a_ii in; xt out), the other sweeps (rows once, perm,
+          // b, 1/a_ii, xt read and written), the residual; up: every sweep
+          lp.gs = true;
+          lp.nkmax = std::max(lp.nkmax, lv.nk);
+          if ((int)lp.seg_pre.size() < lv.nk) {
+            lp.seg_pre.resize(lv.nk, 0);
+            lp.seg_post.resize(lv.nk, 0);
+          }
+          for (int k = 0; k < lv.nk; ++k) {
+            int c = lv.koff_h[k + 1] - lv.koff_h[k];
+            lp.seg_pre[k] = std::max(lp.seg_pre[k], c);
+            lp.seg_post[lv.nk - 1 - k] = std::max(lp.seg_post[lv.nk - 1 - k], c);
+          }
+          lp.bytes_pre += (4.0 + 3.0 * sv) * n + sp_bytes(nnz, n, sv) + (4.0 + 4.0 * sv) * n +
+                          sp_bytes(nnz, n, sv) + 3.0 * sv * n;
+          lp.bytes_post += sp_bytes(nnz, n, sv) + (4.0 + 4.0 * sv) * n;
+        } else {
+          lp.bytes_pre += sp_bytes(nnz, n, sv) + 4.0 * sv * n;
+          lp.bytes_post += sp_bytes(nnz, n, sv) + 4.0 * sv * n;
+        }
         lp.bytes_restrict += sp_bytes(lv.R.nnz, lv.nc, sv) + (double)sv * (n + lv.nc);
         lp.bytes_prolong += sp_bytes(lv.P.nnz, n, sv) + (double)sv * (lv.nc + 2 * n);
       } else if (h->coarse_lu) {
@@ -606,6 +723,19 @@ static void build_plan(Arena& ar, VBatch<T>& vb, bool trans, cudaStream_t s) {
   MGD_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope
 }
 
+// Gauss-Seidel smoothing of one level of a batch: down = first sweep from
+// zero, sweeps 1.., residual; up = the sweeps in the opposite order
+template <typename T>
+static void run_gs_down(const typename VBatch<T>::LP& lp, cudaStream_t s) {
+  launch_gs_first<T>(lp.d_down, lp.ndown, lp.maxn, s);
+  for (int t = 1; t < lp.nkmax; ++t) launch_gs_sweep<T>(lp.tprGS, lp.d_down, lp.ndown, lp.seg_pre[t], t, 0, s);
+  launch_gs_resid<T>(lp.fmtA, lp.d_down, lp.ndown, lp.maxn, s);
+}
+template <typename T>
+static void run_gs_up(const typename VBatch<T>::LP& lp, cudaStream_t s) {
+  for (int t = 0; t < lp.nkmax; ++t) launch_gs_sweep<T>(lp.tprGS, lp.d_down, lp.ndown, lp.seg_post[t], t, 1, s);
+}
+
 template <typename T>
 static void run_vbatch(VBatch<T>& vb, bool trans, cudaStream_t s, Profiler& prof) {
   auto& plan = trans ? vb.planT : vb.plan;
@@ -616,7 +746,8 @@ static void run_vbatch(VBatch<T>& vb, bool trans, cudaStream_t s, Profiler& prof
     if (lp.ndown) {
       prof.next_detail = 16 + 4 * l + 0;
       int id = prof.begin(s, l == 0 ? 0 : 1);
-      launch_phase<T>(PH_PRE, lp.fmtA, lp.fmtR, lp.d_down, lp.ndown, lp.maxn, s);
+      if (lp.gs) run_gs_down<T>(lp, s);
+      else launch_phase<T>(PH_PRE, lp.fmtA, lp.fmtR, lp.d_down, lp.ndown, lp.maxn, s);
       prof.end(id, l == 0 ? 0 : 1, lp.bytes_pre, s);
       prof.next_detail = 16 + 4 * l + 1;
       id = prof.begin(s, 1);
@@ -652,7 +783,8 @@ static void run_vbatch(VBatch<T>& vb, bool trans, cudaStream_t s, Profiler& prof
     prof.end(id, 1, lp.bytes_prolong, s);
     prof.next_detail = 16 + 4 * l + 3;
     id = prof.begin(s, l == 0 ? 0 : 1);
-    launch_phase<T>(PH_POST, lp.fmtA, lp.fmtP, lp.d_down, lp.ndown, lp.maxn, s);
+    if (lp.gs) run_gs_up<T>(lp, s);
+    else launch_phase<T>(PH_POST, lp.fmtA, lp.fmtP, lp.d_down, lp.ndown, lp.maxn, s);
     prof.end(id, l == 0 ? 0 : 1, lp.bytes_post, s);
   }
 }
@@ -760,10 +892,24 @@ static void autotune(VBatch<T>& vb, bool trans, cudaStream_t s) {
     if (!lp.ndown) continue;
     float best = 1e30f;
     for (int f : candA) {
-      float ms = time_it([&] { launch_phase<T>(PH_PRE, f, lp.fmtR, lp.d_down, lp.ndown, lp.maxn, s); });
+      float ms = time_it([&] {
+        if (lp.gs) launch_gs_resid<T>(f, lp.d_down, lp.ndown, lp.maxn, s);
+        else launch_phase<T>(PH_PRE, f, lp.fmtR, lp.d_down, lp.ndown, lp.maxn, s);
+      });
       if (ms < best) {
         best = ms;
         lp.fmtA = f;
+      }
+    }
+    if (lp.gs) {  // threads per row of the sweeps: time a whole down-smoothing
+      best = 1e30f;
+      for (int tpr : {1, 2, 4, 8}) {
+        lp.tprGS = tpr;
+        float ms = time_it([&] { run_gs_down<T>(lp, s); });
+        if (ms < best) {
+          best = ms;
+          lp.tprGS = tpr;
+        }
       }
     }
     best = 1e30f;
@@ -1491,7 +1637,7 @@ static void run_program(mgd_ctx* c, bool trans) {
 // level the subsystem count, largest row count and nonzeros): a setup of a
 // system with the same hierarchy shape reuses them instead of re-timing.
 struct TuneResult {
-  std::vector<int> fmtA, fmtR, fmtP;
+  std::vector<int> fmtA, fmtR, fmtP, tprGS;
   int tail_level;
 };
 static std::mutex g_tune_mu;
@@ -1504,6 +1650,7 @@ static std::vector<long long> tune_key(const VBatch<T>& vb, bool trans, int fuse
     long long nnz = 0;
     for (Hier* h : vb.hs)
       if (l < h->nlev()) nnz += h->L[l].A.nnz;
+    k.push_back(vb.plan[l].gs ? vb.plan[l].nkmax : -1);
     k.push_back(vb.plan[l].ndown);
     k.push_back(vb.plan[l].maxn);
     k.push_back(nnz);
@@ -1639,10 +1786,12 @@ static void build_batches(mgd_ctx* c) {
           vb.plan[l].fmtA = it->second.fmtA[l];
           vb.plan[l].fmtR = it->second.fmtR[l];
           vb.plan[l].fmtP = it->second.fmtP[l];
+          vb.plan[l].tprGS = it->second.tprGS[l];
           if (c->o.keep_transpose) {
             vb.planT[l].fmtA = it->second.fmtA[l];
             vb.planT[l].fmtR = it->second.fmtR[l];
             vb.planT[l].fmtP = it->second.fmtP[l];
+            vb.planT[l].tprGS = it->second.tprGS[l];
           }
         }
         cached = true;
@@ -1675,6 +1824,7 @@ static void build_batches(mgd_ctx* c) {
         r.fmtA.push_back(vb.plan[l].fmtA);
         r.fmtR.push_back(vb.plan[l].fmtR);
         r.fmtP.push_back(vb.plan[l].fmtP);
+        r.tprGS.push_back(vb.plan[l].tprGS);
       }
       r.tail_level = vb.tail_level;
       std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -2286,6 +2436,7 @@ int mgd_opts_default(mgd_opts* o) {
   o->interp_type = 0;
   o->pdl = 1;
   o->inner_mode = 0;
+  o->smoother = 0;
   return MGD_OK;
 }
 
@@ -2300,7 +2451,7 @@ int mgd_create(mgd_ctx** out, const mgd_opts* o, void* stream) {
   if (q.max_coarse < 1 || q.max_coarse > 4096 || q.max_levels < 1 || q.restart < 1 || q.restart > 30 ||
       q.precision < 0 || q.precision > 1 || q.inner_mode < 0 || q.inner_mode > 1 || q.inner_maxit < 1 ||
       q.inner_maxit > 100000 || !(q.inner_tol >= 0.0) || q.nvcyc_group > 1000 || q.nvcyc_E > 1000 ||
-      q.nvcyc_I > 1000 || q.nvcyc_other > 1000 || q.jacobi_sweeps > 1000) {
+      q.nvcyc_I > 1000 || q.nvcyc_other > 1000 || q.jacobi_sweeps > 1000 || q.smoother < 0 || q.smoother > 1) {
     delete c;
     return MGD_EINVAL;
   }
@@ -2483,6 +2634,21 @@ int mgd_op_cycles(mgd_ctx* c, int op, long long* cycles) {
       }
     }
     *cycles = n;
+    return MGD_OK;
+  });
+}
+
+int mgd_level_keys(mgd_ctx* c, int op, int level, int* nkeys, int* h_key) {
+  return guarded(c, [&]() -> int {
+    if (!c->ready || op < 0 || op >= (int)c->ops.size() || !nkeys) throw Error{MGD_EINVAL, "bad operator"};
+    InvOp& o = c->ops[op];
+    if (o.jacobi || level < 0 || level >= o.h.nlev()) throw Error{MGD_EINVAL, "bad level"};
+    Level& lv = o.h.L[level];
+    *nkeys = lv.nk;
+    if (h_key && lv.nk > 0) {
+      MGD_CUDA(cudaMemcpyAsync(h_key, lv.key, sizeof(int) * lv.A.n, cudaMemcpyDeviceToHost, c->s));
+      MGD_CUDA(cudaStreamSynchronize(c->s));
+    }
     return MGD_OK;
   });
 }

@@ -208,6 +208,13 @@ struct LDesc {
   // option #3 / multi-cycle loops: the subsystem's flag (nullptr: always
   // run); a V-cycle kernel skips a subsystem whose flag is 0
   const int* active;
+  // Gauss-Seidel smoother (nk > 0): sweep index per row, the rows of sweep k
+  // at perm[koff[k] .. koff[k+1]), and 1 / a_ii
+  const int* key;
+  const int* perm;
+  const int* koff;
+  int nk;
+  const T* gdinv;
 };
 
 // the V-cycle kernels' first statement after the dependency wait: leave a
@@ -320,6 +327,14 @@ void launch_pmis_init(int n, const int* rp, const uint8_t* S, const int* cnt, un
                       double* w, signed char* CF, cudaStream_t s);
 void launch_pmis_round(int n, const int* rp, const int* ci, const uint8_t* S, const int* strp, const int* stci,
                        const double* w, signed char* CF, uint8_t* newc, int* undecided, cudaStream_t s);
+void launch_colour_init(int n, unsigned long long seed, int level, double* w, int* col, cudaStream_t s);
+void launch_colour_round(int n, const int* rp, const int* ci, const int* trp, const int* tci, const double* w,
+                         const int* col, int* next, int* left, cudaStream_t s);
+void launch_colour_max(int n, const int* col, int* mx, cudaStream_t s);
+void launch_key_count(int n, const int* col, const signed char* CF, int ncol, int* cnt, cudaStream_t s);
+void launch_key_assign(int n, const int* col, const signed char* CF, int ncol, const int* map, int* key,
+                       cudaStream_t s);
+void launch_key_perm(int n, int nk, const int* key, const int* koff, int* perm, cudaStream_t s);
 void launch_interp_count(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF, int* cnt,
                          int* isc, cudaStream_t s);
 void launch_interp_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S,
@@ -364,6 +379,13 @@ enum Phase { PH_PRE = 0, PH_RESTRICT = 1, PH_PROLONG = 2, PH_POST = 3, PH_COARSE
 template <typename T>
 void launch_phase(int phase, int fmtA, int tprRP, const LDesc<T>* d_descs, int ndesc, int maxrows,
                   cudaStream_t s);
+// Gauss-Seidel smoothing phases (levels with nk > 0)
+template <typename T>
+void launch_gs_first(const LDesc<T>* d, int nd, int maxrows, cudaStream_t s);
+template <typename T>
+void launch_gs_sweep(int tpr, const LDesc<T>* d, int nd, int maxrows, int t, int up, cudaStream_t s);
+template <typename T>
+void launch_gs_resid(int fmtA, const LDesc<T>* d, int nd, int maxrows, cudaStream_t s);
 // fused coarse-level V-cycle: one thread-block cluster of `cs` CTAs per subsystem
 template <typename T>
 void launch_vtail(const TailSub<T>* d_subs, int nsub, int cs, cudaStream_t s);

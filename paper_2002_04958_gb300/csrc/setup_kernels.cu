@@ -320,6 +320,144 @@ void launch_pmis_init(int n, const int* rp, const uint8_t* S, const int* cnt, un
   MGD_LAUNCH_CHECK();
 }
 
+// ---------------------------------------------------------------- Gauss-Seidel order (Section 3.1 smoother)
+// Jones-Plassmann colouring of the symmetrised graph of A (neighbours from A's
+// and A^T's rows), weights u_i of the counter generator on stream 2000+level.
+// Each round reads the colours of the previous round (col) and writes all of
+// them to next, so points coloured in the same round never see each other.
+__global__ void k_colour_init(int n, unsigned long long seed, int level, double* w, int* col) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  w[i] = splitmix_uniform(seed, 2000ULL + (uint64_t)level, (uint64_t)i);
+  col[i] = -1;
+}
+
+__device__ __forceinline__ bool colour_beaten(const int* rp, const int* ci, int i, const int* col, const double* w) {
+  double wi = w[i];
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = ci[p];
+    if (j == i || col[j] >= 0) continue;
+    double wj = w[j];
+    if (wj > wi || (wj == wi && j > i)) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool colour_taken(const int* rp, const int* ci, const int* trp, const int* tci, int i,
+                                             const int* col, int c) {
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (ci[p] != i && col[ci[p]] == c) return true;
+  for (int p = trp[i]; p < trp[i + 1]; ++p)
+    if (tci[p] != i && col[tci[p]] == c) return true;
+  return false;
+}
+
+__global__ void k_colour_round(int n, const int* rp, const int* ci, const int* trp, const int* tci, const double* w,
+                               const int* col, int* next, int* left) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (col[i] >= 0) {
+    next[i] = col[i];
+    return;
+  }
+  if (colour_beaten(rp, ci, i, col, w) || colour_beaten(trp, tci, i, col, w)) {
+    next[i] = -1;
+    atomicAdd(left, 1);
+    return;
+  }
+  // the smallest colour no coloured neighbour has: a bit mask for colours < 64
+  unsigned long long used = 0ULL;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int c = col[ci[p]];
+    if (ci[p] != i && c >= 0 && c < 64) used |= 1ULL << c;
+  }
+  for (int p = trp[i]; p < trp[i + 1]; ++p) {
+    int c = col[tci[p]];
+    if (tci[p] != i && c >= 0 && c < 64) used |= 1ULL << c;
+  }
+  int c;
+  if (~used) {
+    c = __ffsll((long long)~used) - 1;
+  } else {
+    c = 64;
+    while (colour_taken(rp, ci, trp, tci, i, col, c)) ++c;
+  }
+  next[i] = c;
+}
+
+// raw sweep class (C: colour, F: ncol + colour) counts and the largest colour
+__global__ void k_colour_max(int n, const int* col, int* mx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicMax(mx, col[i]);
+}
+__global__ void k_key_count(int n, const int* col, const signed char* CF, int ncol, int* cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(cnt + (CF[i] == 1 ? 0 : ncol) + col[i], 1);
+}
+__global__ void k_key_assign(int n, const int* col, const signed char* CF, int ncol, const int* map, int* key) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) key[i] = map[(CF[i] == 1 ? 0 : ncol) + col[i]];
+}
+
+// perm[koff[k] ..): the points of sweep k in increasing index order, one block per sweep
+constexpr int kPermThreads = 1024;
+__global__ void __launch_bounds__(kPermThreads) k_key_perm(int n, const int* __restrict__ key,
+                                                           const int* __restrict__ koff, int* __restrict__ perm) {
+  __shared__ int wsum[kPermThreads / 32];
+  __shared__ int wpre[kPermThreads / 32];
+  __shared__ int total;
+  const int k = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int base = koff[k];
+  for (int start = 0; start < n; start += kPermThreads) {
+    int i = start + threadIdx.x;
+    bool f = i < n && key[i] == k;
+    unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int w = 0; w < kPermThreads / 32; ++w) {
+        wpre[w] = acc;
+        acc += wsum[w];
+      }
+      total = acc;
+    }
+    __syncthreads();
+    if (f) perm[base + wpre[warp] + __popc(bal & ((1u << lane) - 1u))] = i;
+    base += total;
+    __syncthreads();
+  }
+}
+
+void launch_colour_init(int n, unsigned long long seed, int level, double* w, int* col, cudaStream_t s) {
+  k_colour_init<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, seed, level, w, col);
+  MGD_LAUNCH_CHECK();
+}
+void launch_colour_round(int n, const int* rp, const int* ci, const int* trp, const int* tci, const double* w,
+                         const int* col, int* next, int* left, cudaStream_t s) {
+  k_colour_round<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, trp, tci, w, col, next, left);
+  MGD_LAUNCH_CHECK();
+}
+void launch_colour_max(int n, const int* col, int* mx, cudaStream_t s) {
+  k_colour_max<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, col, mx);
+  MGD_LAUNCH_CHECK();
+}
+void launch_key_count(int n, const int* col, const signed char* CF, int ncol, int* cnt, cudaStream_t s) {
+  k_key_count<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, col, CF, ncol, cnt);
+  MGD_LAUNCH_CHECK();
+}
+void launch_key_assign(int n, const int* col, const signed char* CF, int ncol, const int* map, int* key,
+                       cudaStream_t s) {
+  k_key_assign<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, col, CF, ncol, map, key);
+  MGD_LAUNCH_CHECK();
+}
+void launch_key_perm(int n, int nk, const int* key, const int* koff, int* perm, cudaStream_t s) {
+  if (nk <= 0) return;
+  k_key_perm<<<nk, kPermThreads, 0, s>>>(n, key, koff, perm);
+  MGD_LAUNCH_CHECK();
+}
+
 __device__ __forceinline__ bool beats(const double* w, int i, int j) {
   return w[i] > w[j] || (w[i] == w[j] && i > j);
 }

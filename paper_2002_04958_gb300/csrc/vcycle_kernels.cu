@@ -154,6 +154,98 @@ void launch_phase(int phase, int fmtA, int fmtRP, const LDesc<T>* d_descs, int n
 template void launch_phase<double>(int, int, int, const LDesc<double>*, int, int, cudaStream_t);
 template void launch_phase<float>(int, int, int, const LDesc<float>*, int, int, cudaStream_t);
 
+// ---------------------------------------------------------------- Gauss-Seidel smoothing (Section 3.1)
+// Multicolour Gauss-Seidel in C/F order.  Down: the first sweep from a zero
+// iterate (xt = b / a_ii on sweep 0's points, 0 elsewhere), then sweeps
+// 1 .. nk-1, then r = b - A xt.  Up (after the prolongation): sweeps
+// nk-1 .. 0.  A sweep updates its points in place: they are uncoupled, so
+// every point reads only values of other sweeps.  x is the same buffer as xt
+// on these levels.
+template <typename T>
+__global__ void k_gs_first(const LDesc<T>* __restrict__ descs) {
+  MGD_PDL_ENTRY();
+  const LDesc<T>* d = descs + blockIdx.y;
+  MGD_SKIP_INACTIVE(d);
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d->n) d->xt[i] = d->key[i] == 0 ? d->b[i] * d->gdinv[i] : T(0);
+}
+
+// step t of the down (up == 0: sweep t) or up (up == 1: sweep nk-1-t) smoothing
+template <typename T, int TPR>
+__global__ void __launch_bounds__(kThreads) k_gs_sweep(const LDesc<T>* __restrict__ descs, int t, int up) {
+  MGD_PDL_ENTRY();
+  const LDesc<T>* d = descs + blockIdx.y;
+  MGD_SKIP_INACTIVE(d);
+  const int nk = d->nk;
+  const int k = up ? nk - 1 - t : t;
+  if (k < 0 || k >= nk) return;
+  const int seg = d->koff[k], cnt = d->koff[k + 1] - seg;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int idx = g / TPR, lane = g % TPR;
+  if (((g & ~31) / TPR) >= cnt) return;  // whole warp past the sweep's last point
+  bool valid = idx < cnt;
+  int row = valid ? d->perm[seg + idx] : 0;
+  T s = T(0);
+  if (valid) {
+    int e = d->rp[row + 1];
+    for (int p = d->rp[row] + lane; p < e; p += TPR) s += d->v[p] * d->xt[d->ci[p]];
+  }
+#pragma unroll
+  for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (valid && lane == 0) d->xt[row] = d->xt[row] + (d->b[row] - s) * d->gdinv[row];
+}
+
+// r = b - A xt after the down sweeps (the level's A layout)
+template <typename T, int FMT>
+__global__ void __launch_bounds__(kThreads) k_gs_resid(const LDesc<T>* __restrict__ descs) {
+  MGD_PDL_ENTRY();
+  const LDesc<T>* d = descs + blockIdx.y;
+  MGD_SKIP_INACTIVE(d);
+  constexpr int TPR = FmtTraits<FMT>::tpr;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = g / TPR, lane = g % TPR;
+  int n = d->n;
+  if (((g & ~31) / TPR) >= n) return;
+  bool valid = row < n;
+  XPlain<T> xf{d->xt};
+  T s = row_dot<T, FMT>(row, lane, valid, d->rp, d->ci, d->v, d->sptr, d->sci, d->sv, xf);
+  if (valid && lane == 0) d->r[row] = d->b[row] - s;
+}
+
+template <typename T>
+void launch_gs_first(const LDesc<T>* d, int nd, int maxrows, cudaStream_t s) {
+  if (nd <= 0 || maxrows <= 0) return;
+  launch_k(k_gs_first<T>, dim3(cdiv(maxrows, kThreads), nd), dim3(kThreads), 0, s, d);
+  MGD_LAUNCH_CHECK();
+}
+
+template <typename T>
+void launch_gs_sweep(int tpr, const LDesc<T>* d, int nd, int maxrows, int t, int up, cudaStream_t s) {
+  if (nd <= 0 || maxrows <= 0) return;
+  dim3 g(cdiv((long long)maxrows * tpr + 32, kThreads), nd);
+  switch (tpr) {
+    case 1: launch_k(k_gs_sweep<T, 1>, g, dim3(kThreads), 0, s, d, t, up); break;
+    case 2: launch_k(k_gs_sweep<T, 2>, g, dim3(kThreads), 0, s, d, t, up); break;
+    case 4: launch_k(k_gs_sweep<T, 4>, g, dim3(kThreads), 0, s, d, t, up); break;
+    default: launch_k(k_gs_sweep<T, 8>, g, dim3(kThreads), 0, s, d, t, up); break;
+  }
+  MGD_LAUNCH_CHECK();
+}
+
+template <typename T>
+void launch_gs_resid(int fmtA, const LDesc<T>* d, int nd, int maxrows, cudaStream_t s) {
+  if (nd <= 0 || maxrows <= 0) return;
+  MGD_DISPATCH_FMT(k_gs_resid, fmtA, maxrows, nd, s, d);
+  MGD_LAUNCH_CHECK();
+}
+
+template void launch_gs_first<double>(const LDesc<double>*, int, int, cudaStream_t);
+template void launch_gs_first<float>(const LDesc<float>*, int, int, cudaStream_t);
+template void launch_gs_sweep<double>(int, const LDesc<double>*, int, int, int, int, cudaStream_t);
+template void launch_gs_sweep<float>(int, const LDesc<float>*, int, int, int, int, cudaStream_t);
+template void launch_gs_resid<double>(int, const LDesc<double>*, int, int, cudaStream_t);
+template void launch_gs_resid<float>(int, const LDesc<float>*, int, int, cudaStream_t);
+
 // ---------------------------------------------------------------- fused coarse levels
 // All levels from the first fused level down to the coarsest, and back up,
 // in one launch: one thread-block cluster per subsystem, the phases separated
@@ -207,19 +299,46 @@ __global__ void __launch_bounds__(kTailThreads) k_vtail(const TailSub<T>* __rest
       body(r, r < nrows);
     }
   };
+  // one Gauss-Seidel sweep (index sw) of level d, in place on xt
+  auto gs_sweep = [&](const LDesc<T>* d, int sw) {
+    const int seg = __ldg(d->koff + sw), cnt = __ldg(d->koff + sw + 1) - seg;
+    for_rows(cnt, [&](int r, bool ok) {
+      int row = ok ? __ldg(d->perm + seg + r) : 0;
+      T s = tail_row<T>(d->rp, d->ci, d->v, d->xt, row, lane, ok);
+      if (ok && lane == 0) d->xt[row] = __ldcg(d->xt + row) + (__ldcg(d->b + row) - s) * __ldg(d->gdinv + row);
+    });
+  };
   const int L = S.nlev;
   for (int k = 0; k < L - 1; ++k) {
     const LDesc<T>* d = S.lev + k;
     const int n = d->n, nc = d->nc;
-    // pre-smoothing from zero + residual: xt = D^-1 b, r = b - (A D^-1) b
-    for_rows(n, [&](int r, bool ok) {
-      T s = tail_row<T>(d->rp, d->ci, d->vpre, d->b, r, lane, ok);
-      if (ok && lane == 0) {
-        T bi = __ldcg(d->b + r);
-        d->xt[r] = __ldg(d->dinv + r) * bi;
-        d->r[r] = bi - s;
+    const int nk = d->nk;
+    if (nk > 0) {
+      // Gauss-Seidel down: sweep 0 from zero, sweeps 1 .. nk-1, then r = b - A xt
+      for_rows(n, [&](int r, bool ok) {
+        if (ok && lane == 0)
+          d->xt[r] = __ldg(d->key + r) == 0 ? __ldcg(d->b + r) * __ldg(d->gdinv + r) : T(0);
+      });
+      cl.sync();
+      for (int sw = 1; sw < nk; ++sw) {
+        gs_sweep(d, sw);
+        cl.sync();
       }
-    });
+      for_rows(n, [&](int r, bool ok) {
+        T s = tail_row<T>(d->rp, d->ci, d->v, d->xt, r, lane, ok);
+        if (ok && lane == 0) d->r[r] = __ldcg(d->b + r) - s;
+      });
+    } else {
+      // pre-smoothing from zero + residual: xt = D^-1 b, r = b - (A D^-1) b
+      for_rows(n, [&](int r, bool ok) {
+        T s = tail_row<T>(d->rp, d->ci, d->vpre, d->b, r, lane, ok);
+        if (ok && lane == 0) {
+          T bi = __ldcg(d->b + r);
+          d->xt[r] = __ldg(d->dinv + r) * bi;
+          d->r[r] = bi - s;
+        }
+      });
+    }
     cl.sync();
     for_rows(nc, [&](int r, bool ok) {  // restriction
       T s = tail_row<T>(d->rrp, d->rci, d->rv, d->r, r, lane, ok);
@@ -259,6 +378,13 @@ __global__ void __launch_bounds__(kTailThreads) k_vtail(const TailSub<T>* __rest
       if (ok && lane == 0) d->xt[r] = __ldcg(d->xt + r) + s;
     });
     cl.sync();
+    if (d->nk > 0) {  // Gauss-Seidel up: the opposite traversal, in place (x is xt)
+      for (int sw = d->nk - 1; sw >= 0; --sw) {
+        gs_sweep(d, sw);
+        cl.sync();
+      }
+      continue;
+    }
     for_rows(n, [&](int r, bool ok) {  // post-smoothing
       T s = tail_row<T>(d->rp, d->ci, d->v, d->xt, r, lane, ok);
       if (ok && lane == 0) d->x[r] = __ldcg(d->xt + r) + __ldg(d->dinv + r) * (__ldcg(d->b + r) - s);

@@ -25,7 +25,7 @@ ENTRY_POINTS = ["mgd_opts_default", "mgd_create", "mgd_setup", "mgd_update_value
                 "mgd_solve_transpose", "mgd_grad_values", "mgd_precond_apply", "mgd_get_stats", "mgd_get_history",
                 "mgd_op_info", "mgd_level_info", "mgd_level_export", "mgd_block_vector", "mgd_coupling_dropped",
                 "mgd_profile_enable", "mgd_profile_read", "mgd_kernel_launches", "mgd_last_error", "mgd_destroy", "mgd_plan_info",
-                "mgd_setup_phases", "mgd_op_cycles",
+                "mgd_setup_phases", "mgd_op_cycles", "mgd_level_keys",
                 "mgd_relres_noalloc"]
 
 
@@ -37,7 +37,8 @@ class MgdOpts(C.Structure):
                 ("jacobi_sweeps", C.c_int), ("adaptive", C.c_int), ("seed", C.c_ulonglong),
                 ("restart", C.c_int), ("max_it", C.c_int), ("precision", C.c_int), ("batched", C.c_int),
                 ("use_graph", C.c_int), ("autotune", C.c_int), ("keep_transpose", C.c_int),
-                ("fuse_rows", C.c_int), ("interp_type", C.c_int), ("pdl", C.c_int), ("inner_mode", C.c_int)]
+                ("fuse_rows", C.c_int), ("interp_type", C.c_int), ("pdl", C.c_int), ("inner_mode", C.c_int),
+                ("smoother", C.c_int)]
 
 
 class MgdStats(C.Structure):
@@ -79,6 +80,7 @@ def lib():
             "mgd_op_info": (I, [P, I, pI, pI, pI, pI, pI]),
             "mgd_level_info": (I, [P, I, I, pI, pI, pI, pI]),
             "mgd_op_cycles": (I, [P, I, pLL]),
+            "mgd_level_keys": (I, [P, I, I, pI, P]),
             "mgd_level_export": (I, [P, I, I, P, P, P, P, P, P, P]),
             "mgd_block_vector": (I, [P, I, I, I, P]),
             "mgd_coupling_dropped": (I, [P, I, I]),
@@ -258,6 +260,18 @@ class Solver:
         self._check(lib().mgd_op_cycles(self.h, op, C.byref(v)))
         return v.value
 
+    def level_keys(self, op, l):
+        """Gauss-Seidel sweep index per point of level l of operator op (None without GS there)."""
+        nk = C.c_int()
+        self._check(lib().mgd_level_keys(self.h, op, l, C.byref(nk), None))
+        if nk.value == 0:
+            return None, 0
+        n = C.c_int()
+        self._check(lib().mgd_level_info(self.h, op, l, C.byref(n), None, None, None))
+        key = np.zeros(n.value, np.int32)
+        self._check(lib().mgd_level_keys(self.h, op, l, C.byref(nk), key.ctypes.data_as(C.c_void_p)))
+        return key, nk.value
+
     def total_cycles(self):
         """V-cycles applied by every inverse since setup."""
         return sum(self.op_cycles(k) for k in range(self.stats()["n_ops"]))
@@ -283,7 +297,8 @@ class Solver:
         return out
 
     SETUP_PHASES = ["strength", "pmis", "interp", "transpose", "AP", "RAP", "finalize", "coarse_inverse",
-                    "validate", "blocks", "hierarchies_wall", "pctl", "program_autotune", "krylov_graph"]
+                    "validate", "blocks", "hierarchies_wall", "pctl", "program_autotune", "krylov_graph",
+                    "gs_colouring"]
 
     def setup_phases(self):
         ms = np.zeros(16)
