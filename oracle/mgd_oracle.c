@@ -90,6 +90,7 @@ void or_default_opts(or_opts *o) {
   o->inner_mode = 0;
   o->interp_type = 0;
   o->smoother = 0;
+  o->agg_levels = 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -766,6 +767,39 @@ static void gs_order(or_amg *h, int l, const or_csr *A, const int8_t *CF, uint64
   free(map);
 }
 
+/* Aggressive coarsening of level l (Section 3.1): the first pass gave CF and
+   P1 = h->P[l].  A second strength + PMIS pass (weights from stream 1100 + l)
+   on A1 = P1^T A P1 picks the final C points among the first pass's; P2
+   interpolates from them to A1's points and P = P1 P2.  A1 is not a level.
+   The level's C/F marks become: C where the first pass's C point stays C,
+   F (-1) where it does not, the first pass's mark elsewhere.  If the second
+   pass stalls (no C point, or all C) the level keeps the first pass. */
+static void aggressive_pass(or_amg *h, int l, const or_csr *A, const or_opts *o) {
+  or_csr *P1 = h->P[l];
+  or_csr *A1 = or_rap(A, P1);
+  int n1 = A1->n;
+  uint8_t *S1 = (uint8_t *)xmalloc((size_t)A1->nnz + 1);
+  or_strength(A1, o->theta_str, S1);
+  int8_t *CF1 = (int8_t *)xmalloc((size_t)n1 + 1);
+  int nc1 = or_pmis(A1, S1, o->seed, 100 + l, CF1);
+  if (nc1 > 0 && nc1 < n1) {
+    or_csr *P2 = o->interp_type == 1 ? or_interp_exti(A1, S1, CF1) : or_interp(A1, S1, CF1);
+    h->P[l] = or_spgemm(P1, P2);
+    int8_t *CF = h->CF[l];
+    int c = 0;
+    for (int i = 0; i < A->n; ++i) {
+      if (CF[i] != 1) continue;
+      CF[i] = CF1[c] == 1 ? 1 : -1;
+      ++c;
+    }
+    or_csr_free(P1);
+    or_csr_free(P2);
+  }
+  or_csr_free(A1);
+  free(S1);
+  free(CF1);
+}
+
 or_amg *or_amg_setup(const or_csr *A0, const or_opts *o) {
   int cap = o->max_levels > 0 ? o->max_levels : 1;
   or_amg *h = (or_amg *)xcalloc(1, sizeof(or_amg));
@@ -801,8 +835,9 @@ or_amg *or_amg_setup(const or_csr *A0, const or_opts *o) {
       break;
     }
     h->CF[l] = CF;
-    if (o->smoother == 1) gs_order(h, l, A, CF, o->seed);
     h->P[l] = o->interp_type == 1 ? or_interp_exti(A, S, CF) : or_interp(A, S, CF);
+    if (l < o->agg_levels) aggressive_pass(h, l, A, o);
+    if (o->smoother == 1) gs_order(h, l, A, h->CF[l], o->seed);
     h->R[l] = or_transpose(h->P[l]);
     h->A[l + 1] = or_rap(A, h->P[l]);
     free(S);

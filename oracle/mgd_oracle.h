@@ -42,6 +42,9 @@ typedef struct or_opts {
   int interp_type;        /* 0: classical modified (Section 3.1); 1: extended+i (distance two) */
   int smoother;           /* 0: l1-Jacobi; 1: Gauss-Seidel in C/F order (Section 3.1's hybrid GS), read
                              as multicolour GS: C colours then F colours on the way down, the reverse up */
+  int agg_levels;         /* levels, from the finest, coarsened aggressively (Section 3.1): a second PMIS
+                             pass on the Galerkin operator of the first, which is not kept as a level;
+                             P = P1 P2 (two-stage interpolation).  0: none (default) */
 } or_opts;
 
 /* preconditioner kinds */

@@ -442,3 +442,39 @@ def test_option3_cycle_counts_are_the_first_to_reach_tolerance(orc):
             k += 1
         assert 1 < k < 100
         assert M.cycles(3, g) == k, (g, M.cycles(3, g), k)
+
+
+# ---------------------------------------------------------------- aggressive coarsening (Section 3.1)
+@pytest.mark.parametrize("interp_type", [0, 1])
+def test_aggressive_level_is_two_passes_with_product_interpolation(orc, interp_type):
+    s = I.make_system(1, (40, 36), inclusion=True)
+    Ao = orc.csr_of_system(s)
+    A = s.scipy().toarray()
+    ha = orc.Amg(Ao, orc.opts(agg_levels=1, interp_type=interp_type))
+    hp = orc.Amg(Ao, orc.opts(interp_type=interp_type, max_levels=2))   # first pass only
+    P1 = hp.P(0).scipy().toarray()
+    A1 = hp.A(1)
+    S1 = orc.strength(A1)
+    nc1, CF1 = orc.pmis(A1, S1, seed=0, level=100)                     # the second pass's weight stream
+    P2 = (orc.interp_exti if interp_type else orc.interp)(A1, S1, CF1).scipy().toarray()
+    P = ha.P(0).scipy().toarray()
+    assert P.shape == (s.n, nc1) and 0 < nc1 < A1.info()[0]
+    assert np.allclose(P, P1 @ P2, rtol=0, atol=1e-14 * abs(P).max())
+    # C/F marks: C exactly where the first pass's C point stays C; those rows of P are identity rows
+    CF, CF0 = ha.CF(0), hp.CF(0)
+    assert np.array_equal(CF[CF0 == 1] == 1, CF1 == 1) and np.array_equal(CF[CF0 != 1], CF0[CF0 != 1])
+    cols = np.cumsum(CF == 1) - 1
+    for i in np.flatnonzero(CF == 1):
+        row = np.zeros(nc1)
+        row[cols[i]] = 1.0
+        assert np.array_equal(P[i], row)
+    Ac = ha.A(1).scipy().toarray()
+    assert np.allclose(Ac, P.T @ A @ P, rtol=0, atol=1e-12 * abs(Ac).max())
+    # fewer coarse points and a smaller operator complexity than the standard hierarchy
+    hs = orc.Amg(Ao, orc.opts(interp_type=interp_type))
+    assert nc1 < 0.5 * hs.A(1).info()[0]
+    cplx = lambda h: sum(h.A(l).info()[2] for l in range(h.nlevels))
+    assert cplx(ha) < 0.8 * cplx(hs)
+    # a working preconditioner still
+    x, it, _, st, _ = orc.fgmres(Ao, s.b, orc.Block(Ao, s.G, s.N, "schur1", orc.opts(agg_levels=1)), tol=1e-8)
+    assert st == 0
