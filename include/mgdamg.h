@@ -97,6 +97,10 @@ typedef struct mgd_opts {
                              counter generator, stream 2000 + level); pre-smoothing sweeps the C colours then
                              the F colours, post-smoothing the same classes in the opposite order; each sweep
                              updates x_i += (b_i - (A x)_i) / a_ii for its (mutually uncoupled) points */
+  int agg_levels;         /* levels, from the finest, coarsened aggressively (Section 3.1): a second strength +
+                             PMIS pass (weight stream 1100 + level) on A1 = P1^T A P1, which is not kept as a
+                             level, chooses the final C points among the first pass's; P = P1 P2 (two-stage
+                             interpolation, each stage of interp_type).  0: none (default); at most max_levels */
 } mgd_opts;
 
 /* Fill *o with the defaults listed above.  Returns MGD_EINVAL if o is NULL. */

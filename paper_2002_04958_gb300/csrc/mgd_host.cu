@@ -176,6 +176,7 @@ struct Level {
   std::vector<int> koff_h;
   double* gdinv = nullptr;
   float* gdinv32 = nullptr;
+  Sell gsell;  // rows in sweep order (forward operator)
 };
 
 struct Hier {
@@ -275,7 +276,7 @@ static Csr spgemm(Arena& a, const Csr& X, const Csr& Y, cudaStream_t s, Scratch*
   return C;
 }
 
-static Csr transpose(Arena& a, const Csr& X, cudaStream_t s) {
+static Csr transpose(Arena& a, const Csr& X, cudaStream_t s, Scratch* keep = nullptr) {
   Scratch sc(s);
   Csr T;
   T.n = X.m;
@@ -284,10 +285,10 @@ static Csr transpose(Arena& a, const Csr& X, cudaStream_t s) {
   int* cnt = sc.alloc<int>(X.m);
   MGD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * std::max(X.m, 1), s));
   launch_transpose_count(X.nnz, X.ci, cnt, s);
-  T.rp = a.alloc<int>(T.n + 1);
+  T.rp = keep ? keep->alloc<int>(T.n + 1) : a.alloc<int>(T.n + 1);
   exclusive_scan(cnt, T.rp, T.n, s);
-  T.ci = a.alloc<int>(T.nnz);
-  T.v = a.alloc<double>(T.nnz);
+  T.ci = keep ? keep->alloc<int>(T.nnz) : a.alloc<int>(T.nnz);
+  T.v = keep ? keep->alloc<double>(T.nnz) : a.alloc<double>(T.nnz);
   int* cur = sc.alloc<int>(X.m);
   MGD_CUDA(cudaMemsetAsync(cur, 0, sizeof(int) * std::max(X.m, 1), s));
   launch_transpose_fill(X.n, X.rp, X.ci, X.v, T.rp, cur, T.ci, T.v, s);
@@ -295,7 +296,7 @@ static Csr transpose(Arena& a, const Csr& X, cudaStream_t s) {
   return T;
 }
 
-static Sell build_sell(Arena& a, const Csr& A, bool mixed, cudaStream_t s) {
+static Sell build_sell(Arena& a, const Csr& A, bool mixed, cudaStream_t s, const int* selfmap = nullptr) {
   Scratch sc(s);
   Sell S;
   S.n = A.n;
@@ -307,7 +308,7 @@ static Sell build_sell(Arena& a, const Csr& A, bool mixed, cudaStream_t s) {
   S.nstored = read_int(S.sptr + S.nslices, s);
   S.ci = a.alloc<int>(S.nstored);
   S.v = a.alloc<double>(S.nstored);
-  launch_sell_fill(A.n, A.rp, A.ci, A.v, S.sptr, S.ci, S.v, s);
+  launch_sell_fill(A.n, A.rp, A.ci, A.v, S.sptr, S.ci, S.v, s, selfmap);
   if (mixed) {
     S.v32 = a.alloc<float>(S.nstored);
     launch_cast_f64_f32((int)S.nstored, S.v, S.v32, s);
@@ -383,6 +384,117 @@ static void gs_order(Arena& ar, Level& lv, int level, unsigned long long seed, c
   MGD_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope
 }
 
+// One coarsening pass on A (Section 3.1): strength, PMIS with the weight stream
+// 1000 + lid, interpolation.  CF and P come from `keep` when given (a pass
+// whose result is not kept as a level), else from the arena.  Returns false
+// when the pass stalls (no C point, or all C).
+struct Pass {
+  signed char* CF = nullptr;
+  int nc = 0;
+  Csr P;
+};
+static bool coarsen_pass(SetupCtx& sc, const Csr& A, int lid, Scratch* keep, Pass& out) {
+  Arena& ar = *sc.arena;
+  cudaStream_t s = sc.s;
+  const mgd_opts& o = *sc.o;
+  const int n = A.n;
+  Scratch tmp(s);
+  PhaseTimer pt_str(sc.clk, SP_STRENGTH);
+  uint8_t* S = tmp.alloc<uint8_t>(A.nnz);
+  launch_strength(n, A.rp, A.ci, A.v, o.theta_str, S, s);
+  int* cnt = tmp.alloc<int>(n);
+  MGD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * n, s));
+  launch_count_st(n, A.rp, A.ci, S, cnt, s);
+  int* strp = tmp.alloc<int>(n + 1);
+  exclusive_scan(cnt, strp, n, s);
+  int nst = read_int(strp + n, s);
+  int* stci = tmp.alloc<int>(nst);
+  int* cur = tmp.alloc<int>(n);
+  MGD_CUDA(cudaMemsetAsync(cur, 0, sizeof(int) * n, s));
+  launch_fill_st(n, A.rp, A.ci, S, strp, cur, stci, s);
+  pt_str.stop();
+  PhaseTimer pt_pmis(sc.clk, SP_PMIS);
+  double* w = tmp.alloc<double>(n);
+  signed char* CF = keep ? keep->alloc<signed char>(n) : ar.alloc<signed char>(n);
+  launch_pmis_init(n, A.rp, S, cnt, o.seed, lid, w, CF, s);
+  uint8_t* newc = tmp.alloc<uint8_t>(n);
+  int* und = tmp.alloc<int>(1);
+  // rounds are idempotent once every point is decided, so the undecided
+  // count is read back only every second round
+  for (int round = 0; round < n + 1; round += 2) {
+    launch_pmis_round(n, A.rp, A.ci, S, strp, stci, w, CF, newc, und, s);
+    launch_pmis_round(n, A.rp, A.ci, S, strp, stci, w, CF, newc, und, s);
+    if (read_int(und, s) == 0) break;
+  }
+  pt_pmis.stop();
+  PhaseTimer pt_int(sc.clk, SP_INTERP);
+  int* pcnt = tmp.alloc<int>(n);
+  int* isc = tmp.alloc<int>(n);
+  launch_interp_count(n, A.rp, A.ci, S, CF, pcnt, isc, s);
+  int* cidx = tmp.alloc<int>(n + 1);
+  exclusive_scan(isc, cidx, n, s);
+  int nc = read_int(cidx + n, s);
+  if (nc == 0 || nc == n) return false;
+  Csr P;
+  P.n = n;
+  P.m = nc;
+  P.rp = keep ? keep->alloc<int>(n + 1) : ar.alloc<int>(n + 1);
+  if (o.interp_type == 1) {  // extended+i: distance-two interpolatory sets
+    int* ub = tmp.alloc<int>(n);
+    launch_exti_ub(n, A.rp, A.ci, S, CF, pcnt, ub, s);
+    long long* off = tmp.alloc<long long>(n + 1);
+    launch_offsets64(ub, off, n, s);
+    long long tot = 0;
+    MGD_CUDA(cudaMemcpyAsync(&tot, off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    MGD_CUDA(cudaStreamSynchronize(s));
+    int* list = tmp.alloc<int>(tot);
+    int* len = tmp.alloc<int>(n);
+    launch_exti_list(n, A.rp, A.ci, S, CF, off, list, len, s);
+    exclusive_scan(len, P.rp, n, s);
+    P.nnz = read_int(P.rp + n, s);
+    P.ci = keep ? keep->alloc<int>(P.nnz) : ar.alloc<int>(P.nnz);
+    P.v = keep ? keep->alloc<double>(P.nnz) : ar.alloc<double>(P.nnz);
+    launch_exti_fill(n, A.rp, A.ci, A.v, S, CF, cidx, off, list, P.rp, P.ci, P.v, s);
+  } else {
+    exclusive_scan(pcnt, P.rp, n, s);
+    P.nnz = read_int(P.rp + n, s);
+    P.ci = keep ? keep->alloc<int>(P.nnz) : ar.alloc<int>(P.nnz);
+    P.v = keep ? keep->alloc<double>(P.nnz) : ar.alloc<double>(P.nnz);
+    launch_interp_fill(n, A.rp, A.ci, A.v, S, CF, cidx, P.rp, P.ci, P.v, s);
+  }
+  pt_int.stop();
+  out.CF = CF;
+  out.nc = nc;
+  out.P = P;
+  return true;
+}
+
+// Aggressive coarsening of level l (Section 3.1): a second pass, with the
+// weight stream 1100 + l, on A1 = P1^T A P1 (not kept as a level) picks the
+// final C points among the first pass's; P = P1 P2.  The first pass's C
+// points that the second pass makes F become F.  A stalled second pass keeps
+// the first pass.
+static void aggressive_pass(SetupCtx& sc, const Csr& A, int l, Pass& pass) {
+  Arena& ar = *sc.arena;
+  cudaStream_t s = sc.s;
+  const int n = A.n;
+  Scratch ak(s, ar.pool);
+  Csr R1 = transpose(ar, pass.P, s, &ak);
+  Csr AP1 = spgemm(ar, A, pass.P, s, &ak);
+  Csr A1 = spgemm(ar, R1, AP1, s, &ak);
+  Pass p2;
+  if (!coarsen_pass(sc, A1, 100 + l, &ak, p2)) return;
+  Csr P = spgemm(ar, pass.P, p2.P, s);
+  int* flag = ak.alloc<int>(n);
+  int* cidx = ak.alloc<int>(n + 1);
+  launch_cf_flag(n, pass.CF, flag, s);
+  exclusive_scan(flag, cidx, n, s);
+  launch_cf_compose(n, pass.CF, cidx, p2.CF, s);
+  pass.P = P;
+  pass.nc = p2.nc;
+  MGD_CUDA(cudaStreamSynchronize(s));
+}
+
 // Section 3.1 setup: strength -> PMIS -> interpolation -> R = P^T -> A_c = R (A P),
 // level by level until the coarsest criterion; then smoother diagonals,
 // kernel layouts, FP32 copies and the coarsest dense inverse.
@@ -397,78 +509,17 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
     Level& lv = h.L[l];
     int n = lv.A.n;
     if (n <= o.max_coarse || l == o.max_levels - 1) break;
-    Scratch tmp(s);
-    PhaseTimer pt_str(sc.clk, SP_STRENGTH);
-    uint8_t* S = tmp.alloc<uint8_t>(lv.A.nnz);
-    launch_strength(n, lv.A.rp, lv.A.ci, lv.A.v, o.theta_str, S, s);
-    int* cnt = tmp.alloc<int>(n);
-    MGD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * n, s));
-    launch_count_st(n, lv.A.rp, lv.A.ci, S, cnt, s);
-    int* strp = tmp.alloc<int>(n + 1);
-    exclusive_scan(cnt, strp, n, s);
-    int nst = read_int(strp + n, s);
-    int* stci = tmp.alloc<int>(nst);
-    int* cur = tmp.alloc<int>(n);
-    MGD_CUDA(cudaMemsetAsync(cur, 0, sizeof(int) * n, s));
-    launch_fill_st(n, lv.A.rp, lv.A.ci, S, strp, cur, stci, s);
-    pt_str.stop();
-    PhaseTimer pt_pmis(sc.clk, SP_PMIS);
-    double* w = tmp.alloc<double>(n);
-    signed char* CF = ar.alloc<signed char>(n);
-    launch_pmis_init(n, lv.A.rp, S, cnt, o.seed, l, w, CF, s);
-    uint8_t* newc = tmp.alloc<uint8_t>(n);
-    int* und = tmp.alloc<int>(1);
-    // rounds are idempotent once every point is decided, so the undecided
-    // count is read back only every second round
-    for (int round = 0; round < n + 1; round += 2) {
-      launch_pmis_round(n, lv.A.rp, lv.A.ci, S, strp, stci, w, CF, newc, und, s);
-      launch_pmis_round(n, lv.A.rp, lv.A.ci, S, strp, stci, w, CF, newc, und, s);
-      if (read_int(und, s) == 0) break;
-    }
-    pt_pmis.stop();
-    PhaseTimer pt_int(sc.clk, SP_INTERP);
-    int* pcnt = tmp.alloc<int>(n);
-    int* isc = tmp.alloc<int>(n);
-    launch_interp_count(n, lv.A.rp, lv.A.ci, S, CF, pcnt, isc, s);
-    int* cidx = tmp.alloc<int>(n + 1);
-    exclusive_scan(isc, cidx, n, s);
-    int nc = read_int(cidx + n, s);
-    if (nc == 0 || nc == n) break;  // coarsening stalled: this level is the coarsest
-    lv.CF = CF;
-    lv.nc = nc;
+    Pass pass;
+    if (!coarsen_pass(sc, lv.A, l, nullptr, pass)) break;  // coarsening stalled: this level is the coarsest
+    if (l < o.agg_levels) aggressive_pass(sc, lv.A, l, pass);
+    lv.CF = pass.CF;
+    lv.nc = pass.nc;
     if (o.smoother == 1) {
       PhaseTimer pt_col(sc.clk, SP_COLOUR);
       gs_order(ar, lv, l, o.seed, s);
     }
-    Csr P;
-    P.n = n;
-    P.m = nc;
-    P.rp = ar.alloc<int>(n + 1);
-    if (o.interp_type == 1) {  // extended+i: distance-two interpolatory sets
-      int* ub = tmp.alloc<int>(n);
-      launch_exti_ub(n, lv.A.rp, lv.A.ci, S, CF, pcnt, ub, s);
-      long long* off = tmp.alloc<long long>(n + 1);
-      launch_offsets64(ub, off, n, s);
-      long long tot = 0;
-      MGD_CUDA(cudaMemcpyAsync(&tot, off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
-      MGD_CUDA(cudaStreamSynchronize(s));
-      int* list = tmp.alloc<int>(tot);
-      int* len = tmp.alloc<int>(n);
-      launch_exti_list(n, lv.A.rp, lv.A.ci, S, CF, off, list, len, s);
-      exclusive_scan(len, P.rp, n, s);
-      P.nnz = read_int(P.rp + n, s);
-      P.ci = ar.alloc<int>(P.nnz);
-      P.v = ar.alloc<double>(P.nnz);
-      launch_exti_fill(n, lv.A.rp, lv.A.ci, lv.A.v, S, CF, cidx, off, list, P.rp, P.ci, P.v, s);
-    } else {
-      exclusive_scan(pcnt, P.rp, n, s);
-      P.nnz = read_int(P.rp + n, s);
-      P.ci = ar.alloc<int>(P.nnz);
-      P.v = ar.alloc<double>(P.nnz);
-      launch_interp_fill(n, lv.A.rp, lv.A.ci, lv.A.v, S, CF, cidx, P.rp, P.ci, P.v, s);
-    }
+    Csr P = pass.P;
     lv.P = P;
-    pt_int.stop();
     PhaseTimer pt_tr(sc.clk, SP_TRANSPOSE);
     lv.R = transpose(ar, P, s);
     pt_tr.stop();
@@ -493,6 +544,19 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
       lv.gdinv = ar.alloc<double>(n);
       launch_diag_inv(n, lv.A.rp, lv.A.ci, lv.A.v, lv.gdinv, s);
       if (sc.mixed) lv.gdinv32 = cast32(ar, lv.gdinv, n, s);
+      Scratch ps(s);
+      Csr Ap;
+      Ap.n = n;
+      Ap.m = lv.A.m;
+      Ap.nnz = lv.A.nnz;
+      int* len = ps.alloc<int>(n);
+      launch_perm_row_len(n, lv.perm, lv.A.rp, len, s);
+      Ap.rp = ps.alloc<int>(n + 1);
+      exclusive_scan(len, Ap.rp, n, s);
+      Ap.ci = ps.alloc<int>(Ap.nnz);
+      Ap.v = ps.alloc<double>(Ap.nnz);
+      launch_perm_rows_fill(n, lv.perm, lv.A.rp, lv.A.ci, lv.A.v, Ap.rp, Ap.ci, Ap.v, s);
+      lv.gsell = build_sell(ar, Ap, sc.mixed, s, lv.perm);
     }
     lv.sell = build_sell(ar, lv.A, sc.mixed, s);
     const bool jac = lv.nk == 0;  // A D^-1 feeds only the l1-Jacobi pre-smoothing
@@ -580,7 +644,8 @@ struct VBatch {
     double bytes_post_cj = 0;  // post-smoothing of the stalled coarsest levels
     // Gauss-Seidel levels: sweep steps and, per step, the largest class over the subsystems
     bool gs = false;
-    int nkmax = 0, tprGS = 4;
+    int nkmax = 0, fmtGS = FMT_CSR4;  // sweep layout; SELL only where the sweep-ordered copy exists
+    bool gs_sell = false;
     std::vector<int> seg_pre, seg_post;
   };
   std::vector<LP> plan, planT;
@@ -646,6 +711,11 @@ static LDesc<T> make_desc(Hier& h, int l, bool trans) {
   d.perm = lv.perm;
   d.koff = lv.koff;
   d.gdinv = pick<T>(lv.gdinv, lv.gdinv32);
+  if (!trans) {
+    d.gsptr = lv.gsell.sptr;
+    d.gsci = lv.gsell.ci;
+    d.gsv = pick<T>(lv.gsell.v, lv.gsell.v32);
+  }
   return d;
 }
 
@@ -674,6 +744,10 @@ static void build_plan(Arena& ar, VBatch<T>& vb, bool trans, cudaStream_t s) {
         if (lv.nk > 0) {
           // first sweep (key, b, 1/a_ii in; xt out), the other sweeps (rows once, perm,
           // b, 1/a_ii, xt read and written), the residual; up: every sweep
+          if (!lp.gs) {
+            lp.gs_sell = !trans;
+            lp.fmtGS = lp.gs_sell ? FMT_SELL : FMT_CSR4;
+          }
           lp.gs = true;
           lp.nkmax = std::max(lp.nkmax, lv.nk);
           if ((int)lp.seg_pre.size() < lv.nk) {
@@ -728,12 +802,12 @@ static void build_plan(Arena& ar, VBatch<T>& vb, bool trans, cudaStream_t s) {
 template <typename T>
 static void run_gs_down(const typename VBatch<T>::LP& lp, cudaStream_t s) {
   launch_gs_first<T>(lp.d_down, lp.ndown, lp.maxn, s);
-  for (int t = 1; t < lp.nkmax; ++t) launch_gs_sweep<T>(lp.tprGS, lp.d_down, lp.ndown, lp.seg_pre[t], t, 0, s);
+  for (int t = 1; t < lp.nkmax; ++t) launch_gs_sweep<T>(lp.fmtGS, lp.d_down, lp.ndown, lp.seg_pre[t], t, 0, s);
   launch_gs_resid<T>(lp.fmtA, lp.d_down, lp.ndown, lp.maxn, s);
 }
 template <typename T>
 static void run_gs_up(const typename VBatch<T>::LP& lp, cudaStream_t s) {
-  for (int t = 0; t < lp.nkmax; ++t) launch_gs_sweep<T>(lp.tprGS, lp.d_down, lp.ndown, lp.seg_post[t], t, 1, s);
+  for (int t = 0; t < lp.nkmax; ++t) launch_gs_sweep<T>(lp.fmtGS, lp.d_down, lp.ndown, lp.seg_post[t], t, 1, s);
 }
 
 template <typename T>
@@ -901,16 +975,19 @@ static void autotune(VBatch<T>& vb, bool trans, cudaStream_t s) {
         lp.fmtA = f;
       }
     }
-    if (lp.gs) {  // threads per row of the sweeps: time a whole down-smoothing
+    if (lp.gs) {  // layout of the sweeps: time a whole down-smoothing
       best = 1e30f;
-      for (int tpr : {1, 2, 4, 8}) {
-        lp.tprGS = tpr;
+      int pick = lp.fmtGS;
+      for (int f : candA) {
+        if (f == FMT_SELL && !lp.gs_sell) continue;
+        lp.fmtGS = f;
         float ms = time_it([&] { run_gs_down<T>(lp, s); });
         if (ms < best) {
           best = ms;
-          lp.tprGS = tpr;
+          pick = f;
         }
       }
+      lp.fmtGS = pick;
     }
     best = 1e30f;
     for (int f : candRP) {
@@ -1637,7 +1714,7 @@ static void run_program(mgd_ctx* c, bool trans) {
 // level the subsystem count, largest row count and nonzeros): a setup of a
 // system with the same hierarchy shape reuses them instead of re-timing.
 struct TuneResult {
-  std::vector<int> fmtA, fmtR, fmtP, tprGS;
+  std::vector<int> fmtA, fmtR, fmtP, fmtGS;
   int tail_level;
 };
 static std::mutex g_tune_mu;
@@ -1786,12 +1863,13 @@ static void build_batches(mgd_ctx* c) {
           vb.plan[l].fmtA = it->second.fmtA[l];
           vb.plan[l].fmtR = it->second.fmtR[l];
           vb.plan[l].fmtP = it->second.fmtP[l];
-          vb.plan[l].tprGS = it->second.tprGS[l];
+          vb.plan[l].fmtGS = it->second.fmtGS[l];
           if (c->o.keep_transpose) {
             vb.planT[l].fmtA = it->second.fmtA[l];
             vb.planT[l].fmtR = it->second.fmtR[l];
             vb.planT[l].fmtP = it->second.fmtP[l];
-            vb.planT[l].tprGS = it->second.tprGS[l];
+            int f = it->second.fmtGS[l];  // the transposed plan has no sweep-ordered copy
+            vb.planT[l].fmtGS = f == FMT_SELL ? FMT_CSR4 : f;
           }
         }
         cached = true;
@@ -1824,7 +1902,7 @@ static void build_batches(mgd_ctx* c) {
         r.fmtA.push_back(vb.plan[l].fmtA);
         r.fmtR.push_back(vb.plan[l].fmtR);
         r.fmtP.push_back(vb.plan[l].fmtP);
-        r.tprGS.push_back(vb.plan[l].tprGS);
+        r.fmtGS.push_back(vb.plan[l].fmtGS);
       }
       r.tail_level = vb.tail_level;
       std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -2437,6 +2515,7 @@ int mgd_opts_default(mgd_opts* o) {
   o->pdl = 1;
   o->inner_mode = 0;
   o->smoother = 0;
+  o->agg_levels = 0;
   return MGD_OK;
 }
 
@@ -2451,7 +2530,8 @@ int mgd_create(mgd_ctx** out, const mgd_opts* o, void* stream) {
   if (q.max_coarse < 1 || q.max_coarse > 4096 || q.max_levels < 1 || q.restart < 1 || q.restart > 30 ||
       q.precision < 0 || q.precision > 1 || q.inner_mode < 0 || q.inner_mode > 1 || q.inner_maxit < 1 ||
       q.inner_maxit > 100000 || !(q.inner_tol >= 0.0) || q.nvcyc_group > 1000 || q.nvcyc_E > 1000 ||
-      q.nvcyc_I > 1000 || q.nvcyc_other > 1000 || q.jacobi_sweeps > 1000 || q.smoother < 0 || q.smoother > 1) {
+      q.nvcyc_I > 1000 || q.nvcyc_other > 1000 || q.jacobi_sweeps > 1000 || q.smoother < 0 || q.smoother > 1 ||
+      q.agg_levels < 0 || q.agg_levels > q.max_levels) {
     delete c;
     return MGD_EINVAL;
   }

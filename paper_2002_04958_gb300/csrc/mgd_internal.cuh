@@ -215,6 +215,10 @@ struct LDesc {
   const int* koff;
   int nk;
   const T* gdinv;
+  // A's rows in sweep order as SELL-32 (row q = row perm[q], original columns)
+  const int* gsptr;
+  const int* gsci;
+  const T* gsv;
 };
 
 // the V-cycle kernels' first statement after the dependency wait: leave a
@@ -335,6 +339,11 @@ void launch_key_count(int n, const int* col, const signed char* CF, int ncol, in
 void launch_key_assign(int n, const int* col, const signed char* CF, int ncol, const int* map, int* key,
                        cudaStream_t s);
 void launch_key_perm(int n, int nk, const int* key, const int* koff, int* perm, cudaStream_t s);
+void launch_cf_flag(int n, const signed char* CF, int* flag, cudaStream_t s);
+void launch_cf_compose(int n, signed char* CF, const int* cidx, const signed char* CF2, cudaStream_t s);
+void launch_perm_row_len(int n, const int* perm, const int* rp, int* len, cudaStream_t s);
+void launch_perm_rows_fill(int n, const int* perm, const int* rp, const int* ci, const double* v, const int* prp,
+                           int* pci, double* pv, cudaStream_t s);
 void launch_interp_count(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF, int* cnt,
                          int* isc, cudaStream_t s);
 void launch_interp_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S,
@@ -367,7 +376,7 @@ void launch_pctl_ac_fill(int N, int nc, int G, const int* const* brp, const int*
                          const int* acrp, int* acci, double* acv, cudaStream_t s);
 void launch_sell_widths(int n, const int* rp, int* w, cudaStream_t s);
 void launch_sell_fill(int n, const int* rp, const int* ci, const double* v, const int* sptr, int* sci, double* sv,
-                      cudaStream_t s);
+                      cudaStream_t s, const int* selfmap = nullptr);
 void launch_colscale(long long nnz, const int* ci, const double* v, const double* d, double* out, cudaStream_t s);
 void launch_grad_vals(int n, const int* rp, const int* ci, const double* x, const double* lam, double* g,
                       cudaStream_t s);
@@ -383,7 +392,7 @@ void launch_phase(int phase, int fmtA, int tprRP, const LDesc<T>* d_descs, int n
 template <typename T>
 void launch_gs_first(const LDesc<T>* d, int nd, int maxrows, cudaStream_t s);
 template <typename T>
-void launch_gs_sweep(int tpr, const LDesc<T>* d, int nd, int maxrows, int t, int up, cudaStream_t s);
+void launch_gs_sweep(int fmt, const LDesc<T>* d, int nd, int maxrows, int t, int up, cudaStream_t s);
 template <typename T>
 void launch_gs_resid(int fmtA, const LDesc<T>* d, int nd, int maxrows, cudaStream_t s);
 // fused coarse-level V-cycle: one thread-block cluster of `cs` CTAs per subsystem

@@ -458,6 +458,51 @@ void launch_key_perm(int n, int nk, const int* key, const int* koff, int* perm, 
   MGD_LAUNCH_CHECK();
 }
 
+// aggressive coarsening: C indicator, and the final marks of the first pass's
+// C points from the second pass (C stays C, anything else becomes F)
+__global__ void k_cf_flag(int n, const signed char* CF, int* flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = CF[i] == 1 ? 1 : 0;
+}
+__global__ void k_cf_compose(int n, signed char* CF, const int* cidx, const signed char* CF2) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && CF[i] == 1) CF[i] = CF2[cidx[i]] == 1 ? 1 : -1;
+}
+void launch_cf_flag(int n, const signed char* CF, int* flag, cudaStream_t s) {
+  k_cf_flag<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, CF, flag);
+  MGD_LAUNCH_CHECK();
+}
+void launch_cf_compose(int n, signed char* CF, const int* cidx, const signed char* CF2, cudaStream_t s) {
+  k_cf_compose<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, CF, cidx, CF2);
+  MGD_LAUNCH_CHECK();
+}
+
+// rows of A in sweep order (row q of the copy is row perm[q]; each row's
+// entries keep their order, so a row sum over the copy is the same sum)
+__global__ void k_perm_row_len(int n, const int* perm, const int* rp, int* len) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) len[q] = rp[perm[q] + 1] - rp[perm[q]];
+}
+__global__ void k_perm_rows_fill(int n, const int* perm, const int* rp, const int* ci, const double* v,
+                                 const int* prp, int* pci, double* pv) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  int i = perm[q], b = rp[i], e = rp[i + 1], o = prp[q];
+  for (int p = b; p < e; ++p) {
+    pci[o + p - b] = ci[p];
+    pv[o + p - b] = v[p];
+  }
+}
+void launch_perm_row_len(int n, const int* perm, const int* rp, int* len, cudaStream_t s) {
+  k_perm_row_len<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, perm, rp, len);
+  MGD_LAUNCH_CHECK();
+}
+void launch_perm_rows_fill(int n, const int* perm, const int* rp, const int* ci, const double* v, const int* prp,
+                           int* pci, double* pv, cudaStream_t s) {
+  k_perm_rows_fill<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, perm, rp, ci, v, prp, pci, pv);
+  MGD_LAUNCH_CHECK();
+}
+
 __device__ __forceinline__ bool beats(const double* w, int i, int j) {
   return w[i] > w[j] || (w[i] == w[j] && i > j);
 }
@@ -1181,8 +1226,10 @@ void launch_sell_widths(int n, const int* rp, int* w, cudaStream_t s) {
 }
 
 // padding: column = the row itself, value 0
+// padding entries: value 0 at the row's own column (self[r] when given: the
+// original index of a row of a row-permuted copy)
 __global__ void k_sell_fill(int n, const int* rp, const int* ci, const double* v, const int* sptr, int* sci,
-                            double* sv) {
+                            double* sv, const int* selfmap) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int nsl = (n + 31) / 32;
   if (r >= nsl * 32) return;
@@ -1191,7 +1238,7 @@ __global__ void k_sell_fill(int n, const int* rp, const int* ci, const double* v
   int width = (sptr[s + 1] - base) >> 5;
   int len = r < n ? rp[r + 1] - rp[r] : 0;
   int b = r < n ? rp[r] : 0;
-  int self = r < n ? r : 0;
+  int self = r < n ? (selfmap ? selfmap[r] : r) : 0;
   for (int j = 0; j < width; ++j) {
     int idx = base + j * 32 + lane;
     if (j < len) {
@@ -1205,9 +1252,9 @@ __global__ void k_sell_fill(int n, const int* rp, const int* ci, const double* v
 }
 
 void launch_sell_fill(int n, const int* rp, const int* ci, const double* v, const int* sptr, int* sci, double* sv,
-                      cudaStream_t s) {
+                      cudaStream_t s, const int* selfmap) {
   int nsl = (n + 31) / 32;
-  k_sell_fill<<<cdiv(nsl * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, sptr, sci, sv);
+  k_sell_fill<<<cdiv(nsl * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, sptr, sci, sv, selfmap);
   MGD_LAUNCH_CHECK();
 }
 

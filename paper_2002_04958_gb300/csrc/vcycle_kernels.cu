@@ -170,12 +170,17 @@ __global__ void k_gs_first(const LDesc<T>* __restrict__ descs) {
   if (i < d->n) d->xt[i] = d->key[i] == 0 ? d->b[i] * d->gdinv[i] : T(0);
 }
 
-// step t of the down (up == 0: sweep t) or up (up == 1: sweep nk-1-t) smoothing
-template <typename T, int TPR>
+// step t of the down (up == 0: sweep t) or up (up == 1: sweep nk-1-t)
+// smoothing.  FMT_SELL reads the level's sweep-ordered SELL copy (coalesced
+// rows; position q of the sweep is row perm[q]); the CSR formats read A's
+// rows through perm with TPR threads per row.
+template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_gs_sweep(const LDesc<T>* __restrict__ descs, int t, int up) {
   MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
   MGD_SKIP_INACTIVE(d);
+  if (FMT == FMT_SELL && d->gsptr == nullptr) return;  // no sweep-ordered copy (never planned so)
+  constexpr int TPR = FmtTraits<FMT>::tpr;
   const int nk = d->nk;
   const int k = up ? nk - 1 - t : t;
   if (k < 0 || k >= nk) return;
@@ -184,14 +189,11 @@ __global__ void __launch_bounds__(kThreads) k_gs_sweep(const LDesc<T>* __restric
   int idx = g / TPR, lane = g % TPR;
   if (((g & ~31) / TPR) >= cnt) return;  // whole warp past the sweep's last point
   bool valid = idx < cnt;
-  int row = valid ? d->perm[seg + idx] : 0;
-  T s = T(0);
-  if (valid) {
-    int e = d->rp[row + 1];
-    for (int p = d->rp[row] + lane; p < e; p += TPR) s += d->v[p] * d->xt[d->ci[p]];
-  }
-#pragma unroll
-  for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  int q = seg + idx;
+  int row = valid ? d->perm[q] : 0;
+  XPlain<T> xf{d->xt};
+  T s = FMT == FMT_SELL ? row_dot<T, FMT>(q, lane, valid, nullptr, nullptr, nullptr, d->gsptr, d->gsci, d->gsv, xf)
+                        : row_dot<T, FMT>(row, lane, valid, d->rp, d->ci, d->v, nullptr, nullptr, nullptr, xf);
   if (valid && lane == 0) d->xt[row] = d->xt[row] + (d->b[row] - s) * d->gdinv[row];
 }
 
@@ -220,14 +222,15 @@ void launch_gs_first(const LDesc<T>* d, int nd, int maxrows, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_gs_sweep(int tpr, const LDesc<T>* d, int nd, int maxrows, int t, int up, cudaStream_t s) {
+void launch_gs_sweep(int fmt, const LDesc<T>* d, int nd, int maxrows, int t, int up, cudaStream_t s) {
   if (nd <= 0 || maxrows <= 0) return;
-  dim3 g(cdiv((long long)maxrows * tpr + 32, kThreads), nd);
-  switch (tpr) {
-    case 1: launch_k(k_gs_sweep<T, 1>, g, dim3(kThreads), 0, s, d, t, up); break;
-    case 2: launch_k(k_gs_sweep<T, 2>, g, dim3(kThreads), 0, s, d, t, up); break;
-    case 4: launch_k(k_gs_sweep<T, 4>, g, dim3(kThreads), 0, s, d, t, up); break;
-    default: launch_k(k_gs_sweep<T, 8>, g, dim3(kThreads), 0, s, d, t, up); break;
+  auto g = [&](int tpr) { return dim3(cdiv((long long)maxrows * tpr + 32, kThreads), nd); };
+  switch (fmt) {
+    case FMT_SELL: launch_k(k_gs_sweep<T, FMT_SELL>, g(1), dim3(kThreads), 0, s, d, t, up); break;
+    case FMT_CSR1: launch_k(k_gs_sweep<T, FMT_CSR1>, g(1), dim3(kThreads), 0, s, d, t, up); break;
+    case FMT_CSR2: launch_k(k_gs_sweep<T, FMT_CSR2>, g(2), dim3(kThreads), 0, s, d, t, up); break;
+    case FMT_CSR4: launch_k(k_gs_sweep<T, FMT_CSR4>, g(4), dim3(kThreads), 0, s, d, t, up); break;
+    default: launch_k(k_gs_sweep<T, FMT_CSR8>, g(8), dim3(kThreads), 0, s, d, t, up); break;
   }
   MGD_LAUNCH_CHECK();
 }

@@ -40,7 +40,7 @@ def test_opts_defaults_and_struct_layout(built):
     assert o.restart == 30 and o.nvcyc_group == 1 and o.precision == 0
     assert o.inner_mode == 0 and o.inner_maxit == 100
     # the ctypes mirror has the C struct's size: the library writes every field
-    assert C.sizeof(mgdamg.MgdOpts) == 136 and C.sizeof(mgdamg.MgdStats) == 112
+    assert C.sizeof(mgdamg.MgdOpts) == 144 and C.sizeof(mgdamg.MgdStats) == 112
     assert mgdamg.lib().mgd_kernel_launches() >= 0
     assert mgdamg.lib().mgd_opts_default(None) == 1
 
