@@ -125,7 +125,7 @@ def run_ours(args):
     opts = dict(precision=args.precision, batched=args.batched, use_graph=args.graph, autotune=1,
                 keep_transpose=int(args.adjoint), max_it=args.max_it, interp_type=args.interp, pdl=args.pdl,
                 inner_mode=args.inner, nvcyc_group=ncyc[0], nvcyc_E=ncyc[1], nvcyc_I=ncyc[2],
-                smoother=args.smoother)
+                smoother=args.smoother, agg_levels=args.agg)
     slv = mgdamg.Solver(**opts)
     adj = {}
 
@@ -223,7 +223,9 @@ def run_ours(args):
                               (f"{args.kind}_fp64_cf_gauss_seidel", args.kind,
                                dict(smoother=1, batched=1, use_graph=1, interp_type=args.interp)),
                               ("monolithic_amg_fp64_cf_gauss_seidel", "amg",
-                               dict(smoother=1, batched=1, use_graph=1, interp_type=args.interp))]:
+                               dict(smoother=1, batched=1, use_graph=1, interp_type=args.interp)),
+                              (f"{args.kind}_fp64_aggressive_level0", args.kind,
+                               dict(agg_levels=1, batched=1, use_graph=1, interp_type=args.interp))]:
             try:
                 v = mgdamg.Solver(autotune=1, **o)
                 v.setup(sysm.G, sysm.N, rp, ci, va, kind)
@@ -237,7 +239,8 @@ def run_ours(args):
                 err = (torch.linalg.vector_norm(xv - xg) / torch.linalg.vector_norm(xg)).item()
                 variants[name] = {"iters": itv, "relres": rrv, "status": rc, "time_s": round(tt, 5),
                                   "setup_ms": round(sv["setup_ms"], 3), "solve_ms": round(sv["solve_ms"], 3),
-                                  "vcycles": v.total_cycles(), "rel_diff_vs_fp64_x": err}
+                                  "vcycles": v.total_cycles(), "op_complexity": round(sv["op_complexity"], 4),
+                                  "rel_diff_vs_fp64_x": err}
                 v.close()
             except Exception as ex:  # report, do not hide
                 variants[name] = {"error": str(ex)}
@@ -267,6 +270,7 @@ def run_ours(args):
                    "inverses": ("option #3: V-cycles to 1e-2 for the Schur-type inverses" if args.inner else
                                 "option #2: V-cycles per group/E/I inverse " + args.nvcyc.replace(",", "/")),
                    "smoother": "Gauss-Seidel in C/F order (multicolour)" if args.smoother else "l1-Jacobi",
+                   "aggressive_levels": args.agg,
                    "step": "device setup + solve", "parallelism": f"replicas{ws}",
                    "launch": ("batched per-level launches" if args.batched else "per-operator launches") +
                              (", preconditioner replayed from a CUDA graph" if args.graph else ""),
@@ -312,7 +316,7 @@ def _oracle_opts(args):
     """The oracle's options for the preconditioner the GPU arm runs."""
     g, e, i = (int(t) for t in args.nvcyc.split(","))
     return dict(interp_type=args.interp, inner_mode=args.inner, nvcyc_group=g, nvcyc_E=e, nvcyc_I=i,
-                smoother=args.smoother)
+                smoother=args.smoother, agg_levels=args.agg)
 
 
 def _traffic_from_profiles():
@@ -430,6 +434,7 @@ def main():
     ap.add_argument("--pdl", type=int, default=1, help="programmatic dependent launch of solve kernels")
     ap.add_argument("--inner", type=int, default=0, help="1: option #3 inverses (V-cycles to 1e-2)")
     ap.add_argument("--smoother", type=int, default=0, help="0 l1-Jacobi, 1 Gauss-Seidel in C/F order")
+    ap.add_argument("--agg", type=int, default=0, help="levels coarsened aggressively (from the finest)")
     ap.add_argument("--nvcyc", default="1,1,1", help="V-cycles per group, E and I inverse")
     ap.add_argument("--interp", type=int, default=None,
                     help="0 classical modified, 1 extended+i (default: 1 for the default workload, else 0)")
