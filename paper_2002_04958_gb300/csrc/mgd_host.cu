@@ -900,7 +900,7 @@ static void build_tail(Arena& ar, VBatch<T>& vb, int Lt, bool keepT, cudaStream_
 // Autotune the first fused level: time whole V-cycles with no fusion and with
 // fusion from the first level whose largest row count is below each threshold.
 template <typename T>
-static void autotune_tail(Arena& ar, VBatch<T>& vb, bool keepT, cudaStream_t s) {
+static void autotune_tail(Arena& ar, VBatch<T>& vb, bool keepT, bool graph, cudaStream_t s) {
   Profiler none;
   std::vector<int> cand{vb.depth};
   for (int thr : {4096, 16384, 65536, 262144}) {
@@ -915,27 +915,65 @@ static void autotune_tail(Arena& ar, VBatch<T>& vb, bool keepT, cudaStream_t s) 
     }
     if (std::find(cand.begin(), cand.end(), Lt) == cand.end()) cand.push_back(Lt);
   }
+  std::vector<int> sizes{8};
+  if (vtail_cluster_fits<T>(16)) sizes.push_back(16);
   cudaEvent_t e0, e1;
   MGD_CUDA(cudaEventCreate(&e0));
   MGD_CUDA(cudaEventCreate(&e1));
-  int best_lt = vb.depth;
-  float best = 1e30f;
-  for (int Lt : cand) {
-    build_tail<T>(ar, vb, Lt, keepT, s);
+  // time five V-cycles the way the solve will run them: replayed from a
+  // captured graph when the context replays graphs (launch costs differ)
+  auto time_cycles = [&]() -> float {
+    float ms = 0;
+    if (graph) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      MGD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      try {
+        for (int r = 0; r < 5; ++r) run_vbatch<T>(vb, false, s, none);
+      } catch (...) {
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      MGD_CUDA(cudaStreamEndCapture(s, &g));
+      MGD_CUDA(cudaGraphInstantiate(&ge, g, 0));
+      cudaGraphDestroy(g);
+      MGD_CUDA(cudaGraphLaunch(ge, s));
+      MGD_CUDA(cudaEventRecord(e0, s));
+      MGD_CUDA(cudaGraphLaunch(ge, s));
+      MGD_CUDA(cudaGraphLaunch(ge, s));
+      MGD_CUDA(cudaEventRecord(e1, s));
+      MGD_CUDA(cudaEventSynchronize(e1));
+      cudaGraphExecDestroy(ge);
+      MGD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      return ms / 2;
+    }
     run_vbatch<T>(vb, false, s, none);
     MGD_CUDA(cudaEventRecord(e0, s));
     for (int r = 0; r < 5; ++r) run_vbatch<T>(vb, false, s, none);
     MGD_CUDA(cudaEventRecord(e1, s));
     MGD_CUDA(cudaEventSynchronize(e1));
-    float ms = 0;
     MGD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best * 0.97f) {  // prefer fewer fused levels unless clearly faster
-      best = ms;
-      best_lt = Lt;
+    return ms;
+  };
+  int best_lt = vb.depth, best_cs = 8;
+  float best = 1e30f;
+  for (int Lt : cand) {
+    for (int cs : sizes) {
+      if (Lt >= vb.depth && cs != 8) continue;
+      vb.tail_cs = cs;
+      build_tail<T>(ar, vb, Lt, keepT, s);
+      float ms = time_cycles();
+      if (ms < best * 0.97f) {  // prefer fewer fused levels unless clearly faster
+        best = ms;
+        best_lt = Lt;
+        best_cs = cs;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  vb.tail_cs = best_cs;
   build_tail<T>(ar, vb, best_lt, keepT, s);
 }
 
@@ -1716,13 +1754,14 @@ static void run_program(mgd_ctx* c, bool trans) {
 struct TuneResult {
   std::vector<int> fmtA, fmtR, fmtP, fmtGS;
   int tail_level;
+  int tail_cs = 8;
 };
 static std::mutex g_tune_mu;
 static std::map<std::vector<long long>, TuneResult> g_tune_cache;
 
 template <typename T>
-static std::vector<long long> tune_key(const VBatch<T>& vb, bool trans, int fuse_rows) {
-  std::vector<long long> k{(long long)sizeof(T), vb.depth, trans ? 1 : 0, fuse_rows};
+static std::vector<long long> tune_key(const VBatch<T>& vb, bool trans, int fuse_rows, bool graph) {
+  std::vector<long long> k{(long long)sizeof(T), vb.depth, trans ? 1 : 0, fuse_rows, graph ? 1 : 0};
   for (int l = 0; l < vb.depth; ++l) {
     long long nnz = 0;
     for (Hier* h : vb.hs)
@@ -1854,7 +1893,7 @@ static void build_batches(mgd_ctx* c) {
     build_plan<T>(c->ar, vb, false, c->s);
     if (c->o.keep_transpose) build_plan<T>(c->ar, vb, true, c->s);
     bool cached = false;
-    std::vector<long long> key = tune_key<T>(vb, false, c->o.fuse_rows);
+    std::vector<long long> key = tune_key<T>(vb, false, c->o.fuse_rows, c->o.use_graph != 0 && c->s != nullptr);
     if (c->o.autotune) {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       auto it = g_tune_cache.find(key);
@@ -1876,6 +1915,7 @@ static void build_batches(mgd_ctx* c) {
       }
     }
     if (cached) {
+      vb.tail_cs = g_tune_cache[key].tail_cs;
       build_tail<T>(c->ar, vb, g_tune_cache[key].tail_level, c->o.keep_transpose != 0, c->s);
       continue;
     }
@@ -1894,7 +1934,7 @@ static void build_batches(mgd_ctx* c) {
       }
       build_tail<T>(c->ar, vb, Lt, c->o.keep_transpose != 0, c->s);
     } else if (c->o.fuse_rows == 0 && c->o.autotune) {
-      autotune_tail<T>(c->ar, vb, c->o.keep_transpose != 0, c->s);
+      autotune_tail<T>(c->ar, vb, c->o.keep_transpose != 0, c->o.use_graph != 0 && c->s != nullptr, c->s);
     }
     if (c->o.autotune) {
       TuneResult r;
@@ -1905,6 +1945,7 @@ static void build_batches(mgd_ctx* c) {
         r.fmtGS.push_back(vb.plan[l].fmtGS);
       }
       r.tail_level = vb.tail_level;
+      r.tail_cs = vb.tail_cs;
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tune_cache[key] = r;
     }

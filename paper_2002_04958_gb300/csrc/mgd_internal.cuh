@@ -45,6 +45,12 @@ constexpr int kThreads = 256;
     asm volatile("griddepcontrol.wait;" ::: "memory");          \
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); \
   } while (0)
+// Split form for kernels that read setup-time data (operators, descriptors)
+// before the wait: they let their successor launch at entry, load what no
+// predecessor in the solve writes, then wait before the first read of a
+// vector (or of an inner-loop flag) that a predecessor wrote.
+#define MGD_PDL_TRIGGER() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
+#define MGD_PDL_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
 
 extern thread_local bool tl_pdl;
 
@@ -399,6 +405,8 @@ void launch_gs_resid(int fmtA, const LDesc<T>* d, int nd, int maxrows, cudaStrea
 template <typename T>
 void launch_vtail(const TailSub<T>* d_subs, int nsub, int cs, cudaStream_t s);
 constexpr int kTailThreads = 512;
+template <typename T>
+bool vtail_cluster_fits(int cs);
 
 template <typename T>
 void launch_produce(const ProduceDesc<T>* d, int nd, int N, const IOSlots* io, cudaStream_t s);

@@ -86,14 +86,17 @@ __global__ void __launch_bounds__(kThreads) k_spmv(int n, const int* __restrict_
                                                    const int* __restrict__ sci, const T* __restrict__ sv,
                                                    const T* __restrict__ b, const T* __restrict__ x,
                                                    T* __restrict__ y) {
-  MGD_PDL_ENTRY();
+  MGD_PDL_TRIGGER();  // the operator is setup-time data: load its rows before the wait
   constexpr int TPR = FmtTraits<FMT>::tpr;
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int row = (int)(g / TPR), lane = (int)(g % TPR);
   if (((g & ~31LL) / TPR) >= n) return;
   bool valid = row < n;
+  RowPre<T, 4> R;
+  row_load<T, FMT, 4>(R, row, lane, valid, rp, ci, v, sptr, sci, sv);
+  MGD_PDL_WAIT();
   XPlain<T> xf{x};
-  T s = row_dot<T, FMT>(row, lane, valid, rp, ci, v, sptr, sci, sv, xf);
+  T s = row_finish<T, FMT, 4>(R, valid, ci, v, sci, sv, xf);
   if (valid && lane == 0) y[row] = MODE ? b[row] - s : s;
 }
 

@@ -16,25 +16,34 @@
 namespace mgd {
 
 // ---------------------------------------------------------------- V-cycle phases
+// Each phase kernel loads its rows' operator entries (and the smoother
+// diagonal) before the dependency wait -- setup-time data -- and gathers the
+// vector its predecessor wrote only after it.
+constexpr int kPre = 4;  // entries per lane loaded before the wait
+
 // PRE: xt = D^-1 b (zero initial guess), r = b - A xt = b - (A D^-1) b, using
 // the column-scaled copy of A so that each nonzero costs one multiply-add
 template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_pre(const LDesc<T>* __restrict__ descs) {
-  MGD_PDL_ENTRY();
+  MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
-  MGD_SKIP_INACTIVE(d);
   constexpr int TPR = FmtTraits<FMT>::tpr;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   int row = g / TPR, lane = g % TPR;
   int n = d->n;
   if (((g & ~31) / TPR) >= n) return;  // the whole warp is past the last row (TPR divides 32)
   bool valid = row < n;
+  RowPre<T, kPre> R;
+  row_load<T, FMT, kPre>(R, row, lane, valid, d->rp, d->ci, d->vpre, d->sptr, d->sci, d->svpre);
+  T di = valid && lane == 0 ? d->dinv[row] : T(0);
+  MGD_PDL_WAIT();
+  MGD_SKIP_INACTIVE(d);
   const T* b = d->b;
   XPlain<T> xf{b};
-  T s = row_dot<T, FMT>(row, lane, valid, d->rp, d->ci, d->vpre, d->sptr, d->sci, d->svpre, xf);
+  T s = row_finish<T, FMT, kPre>(R, valid, d->ci, d->vpre, d->sci, d->svpre, xf);
   if (valid && lane == 0) {
     T bi = b[row];
-    d->xt[row] = d->dinv[row] * bi;
+    d->xt[row] = di * bi;
     d->r[row] = bi - s;
   }
 }
@@ -42,50 +51,60 @@ __global__ void __launch_bounds__(kThreads) k_pre(const LDesc<T>* __restrict__ d
 // POST: x = xt + D^-1 (b - A xt)
 template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_post(const LDesc<T>* __restrict__ descs) {
-  MGD_PDL_ENTRY();
+  MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
-  MGD_SKIP_INACTIVE(d);
   constexpr int TPR = FmtTraits<FMT>::tpr;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   int row = g / TPR, lane = g % TPR;
   int n = d->n;
   if (((g & ~31LL) / TPR) >= n) return;
   bool valid = row < n;
+  RowPre<T, kPre> R;
+  row_load<T, FMT, kPre>(R, row, lane, valid, d->rp, d->ci, d->v, d->sptr, d->sci, d->sv);
+  T di = valid && lane == 0 ? d->dinv[row] : T(0);
+  MGD_PDL_WAIT();
+  MGD_SKIP_INACTIVE(d);
   XPlain<T> xf{d->xt};
-  T s = row_dot<T, FMT>(row, lane, valid, d->rp, d->ci, d->v, d->sptr, d->sci, d->sv, xf);
-  if (valid && lane == 0) d->x[row] = d->xt[row] + d->dinv[row] * (d->b[row] - s);
+  T s = row_finish<T, FMT, kPre>(R, valid, d->ci, d->v, d->sci, d->sv, xf);
+  if (valid && lane == 0) d->x[row] = d->xt[row] + di * (d->b[row] - s);
 }
 
 // RESTRICT: bc = R r ; PROLONG: xt += P xc  (CSR, TPR threads per row)
 template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_restrict(const LDesc<T>* __restrict__ descs) {
-  MGD_PDL_ENTRY();
+  MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
-  MGD_SKIP_INACTIVE(d);
   constexpr int TPR = FmtTraits<FMT>::tpr;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   int row = g / TPR, lane = g % TPR;
   int n = d->nc;
   if (((g & ~31LL) / TPR) >= n) return;
   bool valid = row < n;
+  RowPre<T, kPre> R;
+  row_load<T, FMT, kPre>(R, row, lane, valid, d->rrp, d->rci, d->rv, nullptr, nullptr, nullptr);
+  MGD_PDL_WAIT();
+  MGD_SKIP_INACTIVE(d);
   XPlain<T> xf{d->r};
-  T s = row_dot<T, FMT>(row, lane, valid, d->rrp, d->rci, d->rv, nullptr, nullptr, nullptr, xf);
+  T s = row_finish<T, FMT, kPre>(R, valid, d->rci, d->rv, nullptr, nullptr, xf);
   if (valid && lane == 0) d->bc[row] = s;
 }
 
 template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_prolong(const LDesc<T>* __restrict__ descs) {
-  MGD_PDL_ENTRY();
+  MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
-  MGD_SKIP_INACTIVE(d);
   constexpr int TPR = FmtTraits<FMT>::tpr;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   int row = g / TPR, lane = g % TPR;
   int n = d->n;
   if (((g & ~31LL) / TPR) >= n) return;
   bool valid = row < n;
+  RowPre<T, kPre> R;
+  row_load<T, FMT, kPre>(R, row, lane, valid, d->prp, d->pci, d->pv, nullptr, nullptr, nullptr);
+  MGD_PDL_WAIT();
+  MGD_SKIP_INACTIVE(d);
   XPlain<T> xf{d->xc};
-  T s = row_dot<T, FMT>(row, lane, valid, d->prp, d->pci, d->pv, nullptr, nullptr, nullptr, xf);
+  T s = row_finish<T, FMT, kPre>(R, valid, d->pci, d->pv, nullptr, nullptr, xf);
   if (valid && lane == 0) d->xt[row] += s;
 }
 
@@ -200,17 +219,20 @@ __global__ void __launch_bounds__(kThreads) k_gs_sweep(const LDesc<T>* __restric
 // r = b - A xt after the down sweeps (the level's A layout)
 template <typename T, int FMT>
 __global__ void __launch_bounds__(kThreads) k_gs_resid(const LDesc<T>* __restrict__ descs) {
-  MGD_PDL_ENTRY();
+  MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
-  MGD_SKIP_INACTIVE(d);
   constexpr int TPR = FmtTraits<FMT>::tpr;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   int row = g / TPR, lane = g % TPR;
   int n = d->n;
   if (((g & ~31) / TPR) >= n) return;
   bool valid = row < n;
+  RowPre<T, kPre> R;
+  row_load<T, FMT, kPre>(R, row, lane, valid, d->rp, d->ci, d->v, d->sptr, d->sci, d->sv);
+  MGD_PDL_WAIT();
+  MGD_SKIP_INACTIVE(d);
   XPlain<T> xf{d->xt};
-  T s = row_dot<T, FMT>(row, lane, valid, d->rp, d->ci, d->v, d->sptr, d->sci, d->sv, xf);
+  T s = row_finish<T, FMT, kPre>(R, valid, d->ci, d->v, d->sci, d->sv, xf);
   if (valid && lane == 0) d->r[row] = d->b[row] - s;
 }
 
@@ -414,6 +436,34 @@ void launch_vtail(const TailSub<T>* d_subs, int nsub, int cs, cudaStream_t s) {
   MGD_CUDA(cudaLaunchKernelEx(&cfg, k_vtail<T>, d_subs));
   MGD_LAUNCH_CHECK();
 }
+
+// whether a cluster of cs CTAs of the fused kernel fits the device (sizes
+// above 8 are non-portable and are enabled on the kernel first)
+template <typename T>
+bool vtail_cluster_fits(int cs) {
+  if (cs > 8 && cudaFuncSetAttribute(k_vtail<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs, 1, 1);
+  cfg.blockDim = dim3(kTailThreads, 1, 1);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_vtail<T>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n > 0;
+}
+template bool vtail_cluster_fits<double>(int);
+template bool vtail_cluster_fits<float>(int);
 
 template void launch_vtail<double>(const TailSub<double>*, int, int, cudaStream_t);
 template void launch_vtail<float>(const TailSub<float>*, int, int, cudaStream_t);
