@@ -263,7 +263,8 @@ static Csr spgemm(Arena& a, const Csr& X, const Csr& Y, cudaStream_t s, Scratch*
   int* tc = sc.alloc<int>(total);
   double* tv = sc.alloc<double>(total);
   int* cnt = sc.alloc<int>(n);
-  launch_spgemm_expand(n, X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off, tc, tv, cnt, s);
+  int* work = sc.alloc<int>(n + 1);
+  launch_spgemm_expand(n, X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off, tc, tv, cnt, work, s);
   Csr C;
   C.n = n;
   C.m = Y.m;
@@ -454,7 +455,9 @@ static bool coarsen_pass(SetupCtx& sc, const Csr& A, int lid, Scratch* keep, Pas
     P.nnz = read_int(P.rp + n, s);
     P.ci = keep ? keep->alloc<int>(P.nnz) : ar.alloc<int>(P.nnz);
     P.v = keep ? keep->alloc<double>(P.nnz) : ar.alloc<double>(P.nnz);
-    launch_exti_fill(n, A.rp, A.ci, A.v, S, CF, cidx, off, list, P.rp, P.ci, P.v, s);
+    double* dg = tmp.alloc<double>(n);
+    launch_diag_extract(n, A.rp, A.ci, A.v, dg, s);
+    launch_exti_fill(n, A.rp, A.ci, A.v, S, CF, cidx, off, list, P.rp, P.ci, P.v, dg, s);
   } else {
     exclusive_scan(pcnt, P.rp, n, s);
     P.nnz = read_int(P.rp + n, s);
@@ -2043,8 +2046,6 @@ static void free_setup(mgd_ctx* c) {
   c->bd = BlockData();
   c->ready = false;
   c->napply = c->napplyT = 0;
-  if (c->hpin) cudaFreeHost(c->hpin);
-  c->hpin = nullptr;
 }
 
 static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) {
@@ -2326,10 +2327,20 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
   c->hbuf = c->ar.alloc<double>(128, true);
   c->partial = c->ar.alloc<double>((size_t)kDotBlocks * 32, true);
   c->ybuf = c->ar.alloc<double>(64, true);
-  MGD_CUDA(cudaMallocHost(&c->hpin, 256 * sizeof(double)));
-  // monolithic SpMV layout
+  if (!c->hpin) MGD_CUDA(cudaMallocHost(&c->hpin, 256 * sizeof(double)));  // kept across setups
+  // monolithic SpMV layout (cached by operator size, like the V-cycle plans)
   c->fmtMono = FMT_SELL;
+  const std::vector<long long> mkey{-1, n, c->A.nnz};
+  bool mono_cached = false;
   if (o.autotune) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(mkey);
+    if (it != g_tune_cache.end() && !it->second.fmtA.empty()) {
+      c->fmtMono = it->second.fmtA[0];
+      mono_cached = true;
+    }
+  }
+  if (o.autotune && !mono_cached) {
     cudaEvent_t e0, e1;
     MGD_CUDA(cudaEventCreate(&e0));
     MGD_CUDA(cudaEventCreate(&e1));
@@ -2350,6 +2361,11 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    TuneResult r;
+    r.fmtA.push_back(c->fmtMono);
+    r.tail_level = 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[mkey] = r;
   }
   capture_graph(c);
   MGD_CUDA(cudaStreamSynchronize(s));

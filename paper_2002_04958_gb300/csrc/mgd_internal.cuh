@@ -361,7 +361,7 @@ void launch_exti_list(int n, const int* rp, const int* ci, const uint8_t* S, con
                       const long long* off, int* list, int* len, cudaStream_t s);
 void launch_exti_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S, const signed char* CF,
                       const int* cidx, const long long* off, const int* list, const int* prp, int* pci, double* pv,
-                      cudaStream_t s);
+                      const double* dg, cudaStream_t s);
 void launch_transpose_count(int nnz, const int* ci, int* cnt, cudaStream_t s);
 void launch_transpose_fill(int n, const int* rp, const int* ci, const double* v, const int* trp, int* cursor,
                            int* tci, double* tv, cudaStream_t s);
@@ -369,7 +369,7 @@ void launch_sort_rows(int n, const int* rp, int* ci, double* v, cudaStream_t s);
 void launch_spgemm_ub(int n, const int* xrp, const int* xci, const int* yrp, int* ub, cudaStream_t s);
 void launch_spgemm_expand(int n, const int* xrp, const int* xci, const double* xv, const int* yrp,
                           const int* yci, const double* yv, const long long* off, int* tc, double* tv,
-                          int* cnt, cudaStream_t s);
+                          int* cnt, int* work, cudaStream_t s);  // work: n + 1 ints
 void launch_spgemm_compact(int n, const long long* off, const int* tc, const double* tv, const int* crp,
                            int* cci, double* cv, cudaStream_t s);
 void launch_l1_dinv(int n, const int* rp, const double* v, double* dinv, cudaStream_t s);

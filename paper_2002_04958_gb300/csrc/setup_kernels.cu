@@ -706,9 +706,27 @@ __global__ void k_exti_list(int n, const int* rp, const int* ci, const uint8_t* 
   len[i] = t;
 }
 
+// binary search of j in the sorted list L[0..len)
+__device__ __forceinline__ int find_sorted(const int* L, int len, int j) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (L[mid] < j) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < len && L[lo] == j ? lo : -1;
+}
+
+// Rows with at most kExtiLocal interpolatory points keep the set (sorted by
+// fine index, so membership is a binary search and the coarse columns come
+// out in order: coarse indices grow with fine indices) and the numerators in
+// per-thread local arrays; the arithmetic and its order are those of the
+// general path below.
+constexpr int kExtiLocal = 48;
+
 __global__ void k_exti_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S,
                             const signed char* CF, const int* cidx, const long long* off, const int* list,
-                            const int* prp, int* pci, double* pv) {
+                            const int* prp, int* pci, double* pv, const double* dg) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int base = prp[i], len = prp[i + 1] - base;
@@ -718,9 +736,68 @@ __global__ void k_exti_fill(int n, const int* rp, const int* ci, const double* v
     return;
   }
   if (len == 0) return;
+  const int* src = list + off[i];
+  if (len <= kExtiLocal) {
+    int L[kExtiLocal];
+    double num[kExtiLocal];
+    for (int s = 0; s < len; ++s) {  // insertion sort of the (distinct) fine indices
+      int c = src[s], q = s - 1;
+      while (q >= 0 && L[q] > c) {
+        L[q + 1] = L[q];
+        --q;
+      }
+      L[q + 1] = c;
+      num[s] = 0.0;
+    }
+    double diag = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      int j = ci[p];
+      if (j == i) {
+        diag = v[p];
+        continue;
+      }
+      int sj = find_sorted(L, len, j);
+      if (sj >= 0) num[sj] = v[p];
+    }
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      int k = ci[p];
+      if (k == i) continue;
+      double aik = v[p];
+      if (S[p] && CF[k] == 1) continue;
+      if (S[p] && CF[k] == -1) {
+        double akk = dg[k];
+        double denom = 0.0;
+        for (int q = rp[k]; q < rp[k + 1]; ++q) {
+          int l = ci[q];
+          if ((l == i || find_sorted(L, len, l) >= 0) && opp_sign(v[q], akk)) denom = __dadd_rn(denom, v[q]);
+        }
+        if (denom == 0.0) {
+          diag = __dadd_rn(diag, aik);
+        } else {
+          for (int q = rp[k]; q < rp[k + 1]; ++q) {
+            int l = ci[q];
+            if (!opp_sign(v[q], akk)) continue;
+            double prod = __dmul_rn(aik, v[q]);
+            if (l == i) {
+              diag = __dadd_rn(diag, __ddiv_rn(prod, denom));
+            } else {
+              int sl = find_sorted(L, len, l);
+              if (sl >= 0) num[sl] = __dadd_rn(num[sl], __ddiv_rn(prod, denom));
+            }
+          }
+        }
+      } else if (find_sorted(L, len, k) < 0) {
+        diag = __dadd_rn(diag, aik);
+      }
+    }
+    for (int s = 0; s < len; ++s) {
+      pci[base + s] = cidx[L[s]];
+      pv[base + s] = (diag != 0.0) ? __ddiv_rn(-num[s], diag) : 0.0;
+    }
+    return;
+  }
   int* L = pci + base;
   double* num = pv + base;
-  const int* src = list + off[i];
   for (int s = 0; s < len; ++s) {
     L[s] = src[s];
     num[s] = 0.0;
@@ -741,9 +818,7 @@ __global__ void k_exti_fill(int n, const int* rp, const int* ci, const double* v
     double aik = v[p];
     if (S[p] && CF[k] == 1) continue;
     if (S[p] && CF[k] == -1) {
-      double akk = 0.0;
-      for (int q = rp[k]; q < rp[k + 1]; ++q)
-        if (ci[q] == k) akk = v[q];
+      double akk = dg[k];
       double denom = 0.0;
       for (int q = rp[k]; q < rp[k + 1]; ++q) {
         int l = ci[q];
@@ -798,8 +873,8 @@ void launch_exti_list(int n, const int* rp, const int* ci, const uint8_t* S, con
 }
 void launch_exti_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S, const signed char* CF,
                       const int* cidx, const long long* off, const int* list, const int* prp, int* pci, double* pv,
-                      cudaStream_t s) {
-  k_exti_fill<<<cdiv(n, 128), 128, 0, s>>>(n, rp, ci, v, S, CF, cidx, off, list, prp, pci, pv);
+                      const double* dg, cudaStream_t s) {
+  k_exti_fill<<<cdiv(n, 128), 128, 0, s>>>(n, rp, ci, v, S, CF, cidx, off, list, prp, pci, pv, dg);
   MGD_LAUNCH_CHECK();
 }
 
@@ -881,15 +956,18 @@ void launch_spgemm_ub(int n, const int* xrp, const int* xci, const int* yrp, int
 // kWarpProducts products: products are expanded in order (k along row i of X,
 // then row k of Y), ranked by a stable counting sort on the column (ties keep
 // their expansion order), and each run of equal columns is summed left to
-// right by one lane.  Longer rows run the same three steps (expand, stable
-// insertion sort, run sums) on one lane in global memory.
+// right by one lane.  Rows with up to kLongProducts products are listed for
+// k_spgemm_long (a block per row); longer ones run the same three steps
+// (expand, stable insertion sort, run sums) on one lane in global memory.
 constexpr int kWarpProducts = 256;
 constexpr int kSpgWarps = 4;
+constexpr int kLongProducts = 8192;
+constexpr int kLongThreads = 1024;
 
 __global__ void __launch_bounds__(32 * kSpgWarps) k_spgemm_warp(int n, const int* xrp, const int* xci,
                                                                 const double* xv, const int* yrp, const int* yci,
                                                                 const double* yv, const long long* off, int* tc,
-                                                                double* tv, int* cnt) {
+                                                                double* tv, int* cnt, int* longrows, int* nlong) {
   __shared__ int s_col[kSpgWarps][kWarpProducts];
   __shared__ double s_val[kSpgWarps][kWarpProducts];
   __shared__ int s_scol[kSpgWarps][kWarpProducts];
@@ -899,6 +977,10 @@ __global__ void __launch_bounds__(32 * kSpgWarps) k_spgemm_warp(int n, const int
   if (i >= n) return;  // whole warp
   const long long b = off[i];
   const int L = (int)(off[i + 1] - b);
+  if (L > kWarpProducts && L <= kLongProducts) {
+    if (lane == 0) longrows[atomicAdd(nlong, 1)] = i;
+    return;
+  }
   if (L > kWarpProducts) {
     if (lane != 0) return;
     long long t = b;
@@ -988,10 +1070,115 @@ __global__ void __launch_bounds__(32 * kSpgWarps) k_spgemm_warp(int n, const int
   if (lane == 0) cnt[i] = base;
 }
 
+// One block per listed row (kWarpProducts < L <= kLongProducts): products
+// expanded in order into shared memory with the key (column << 32 | position),
+// a bitonic sort of the keys (the position makes it stable), then the runs of
+// equal columns summed left to right, as in the warp kernel.
+__global__ void __launch_bounds__(kLongThreads) k_spgemm_long(const int* xrp, const int* xci, const double* xv,
+                                                              const int* yrp, const int* yci, const double* yv,
+                                                              const long long* off, int* tc, double* tv, int* cnt,
+                                                              const int* longrows, const int* nlong) {
+  extern __shared__ unsigned long long sm_key[];  // kLongProducts keys, then kLongProducts values
+  double* sm_val = reinterpret_cast<double*>(sm_key + kLongProducts);
+  __shared__ int s_start[kLongThreads];
+  __shared__ int s_flag[kLongThreads];
+  const int tid = threadIdx.x;
+  const int rows = *nlong;
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int i = longrows[r];
+    const long long b = off[i];
+    const int L = (int)(off[i + 1] - b);
+    const int x0 = xrp[i], nx = xrp[i + 1] - x0;
+    // expansion offsets of the entries of row i of X (products of entry p start at s_start[p])
+    for (int c0 = 0; c0 < nx; c0 += kLongThreads) {  // rows of X are short; chunked for safety
+      __syncthreads();
+      if (tid == 0) {
+        int acc = c0 == 0 ? 0 : s_start[kLongThreads - 1] + (yrp[xci[x0 + c0 - 1] + 1] - yrp[xci[x0 + c0 - 1]]);
+        for (int p = c0; p < nx && p < c0 + kLongThreads; ++p) {
+          s_start[p - c0] = acc;
+          int k = xci[x0 + p];
+          acc += yrp[k + 1] - yrp[k];
+        }
+      }
+      __syncthreads();
+      for (int p = c0; p < nx && p < c0 + kLongThreads; ++p) {
+        int k = xci[x0 + p];
+        double x = xv[x0 + p];
+        int yb = yrp[k], len = yrp[k + 1] - yb, t0 = s_start[p - c0];
+        for (int q = tid; q < len; q += kLongThreads) {
+          int t = t0 + q;
+          sm_key[t] = ((unsigned long long)(unsigned)yci[yb + q] << 32) | (unsigned)t;
+          sm_val[t] = __dmul_rn(x, yv[yb + q]);
+        }
+      }
+    }
+    int P2 = 1;
+    while (P2 < L) P2 <<= 1;
+    for (int t = L + tid; t < P2; t += kLongThreads) sm_key[t] = ~0ULL;
+    __syncthreads();
+    for (int k = 2; k <= P2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = tid; t < P2; t += kLongThreads) {
+          int u = t ^ j;
+          if (u > t) {
+            unsigned long long a = sm_key[t], c = sm_key[u];
+            bool up = (t & k) == 0;
+            if ((a > c) == up) {
+              sm_key[t] = c;
+              sm_key[u] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    // run heads, their ranks (chunked block scan), and the run sums
+    int base = 0;
+    for (int c0 = 0; c0 < L; c0 += kLongThreads) {
+      int t = c0 + tid;
+      int head = 0;
+      if (t < L) head = t == 0 || (sm_key[t] >> 32) != (sm_key[t - 1] >> 32);
+      s_flag[tid] = head;
+      __syncthreads();
+      for (int o = 1; o < kLongThreads; o <<= 1) {  // inclusive scan
+        int v = tid >= o ? s_flag[tid - o] : 0;
+        __syncthreads();
+        s_flag[tid] += v;
+        __syncthreads();
+      }
+      if (head) {
+        int u = base + s_flag[tid] - 1;
+        unsigned col = (unsigned)(sm_key[t] >> 32);
+        double acc = sm_val[(unsigned)sm_key[t]];
+        int q = t + 1;
+        while (q < L && (unsigned)(sm_key[q] >> 32) == col) {
+          acc = __dadd_rn(acc, sm_val[(unsigned)sm_key[q]]);
+          ++q;
+        }
+        tc[b + u] = (int)col;
+        tv[b + u] = acc;
+      }
+      base += s_flag[kLongThreads - 1];
+      __syncthreads();
+    }
+    if (tid == 0) cnt[i] = base;
+    __syncthreads();
+  }
+}
+
 void launch_spgemm_expand(int n, const int* xrp, const int* xci, const double* xv, const int* yrp,
                           const int* yci, const double* yv, const long long* off, int* tc, double* tv, int* cnt,
-                          cudaStream_t s) {
-  k_spgemm_warp<<<cdiv(n, kSpgWarps), 32 * kSpgWarps, 0, s>>>(n, xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt);
+                          int* work, cudaStream_t s) {
+  // work: n + 1 ints (list of long rows, then their count)
+  int* nlong = work + n;
+  MGD_CUDA(cudaMemsetAsync(nlong, 0, sizeof(int), s));
+  k_spgemm_warp<<<cdiv(n, kSpgWarps), 32 * kSpgWarps, 0, s>>>(n, xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt, work,
+                                                               nlong);
+  MGD_LAUNCH_CHECK();
+  static const size_t smem = (size_t)kLongProducts * (sizeof(unsigned long long) + sizeof(double));
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_spgemm_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  MGD_CUDA(attr);
+  k_spgemm_long<<<152, kLongThreads, smem, s>>>(xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt, work, nlong);
   MGD_LAUNCH_CHECK();
 }
 
