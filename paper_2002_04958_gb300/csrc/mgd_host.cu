@@ -457,7 +457,9 @@ static bool coarsen_pass(SetupCtx& sc, const Csr& A, int lid, Scratch* keep, Pas
     P.v = keep ? keep->alloc<double>(P.nnz) : ar.alloc<double>(P.nnz);
     double* dg = tmp.alloc<double>(n);
     launch_diag_extract(n, A.rp, A.ci, A.v, dg, s);
-    launch_exti_fill(n, A.rp, A.ci, A.v, S, CF, cidx, off, list, P.rp, P.ci, P.v, dg, s);
+    int* wi = tmp.alloc<int>((size_t)A.nnz + P.nnz);
+    double* wd = tmp.alloc<double>((size_t)A.nnz + n);
+    launch_exti_fill(n, A.nnz, A.rp, A.ci, A.v, S, CF, cidx, off, list, len, P.rp, P.nnz, P.ci, P.v, dg, wi, wd, s);
   } else {
     exclusive_scan(pcnt, P.rp, n, s);
     P.nnz = read_int(P.rp + n, s);

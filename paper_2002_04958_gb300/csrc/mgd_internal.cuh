@@ -359,9 +359,10 @@ void launch_exti_ub(int n, const int* rp, const int* ci, const uint8_t* S, const
                     int* ub, cudaStream_t s);
 void launch_exti_list(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF,
                       const long long* off, int* list, int* len, cudaStream_t s);
-void launch_exti_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S, const signed char* CF,
-                      const int* cidx, const long long* off, const int* list, const int* prp, int* pci, double* pv,
-                      const double* dg, cudaStream_t s);
+void launch_exti_fill(int n, int nnz, const int* rp, const int* ci, const double* v, const uint8_t* S,
+                      const signed char* CF, const int* cidx, const long long* off, const int* list, const int* len,
+                      const int* prp, int nnzp, int* pci, double* pv, const double* dg, int* work_i,
+                      double* work_d, cudaStream_t s);
 void launch_transpose_count(int nnz, const int* ci, int* cnt, cudaStream_t s);
 void launch_transpose_fill(int n, const int* rp, const int* ci, const double* v, const int* trp, int* cursor,
                            int* tci, double* tv, cudaStream_t s);

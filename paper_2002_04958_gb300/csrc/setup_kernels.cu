@@ -661,11 +661,6 @@ void launch_interp_fill(int n, const int* rp, const int* ci, const double* v, co
 // in construction order (strong C neighbours of i in row order, then for each
 // strong F neighbour k in row order its strong C neighbours in row order), and
 // the weights with the same operation order as the definition states.
-__device__ __forceinline__ int find_in(const int* L, int len, int j) {
-  for (int s = 0; s < len; ++s)
-    if (L[s] == j) return s;
-  return -1;
-}
 
 __global__ void k_exti_ub(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF,
                           const int* scount, int* ub) {
@@ -681,6 +676,33 @@ __global__ void k_exti_ub(int n, const int* rp, const int* ci, const uint8_t* S,
   ub[i] = c;
 }
 
+// binary search of j in the sorted list L[0..len)
+__device__ __forceinline__ int find_sorted(const int* L, int len, int j) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (L[mid] < j) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < len && L[lo] == j ? lo : -1;
+}
+
+// insert j into the sorted list L[0..t) unless present; returns the new length
+__device__ __forceinline__ int insert_sorted(int* L, int t, int j) {
+  int lo = 0, hi = t;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (L[mid] < j) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo < t && L[lo] == j) return t;
+  for (int q = t; q > lo; --q) L[q] = L[q - 1];
+  L[lo] = j;
+  return t + 1;
+}
+
+// interpolatory set of each F row, kept sorted by fine index (the coarse
+// indices then come out in order: they grow with the fine ones)
 __global__ void k_exti_list(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF,
                             const long long* off, int* list, int* len) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -693,172 +715,117 @@ __global__ void k_exti_list(int n, const int* rp, const int* ci, const uint8_t* 
   int t = 0;
   for (int p = rp[i]; p < rp[i + 1]; ++p) {
     int j = ci[p];
-    if (S[p] && CF[j] == 1 && find_in(L, t, j) < 0) L[t++] = j;
+    if (S[p] && CF[j] == 1) t = insert_sorted(L, t, j);
   }
   for (int p = rp[i]; p < rp[i + 1]; ++p) {
     int k = ci[p];
     if (!(S[p] && CF[k] == -1)) continue;
     for (int q = rp[k]; q < rp[k + 1]; ++q) {
       int m = ci[q];
-      if (S[q] && CF[m] == 1 && find_in(L, t, m) < 0) L[t++] = m;
+      if (S[q] && CF[m] == 1) t = insert_sorted(L, t, m);
     }
   }
   len[i] = t;
 }
 
-// binary search of j in the sorted list L[0..len)
-__device__ __forceinline__ int find_sorted(const int* L, int len, int j) {
-  int lo = 0, hi = len;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (L[mid] < j) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo < len && L[lo] == j ? lo : -1;
+// Extended+i values in three passes that keep every sum's operand order of
+// the row-sequential definition (and so its bits).  Rows of A have sorted
+// columns, so a_kl is found by binary search in row k.
+__device__ __forceinline__ int find_col(const int* rp, const int* ci, int k, int l) {
+  int b = rp[k];
+  int q = find_sorted(ci + b, rp[k + 1] - b, l);
+  return q < 0 ? -1 : b + q;
 }
 
-// Rows with at most kExtiLocal interpolatory points keep the set (sorted by
-// fine index, so membership is a binary search and the coarse columns come
-// out in order: coarse indices grow with fine indices) and the numerators in
-// per-thread local arrays; the arithmetic and its order are those of the
-// general path below.
-constexpr int kExtiLocal = 48;
-
-__global__ void k_exti_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S,
-                            const signed char* CF, const int* cidx, const long long* off, const int* list,
-                            const int* prp, int* pci, double* pv, const double* dg) {
+// row index of every entry
+__global__ void k_row_of(int n, const int* rp, int* rowof) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int base = prp[i], len = prp[i + 1] - base;
-  if (CF[i] == 1) {
-    pci[base] = cidx[i];
-    pv[base] = 1.0;
-    return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) rowof[p] = i;
+}
+
+// pass 1, one thread per entry (i, k) of A with i an F point and k a strong F
+// neighbour: the distribution sum over row k of the opposite-sign entries at i
+// or at an interpolatory point of i, in row-k order
+__global__ void k_exti_denom(int nnz, const int* rowof, const int* rp, const int* ci, const double* v,
+                             const uint8_t* S, const signed char* CF, const long long* off, const int* list,
+                             const int* len, const double* dg, double* den) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nnz) return;
+  int i = rowof[p], k = ci[p];
+  if (CF[i] == 1 || k == i || !(S[p] && CF[k] == -1)) return;
+  const int* L = list + off[i];
+  int nl = len[i];
+  double akk = dg[k];
+  double denom = 0.0;
+  for (int q = rp[k]; q < rp[k + 1]; ++q) {
+    int l = ci[q];
+    if ((l == i || find_sorted(L, nl, l) >= 0) && opp_sign(v[q], akk)) denom = __dadd_rn(denom, v[q]);
   }
-  if (len == 0) return;
-  const int* src = list + off[i];
-  if (len <= kExtiLocal) {
-    int L[kExtiLocal];
-    double num[kExtiLocal];
-    for (int s = 0; s < len; ++s) {  // insertion sort of the (distinct) fine indices
-      int c = src[s], q = s - 1;
-      while (q >= 0 && L[q] > c) {
-        L[q + 1] = L[q];
-        --q;
-      }
-      L[q + 1] = c;
-      num[s] = 0.0;
-    }
-    double diag = 0.0;
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-      int j = ci[p];
-      if (j == i) {
-        diag = v[p];
-        continue;
-      }
-      int sj = find_sorted(L, len, j);
-      if (sj >= 0) num[sj] = v[p];
-    }
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-      int k = ci[p];
-      if (k == i) continue;
-      double aik = v[p];
-      if (S[p] && CF[k] == 1) continue;
-      if (S[p] && CF[k] == -1) {
-        double akk = dg[k];
-        double denom = 0.0;
-        for (int q = rp[k]; q < rp[k + 1]; ++q) {
-          int l = ci[q];
-          if ((l == i || find_sorted(L, len, l) >= 0) && opp_sign(v[q], akk)) denom = __dadd_rn(denom, v[q]);
-        }
-        if (denom == 0.0) {
-          diag = __dadd_rn(diag, aik);
-        } else {
-          for (int q = rp[k]; q < rp[k + 1]; ++q) {
-            int l = ci[q];
-            if (!opp_sign(v[q], akk)) continue;
-            double prod = __dmul_rn(aik, v[q]);
-            if (l == i) {
-              diag = __dadd_rn(diag, __ddiv_rn(prod, denom));
-            } else {
-              int sl = find_sorted(L, len, l);
-              if (sl >= 0) num[sl] = __dadd_rn(num[sl], __ddiv_rn(prod, denom));
-            }
-          }
-        }
-      } else if (find_sorted(L, len, k) < 0) {
-        diag = __dadd_rn(diag, aik);
-      }
-    }
-    for (int s = 0; s < len; ++s) {
-      pci[base + s] = cidx[L[s]];
-      pv[base + s] = (diag != 0.0) ? __ddiv_rn(-num[s], diag) : 0.0;
-    }
-    return;
-  }
-  int* L = pci + base;
-  double* num = pv + base;
-  for (int s = 0; s < len; ++s) {
-    L[s] = src[s];
-    num[s] = 0.0;
-  }
+  den[p] = denom;
+}
+
+// pass 2, one thread per F row: the lumped diagonal, in row order
+__global__ void k_exti_diag(int n, const int* rp, const int* ci, const double* v, const uint8_t* S,
+                            const signed char* CF, const long long* off, const int* list, const int* len,
+                            const double* dg, const double* den, double* diagv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || CF[i] == 1 || len[i] == 0) return;
+  const int* L = list + off[i];
+  int nl = len[i];
   double diag = 0.0;
-  for (int p = rp[i]; p < rp[i + 1]; ++p) {
-    int j = ci[p];
-    if (j == i) {
-      diag = v[p];
-      continue;
-    }
-    int sj = find_in(L, len, j);
-    if (sj >= 0) num[sj] = v[p];
-  }
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (ci[p] == i) diag = v[p];
   for (int p = rp[i]; p < rp[i + 1]; ++p) {
     int k = ci[p];
     if (k == i) continue;
     double aik = v[p];
     if (S[p] && CF[k] == 1) continue;
     if (S[p] && CF[k] == -1) {
-      double akk = dg[k];
-      double denom = 0.0;
-      for (int q = rp[k]; q < rp[k + 1]; ++q) {
-        int l = ci[q];
-        if ((l == i || find_in(L, len, l) >= 0) && opp_sign(v[q], akk)) denom = __dadd_rn(denom, v[q]);
-      }
+      double denom = den[p];
       if (denom == 0.0) {
         diag = __dadd_rn(diag, aik);
       } else {
-        for (int q = rp[k]; q < rp[k + 1]; ++q) {
-          int l = ci[q];
-          if (!opp_sign(v[q], akk)) continue;
-          double prod = __dmul_rn(aik, v[q]);
-          if (l == i) {
-            diag = __dadd_rn(diag, __ddiv_rn(prod, denom));
-          } else {
-            int sl = find_in(L, len, l);
-            if (sl >= 0) num[sl] = __dadd_rn(num[sl], __ddiv_rn(prod, denom));
-          }
-        }
+        int q = find_col(rp, ci, k, i);
+        if (q >= 0 && opp_sign(v[q], dg[k])) diag = __dadd_rn(diag, __ddiv_rn(__dmul_rn(aik, v[q]), denom));
       }
-    } else if (find_in(L, len, k) < 0) {
+    } else if (find_sorted(L, nl, k) < 0) {
       diag = __dadd_rn(diag, aik);
     }
   }
-  for (int s = 0; s < len; ++s) {
-    num[s] = (diag != 0.0) ? __ddiv_rn(-num[s], diag) : 0.0;
-    L[s] = cidx[L[s]];
+  diagv[i] = diag;
+}
+
+// pass 3, one thread per entry of P: the numerator of interpolatory point l of
+// row i (its direct coefficient, then the distributed strong-F terms in row
+// order), the weight -num / diag, and the coarse column
+__global__ void k_exti_value(int nnzp, const int* prowof, const int* prp, const int* rp, const int* ci,
+                             const double* v, const uint8_t* S, const signed char* CF, const int* cidx,
+                             const long long* off, const int* list, const double* dg, const double* den,
+                             const double* diagv, int* pci, double* pv) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnzp) return;
+  int i = prowof[e];
+  if (CF[i] == 1) {
+    pci[e] = cidx[i];
+    pv[e] = 1.0;
+    return;
   }
-  for (int a = 1; a < len; ++a) {  // sort by coarse index
-    int cc = L[a];
-    double vv = num[a];
-    int q = a - 1;
-    while (q >= 0 && L[q] > cc) {
-      L[q + 1] = L[q];
-      num[q + 1] = num[q];
-      --q;
-    }
-    L[q + 1] = cc;
-    num[q + 1] = vv;
+  int l = list[off[i] + (e - prp[i])];
+  double num = 0.0;
+  int pd = find_col(rp, ci, i, l);
+  if (pd >= 0) num = v[pd];
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int k = ci[p];
+    if (k == i || !(S[p] && CF[k] == -1)) continue;
+    double denom = den[p];
+    if (denom == 0.0) continue;
+    int q = find_col(rp, ci, k, l);
+    if (q >= 0 && opp_sign(v[q], dg[k])) num = __dadd_rn(num, __ddiv_rn(__dmul_rn(v[p], v[q]), denom));
   }
+  double diag = diagv[i];
+  pci[e] = cidx[l];
+  pv[e] = (diag != 0.0) ? __ddiv_rn(-num, diag) : 0.0;
 }
 
 void launch_exti_ub(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF, const int* scount,
@@ -871,11 +838,30 @@ void launch_exti_list(int n, const int* rp, const int* ci, const uint8_t* S, con
   k_exti_list<<<cdiv(n, 128), 128, 0, s>>>(n, rp, ci, S, CF, off, list, len);
   MGD_LAUNCH_CHECK();
 }
-void launch_exti_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S, const signed char* CF,
-                      const int* cidx, const long long* off, const int* list, const int* prp, int* pci, double* pv,
-                      const double* dg, cudaStream_t s) {
-  k_exti_fill<<<cdiv(n, 128), 128, 0, s>>>(n, rp, ci, v, S, CF, cidx, off, list, prp, pci, pv, dg);
+void launch_exti_fill(int n, int nnz, const int* rp, const int* ci, const double* v, const uint8_t* S,
+                      const signed char* CF, const int* cidx, const long long* off, const int* list, const int* len,
+                      const int* prp, int nnzp, int* pci, double* pv, const double* dg, int* work_i,
+                      double* work_d, cudaStream_t s) {
+  // work_i: nnz + nnzp ints (row of each entry of A, of P); work_d: nnz + n doubles (denominators, diagonals)
+  int* rowof = work_i;
+  int* prowof = work_i + nnz;
+  double* den = work_d;
+  double* diagv = work_d + nnz;
+  k_row_of<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, rowof);
   MGD_LAUNCH_CHECK();
+  k_row_of<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, prp, prowof);
+  MGD_LAUNCH_CHECK();
+  if (nnz > 0) {
+    k_exti_denom<<<cdiv(nnz, kThreads), kThreads, 0, s>>>(nnz, rowof, rp, ci, v, S, CF, off, list, len, dg, den);
+    MGD_LAUNCH_CHECK();
+  }
+  k_exti_diag<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, S, CF, off, list, len, dg, den, diagv);
+  MGD_LAUNCH_CHECK();
+  if (nnzp > 0) {
+    k_exti_value<<<cdiv(nnzp, kThreads), kThreads, 0, s>>>(nnzp, prowof, prp, rp, ci, v, S, CF, cidx, off, list,
+                                                           dg, den, diagv, pci, pv);
+    MGD_LAUNCH_CHECK();
+  }
 }
 
 // ------------------------------------------------------------------ transpose
