@@ -63,13 +63,51 @@ static void scan_rec(const I* in, I* out, int n, cudaStream_t s, Scratch& sc) {
   MGD_LAUNCH_CHECK();
 }
 
+// one block: exclusive sums of in[0..n_in) followed by zeros, n outputs,
+// in chunks of kOneThreads * 4 with a running carry
+constexpr int kOneThreads = 1024;
+constexpr int kOneMax = 8 * kOneThreads;  // sizes served by the single-block scan
+template <typename IN, typename I>
+__global__ void __launch_bounds__(kOneThreads) k_scan_one(const IN* in, int n_in, I* out, int n) {
+  __shared__ I sh[kOneThreads];
+  I carry = 0;
+  for (int base = 0; base < n; base += kOneThreads * 4) {
+    I v[4];
+    I tsum = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      int i = base + threadIdx.x * 4 + k;
+      v[k] = i < n_in ? (I)in[i] : (I)0;
+      tsum += v[k];
+    }
+    sh[threadIdx.x] = tsum;
+    __syncthreads();
+    for (int off = 1; off < kOneThreads; off <<= 1) {
+      I t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    I run = carry + sh[threadIdx.x] - tsum;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      int i = base + threadIdx.x * 4 + k;
+      if (i < n) out[i] = run;
+      run += v[k];
+    }
+    carry += sh[kOneThreads - 1];
+    __syncthreads();
+  }
+}
+
 // out[0..n]: exclusive prefix sums of in[0..n), out[n] = total
 void exclusive_scan(const int* in, int* out, int n, cudaStream_t s) {
-  Scratch sc(s);
-  if (n == 0) {
-    MGD_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
+  if (n + 1 <= kOneMax) {
+    k_scan_one<int, int><<<1, kOneThreads, 0, s>>>(in, n, out, n + 1);
+    MGD_LAUNCH_CHECK();
     return;
   }
+  Scratch sc(s);
   int* ext = sc.alloc<int>(n + 1);
   MGD_CUDA(cudaMemcpyAsync(ext, in, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
   MGD_CUDA(cudaMemsetAsync(ext + n, 0, sizeof(int), s));
@@ -83,6 +121,11 @@ __global__ void k_widen(const int* in, long long* out, int n) {
 }
 
 void launch_offsets64(const int* cnt, long long* off, int n, cudaStream_t s) {
+  if (n + 1 <= kOneMax) {
+    k_scan_one<int, long long><<<1, kOneThreads, 0, s>>>(cnt, n, off, n + 1);
+    MGD_LAUNCH_CHECK();
+    return;
+  }
   Scratch sc(s);
   long long* ext = sc.alloc<long long>(n + 1);
   k_widen<<<cdiv(n + 1, kThreads), kThreads, 0, s>>>(cnt, ext, n);
@@ -1013,16 +1056,33 @@ __global__ void __launch_bounds__(32 * kSpgWarps) k_spgemm_warp(int n, const int
   double* val = s_val[warp];
   int* scol = s_scol[warp];
   double* sval = s_sval[warp];
+  // expansion: lane t takes entry t of a 32-entry chunk of row i of X; a warp
+  // prefix sum of the Y row lengths places each lane's products, so the
+  // expansion order (k along row i, then row k of Y) is unchanged
   int p0 = 0;
-  for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
-    int k = xci[p];
-    double x = xv[p];
-    int yb = yrp[k], len = yrp[k + 1] - yb;
-    for (int q = lane; q < len; q += 32) {
-      col[p0 + q] = yci[yb + q];
-      val[p0 + q] = __dmul_rn(x, yv[yb + q]);
+  const int xe = xrp[i + 1];
+  for (int c = xrp[i]; c < xe; c += 32) {
+    int p = c + lane;
+    int yb = 0, len = 0;
+    double x = 0.0;
+    if (p < xe) {
+      int k = xci[p];
+      x = xv[p];
+      yb = yrp[k];
+      len = yrp[k + 1] - yb;
     }
-    p0 += len;
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    int at = p0 + incl - len;
+    for (int q = 0; q < len; ++q) {
+      col[at + q] = yci[yb + q];
+      val[at + q] = __dmul_rn(x, yv[yb + q]);
+    }
+    p0 += __shfl_sync(0xffffffffu, incl, 31);
   }
   __syncwarp();
   for (int p = lane; p < L; p += 32) {  // stable rank by column
@@ -1168,21 +1228,25 @@ void launch_spgemm_expand(int n, const int* xrp, const int* xci, const double* x
   MGD_LAUNCH_CHECK();
 }
 
+// copy each row's result to its final place: 8 lanes per row, consecutive
+// lanes on consecutive entries
+constexpr int kCompactLanes = 8;
 __global__ void k_spgemm_compact(int n, const long long* off, const int* tc, const double* tv, const int* crp,
                                  int* cci, double* cv) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i = (int)(g / kCompactLanes), lane = (int)(g % kCompactLanes);
   if (i >= n) return;
   long long b = off[i];
-  int len = crp[i + 1] - crp[i];
-  for (int k = 0; k < len; ++k) {
-    cci[crp[i] + k] = tc[b + k];
-    cv[crp[i] + k] = tv[b + k];
+  int o = crp[i], len = crp[i + 1] - o;
+  for (int k = lane; k < len; k += kCompactLanes) {
+    cci[o + k] = tc[b + k];
+    cv[o + k] = tv[b + k];
   }
 }
 
 void launch_spgemm_compact(int n, const long long* off, const int* tc, const double* tv, const int* crp, int* cci,
                            double* cv, cudaStream_t s) {
-  k_spgemm_compact<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, off, tc, tv, crp, cci, cv);
+  k_spgemm_compact<<<cdiv((long long)n * kCompactLanes, kThreads), kThreads, 0, s>>>(n, off, tc, tv, crp, cci, cv);
   MGD_LAUNCH_CHECK();
 }
 
