@@ -101,6 +101,9 @@ typedef struct mgd_opts {
                              PMIS pass (weight stream 1100 + level) on A1 = P1^T A P1, which is not kept as a
                              level, chooses the final C points among the first pass's; P = P1 P2 (two-stage
                              interpolation, each stage of interp_type).  0: none (default); at most max_levels */
+  int arnoldi_resident;   /* 1 (default): each FGMRES orthogonalisation runs as one cooperative grid that keeps the
+                             new Krylov vector in shared memory (one block per SM; used when n fits, else 0);
+                             0: one streaming kernel per basis vector.  Same modified Gram-Schmidt either way */
 } mgd_opts;
 
 /* Fill *o with the defaults listed above.  Returns MGD_EINVAL if o is NULL. */

@@ -1142,6 +1142,7 @@ struct mgd_ctx {
   cudaStream_t s_body = nullptr;     // stream that records conditional-node bodies
   long long graph_kernels = 0;
   long long napply = 0, napplyT = 0; // preconditioner applies since setup (forward, transposed)
+  int arn_nb = 0;                    // blocks of the cooperative Arnoldi grid (0: streaming kernels)
   mgd_stats st;
   int n_jacobi = 0;
   mgd::PhaseClock phases;
@@ -2330,6 +2331,7 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
   c->partial = c->ar.alloc<double>((size_t)kDotBlocks * 32, true);
   c->ybuf = c->ar.alloc<double>(64, true);
   if (!c->hpin) MGD_CUDA(cudaMallocHost(&c->hpin, 256 * sizeof(double)));  // kept across setups
+  c->arn_nb = o.arnoldi_resident ? arnoldi_coop_blocks(n) : 0;
   // monolithic SpMV layout (cached by operator size, like the V-cycle plans)
   c->fmtMono = FMT_SELL;
   const std::vector<long long> mkey{-1, n, c->A.nnz};
@@ -2486,9 +2488,14 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
       spmv(zj, c->w);
       int nv = j + 1;
       int aid = c->prof.begin(s, 3);
-      // modified Gram-Schmidt, one fused pass per basis vector: h in hbuf[0..j], ||w||^2 in hbuf[64]
-      launch_mgs(n, c->V, n, nv, c->w, c->hbuf, c->hbuf + 64, c->partial, c->partial + kDotBlocks, s);
-      launch_scale_by_norm(n, c->w, c->hbuf + 64, c->V + (size_t)(j + 1) * n, s);
+      // modified Gram-Schmidt: h in hbuf[0..j], ||w||^2 in hbuf[64], v_{j+1} = w / ||w||
+      if (c->arn_nb > 0) {
+        launch_arnoldi_coop(c->arn_nb, n, c->V, n, nv, c->w, c->hbuf, c->hbuf + 64, c->partial,
+                            c->V + (size_t)(j + 1) * n, s);
+      } else {
+        launch_mgs(n, c->V, n, nv, c->w, c->hbuf, c->hbuf + 64, c->partial, c->partial + kDotBlocks, s);
+        launch_scale_by_norm(n, c->w, c->hbuf + 64, c->V + (size_t)(j + 1) * n, s);
+      }
       c->prof.end(aid, 3, 8.0 * n * (4.0 * nv + 2.0 + 2.0), s);
       MGD_CUDA(cudaMemcpyAsync(hp, c->hbuf, 65 * sizeof(double), cudaMemcpyDeviceToHost, s));
       MGD_CUDA(cudaStreamSynchronize(s));
@@ -2575,6 +2582,7 @@ int mgd_opts_default(mgd_opts* o) {
   o->inner_mode = 0;
   o->smoother = 0;
   o->agg_levels = 0;
+  o->arnoldi_resident = 1;
   return MGD_OK;
 }
 
@@ -2590,7 +2598,7 @@ int mgd_create(mgd_ctx** out, const mgd_opts* o, void* stream) {
       q.precision < 0 || q.precision > 1 || q.inner_mode < 0 || q.inner_mode > 1 || q.inner_maxit < 1 ||
       q.inner_maxit > 100000 || !(q.inner_tol >= 0.0) || q.nvcyc_group > 1000 || q.nvcyc_E > 1000 ||
       q.nvcyc_I > 1000 || q.nvcyc_other > 1000 || q.jacobi_sweeps > 1000 || q.smoother < 0 || q.smoother > 1 ||
-      q.agg_levels < 0 || q.agg_levels > q.max_levels) {
+      q.agg_levels < 0 || q.agg_levels > q.max_levels || q.arnoldi_resident < 0 || q.arnoldi_resident > 1) {
     delete c;
     return MGD_EINVAL;
   }

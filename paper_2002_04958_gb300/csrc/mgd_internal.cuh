@@ -455,6 +455,12 @@ constexpr int kDotBlocks = 608;  // 4 x 152 SMs
 void launch_mgs(int n, const double* V, long long ldv, int nv, double* w, double* h, double* nrm2, double* pa,
                 double* pb, cudaStream_t s);
 void launch_scale_by_norm(int n, const double* w, const double* nrm2, double* v, cudaStream_t s);
+// the same modified Gram-Schmidt pass plus the scaling, as one cooperative
+// grid of nb blocks with w in shared memory (nb from arnoldi_coop_blocks; part:
+// (nv + 1) * nb doubles)
+int arnoldi_coop_blocks(int n);
+void launch_arnoldi_coop(int nb, int n, const double* V, long long ldv, int nv, const double* w, double* h,
+                         double* nrm2, double* part, double* vout, cudaStream_t s);
 void launch_vcomb(int n, const double* Z, long long ldz, int nv, const double* y, double* x, cudaStream_t s);
 void launch_norm2(int n, const double* x, double* partial, double* out, cudaStream_t s);
 void launch_block_resid(int N, int nc, const int* const* brp, const int* const* bci, const double* const* bv,

@@ -5,7 +5,11 @@
 #include "mgd_internal.cuh"
 #include "row_dot.cuh"
 
+#include <cooperative_groups.h>
+
 namespace mgd {
+
+namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------- block-level updates
 __device__ __forceinline__ double* resolve(const PRef& r, const IOSlots* io) {
@@ -324,6 +328,106 @@ __global__ void k_scale_by_norm(int n, const double* __restrict__ w, const doubl
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = w[i] * s_inv;
 }
+// ---------------------------------------------------------------- Arnoldi with w resident on chip
+// One cooperative grid, one 1024-thread block per SM: block b keeps its slice
+// of w in shared memory for the whole modified Gram-Schmidt pass.  Step i
+// reads the slice of v_i (its partial <v_i, w> goes to `part`), a grid-wide
+// barrier, then every block sums the per-block partials in the same fixed
+// order (so all hold the same h_i) and updates w -= h_i v_i in shared memory
+// (that second read of v_i comes from L2).  Each basis vector is read once
+// from HBM, instead of w being streamed in and out per step.  Ends with
+// ||w||^2 and v_out = w / ||w||.
+constexpr int kArnThreads = 1024;
+
+__device__ __forceinline__ double arn_block_sum(double v, double* red, double* bc) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kArnThreads / 32; ++k) t += red[k];
+    *bc = t;
+  }
+  __syncthreads();
+  return *bc;
+}
+
+__global__ void __launch_bounds__(kArnThreads, 1) k_arnoldi_coop(int n, const double* __restrict__ V, long long ldv,
+                                                               int nv, const double* __restrict__ w,
+                                                               double* __restrict__ h, double* __restrict__ nrm2,
+                                                               double* __restrict__ part, double* __restrict__ vout) {
+  extern __shared__ double ws[];
+  __shared__ double red[kArnThreads / 32];
+  __shared__ double bc;
+  cg::grid_group grid = cg::this_grid();
+  const int nb = gridDim.x, b = blockIdx.x, t = threadIdx.x;
+  const long long S = ((long long)n + nb - 1) / nb;
+  const long long lo = (long long)b * S;
+  const int len = (int)max(0LL, min((long long)n, lo + S) - lo);
+  for (int e = t; e < len; e += kArnThreads) ws[e] = w[lo + e];
+  // every thread owns the same entries of ws from here on: no block barrier for them
+  for (int i = 0; i < nv; ++i) {  // every block runs every step: the grid barriers always match
+    const double* vi = V + (long long)i * ldv + lo;
+    double d = 0.0;
+    for (int e = t; e < len; e += kArnThreads) d += vi[e] * ws[e];
+    d = arn_block_sum(d, red, &bc);
+    if (t == 0) part[(long long)i * nb + b] = d;
+    grid.sync();
+    double hi = arn_block_sum(t < nb ? __ldcg(part + (long long)i * nb + t) : 0.0, red, &bc);
+    if (b == 0 && t == 0) h[i] = hi;
+    for (int e = t; e < len; e += kArnThreads) ws[e] = ws[e] - hi * vi[e];
+  }
+  double d = 0.0;
+  for (int e = t; e < len; e += kArnThreads) d += ws[e] * ws[e];
+  d = arn_block_sum(d, red, &bc);
+  if (t == 0) part[(long long)nv * nb + b] = d;
+  grid.sync();
+  double nn = arn_block_sum(t < nb ? __ldcg(part + (long long)nv * nb + t) : 0.0, red, &bc);
+  if (b == 0 && t == 0) *nrm2 = nn;
+  double hn = sqrt(nn);
+  double inv = hn != 0.0 ? 1.0 / hn : 0.0;
+  for (int e = t; e < len; e += kArnThreads) vout[lo + e] = ws[e] * inv;
+}
+
+// blocks of the cooperative grid (one per SM), or 0 when n does not fit the
+// shared memory or the device cannot run the grid
+int arnoldi_coop_blocks(int n) {
+  int dev = 0, sms = 0, coop = 0, smax = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) ||
+      cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (!coop || sms <= 0 || sms > kArnThreads) return 0;
+  long long S = ((long long)n + sms - 1) / sms;
+  size_t smem = (size_t)S * sizeof(double);
+  size_t stat = (kArnThreads / 32 + 1) * sizeof(double);
+  if (smem + stat > (size_t)smax) return 0;
+  if (cudaFuncSetAttribute(k_arnoldi_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_arnoldi_coop, kArnThreads, smem) != cudaSuccess ||
+      per < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms;
+}
+
+void launch_arnoldi_coop(int nb, int n, const double* V, long long ldv, int nv, const double* w, double* h,
+                         double* nrm2, double* part, double* vout, cudaStream_t s) {
+  long long S = ((long long)n + nb - 1) / nb;
+  size_t smem = (size_t)S * sizeof(double);
+  void* args[] = {(void*)&n, (void*)&V, (void*)&ldv, (void*)&nv, (void*)&w, (void*)&h, (void*)&nrm2,
+                  (void*)&part, (void*)&vout};
+  MGD_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop, dim3(nb), dim3(kArnThreads), args, smem, s));
+  MGD_LAUNCH_CHECK();
+}
+
 void launch_scale_by_norm(int n, const double* w, const double* nrm2, double* v, cudaStream_t s) {
   launch_k(k_scale_by_norm, dim3(cdiv(n, kThreads)), dim3(kThreads), 0, s, n, w, nrm2, v);
   MGD_LAUNCH_CHECK();

@@ -38,7 +38,7 @@ class MgdOpts(C.Structure):
                 ("restart", C.c_int), ("max_it", C.c_int), ("precision", C.c_int), ("batched", C.c_int),
                 ("use_graph", C.c_int), ("autotune", C.c_int), ("keep_transpose", C.c_int),
                 ("fuse_rows", C.c_int), ("interp_type", C.c_int), ("pdl", C.c_int), ("inner_mode", C.c_int),
-                ("smoother", C.c_int), ("agg_levels", C.c_int)]
+                ("smoother", C.c_int), ("agg_levels", C.c_int), ("arnoldi_resident", C.c_int)]
 
 
 class MgdStats(C.Structure):

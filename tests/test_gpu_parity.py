@@ -285,3 +285,22 @@ def test_adjoint_gradient(gpu, orc):
         fd = ((lp * lp).sum() - (lm * lm).sum()).item() / (2 * h)
         an = (vals.grad * dv).sum().item()
         assert fd == pytest.approx(an, rel=1e-5)
+
+
+@pytest.mark.parametrize("kind", ["amg", "schur1", "bd"])
+@pytest.mark.parametrize("case", [CASES[0], CASES[3], CASES[4]], ids=["G1", "G20", "G2_3d"])
+def test_resident_arnoldi_matches_streaming(gpu, orc, kind, case):
+    # the cooperative orthogonalisation (w in shared memory) and the streaming
+    # kernels run the same modified Gram-Schmidt: same iterations, same x to rounding
+    s = _system(case)
+    b = torch.from_numpy(s.b)
+    xs, its, _, _ = gpu.Solver(arnoldi_resident=0).setup_system(s, kind).solve(b, tol=1e-8)
+    slv = gpu.Solver(arnoldi_resident=1).setup_system(s, kind)
+    xr, itr, rr, rc = slv.solve(b, tol=1e-8)
+    assert rc == 0 and itr == its
+    assert torch.linalg.vector_norm(xr - xs) <= 1e-10 * torch.linalg.vector_norm(xs)
+    Ao = orc.csr_of_system(s)
+    _, ito, _, _, _ = orc.fgmres(Ao, s.b, orc.Block(Ao, s.G, s.N, kind), tol=1e-8)
+    assert itr == ito
+    x2, it2, _, _ = slv.solve(b, tol=1e-8)      # run to run: the same bits
+    assert it2 == itr and torch.equal(x2, xr)
