@@ -256,9 +256,10 @@ def test_solve_host_buffers(gpu, orc):
     assert it == itd and np.array_equal(x, xd.cpu().numpy())
 
 
-def test_adjoint_gradient(gpu, orc):
+@pytest.mark.parametrize("smoother", [0, 1], ids=["l1jacobi", "cf_gauss_seidel"])
+def test_adjoint_gradient(gpu, orc, smoother):
     s = I.make_system(4, (12, 10), multigroup=True)
-    slv = gpu.Solver(keep_transpose=1).setup_system(s, "amg")
+    slv = gpu.Solver(keep_transpose=1, smoother=smoother).setup_system(s, "amg")
     vals = torch.from_numpy(s.val).cuda().requires_grad_(True)
     b = torch.from_numpy(s.b).cuda().requires_grad_(True)
     x = gpu.mgd_solve(vals, b, slv, 1e-13)
@@ -266,7 +267,7 @@ def test_adjoint_gradient(gpu, orc):
     loss.backward()
     # oracle gradient
     Ao = orc.csr_of_system(s)
-    M = orc.Block(Ao, s.G, s.N, "amg")
+    M = orc.Block(Ao, s.G, s.N, "amg", orc.opts(smoother=smoother))
     xo, *_ = orc.fgmres(Ao, s.b, M, tol=1e-14, maxit=2000)
     lo, *_ = orc.fgmres(Ao, 2 * xo, M, tol=1e-14, maxit=2000, transpose=True)
     go = orc.grad_vals(Ao, xo, lo)
