@@ -148,7 +148,9 @@ def run_ours(args):
             dist.barrier()
 
     clocks = ClockSampler(local, enabled=not args.no_clocks)
-    slv.profile(1)            # bracket only the dominant level-0 kernels inside the timed region
+    # the dominant level-0 kernels are bracketed by CUDA events during the first
+    # timed step only: event nodes between kernels cost a few percent of a step
+    slv.profile(1)
     l0 = mgdamg.kernel_launches()
     barrier()
     torch.cuda.synchronize()
@@ -156,12 +158,15 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     setup_ms, solve_ms, iters = [], [], []
-    for _ in range(args.steps):
+    for k in range(args.steps):
         x, it, rr = step()
         st = slv.stats()
         setup_ms.append(st["setup_ms"])
         solve_ms.append(st["solve_ms"])
         iters.append(it)
+        if k == 0:
+            n0, t0, by0 = slv.profile_read(0)    # level-0 smoothing + residual kernels (dominant)
+            slv.profile(0)
     e1.record()
     torch.cuda.synchronize()
     barrier()
@@ -173,7 +178,6 @@ def run_ours(args):
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = t.item()
-    n0, t0, by0 = slv.profile_read(0)    # level-0 smoothing + residual kernels (dominant)
     # V-cycle GB/s over every V-cycle kernel: one more (untimed) step with all V-cycle classes bracketed
     slv.profile(0b11)
     step()
@@ -284,7 +288,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "level-0 l1-Jacobi smoothing + residual (k_pre/k_post)",
                      "achieved": round(ach, 1) if ach else None, "peak": peak, "unit": "GB/s",
                      "frac": round(ach / peak, 4) if ach else None, "traffic": traffic,
-                     "peak_source": peak_kind, "launches": n0, "ms": round(t0, 4)},
+                     "peak_source": peak_kind, "launches": n0, "ms": round(t0, 4),
+                     "sampled": "every launch of the class in the first timed step"},
         "e2e": {"value": round(statistics.median(e2e_ms) / 1e3, 6) if e2e_ms else None, "unit": "s",
                 "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
