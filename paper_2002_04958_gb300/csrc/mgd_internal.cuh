@@ -164,7 +164,8 @@ struct Csr {  // device CSR, FP64 values
 };
 
 // sparse-kernel formats chosen per level by the autotuner
-enum Fmt { FMT_SELL = 0, FMT_CSR1 = 1, FMT_CSR2 = 2, FMT_CSR4 = 3, FMT_CSR8 = 4, FMT_CSR16 = 5, FMT_CSR32 = 6 };
+enum Fmt { FMT_SELL = 0, FMT_CSR1 = 1, FMT_CSR2 = 2, FMT_CSR4 = 3, FMT_CSR8 = 4, FMT_CSR16 = 5, FMT_CSR32 = 6,
+           FMT_SELL2 = 7 };  // SELL2: SELL-32, each thread on the same lane of two adjacent slices (smoothing only)
 constexpr int kNumFmt = 7;
 
 struct Sell {  // sliced ELL, slice height 32, column-major inside a slice
