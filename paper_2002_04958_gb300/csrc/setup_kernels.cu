@@ -1357,7 +1357,105 @@ __global__ void k_dense_inverse(int n, double* a, int* piv, double* inv, double*
   }
 }
 
+// Gauss-Jordan on [A | I] in shared memory, one 1024-thread block (n <= kGjMax).
+// The rows below the pivot are updated exactly as the LU elimination above
+// does (l = a_ik / a_kk, a_ij -= l a_kj, no fused multiply-add in this unit),
+// so the pivot rows and the singularity decision are those of k_dense_inverse;
+// rows above the pivot are eliminated too, and the reduced rows are finally
+// divided by their pivots.
+constexpr int kGjThreads = 1024;
+constexpr int kGjMax = 112;  // 2 n^2 doubles + n multipliers fit the opt-in shared memory
+__global__ void __launch_bounds__(kGjThreads) k_dense_inverse_gj(int n, const double* __restrict__ a0, int* piv,
+                                                                 double* inv, double* invT, int* status) {
+  extern __shared__ double gj[];
+  double* A = gj;          // n x n, row-major
+  double* X = gj + n * n;  // n x n, row-major, starts as I
+  double* L = X + n * n;   // multipliers of the current step
+  __shared__ int s_pr;
+  __shared__ double s_best;
+  const int t = threadIdx.x;
+  for (int e = t; e < n * n; e += kGjThreads) {
+    A[e] = a0[e];
+    X[e] = (e / n == e % n) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (t < 32) {  // pivot: largest |a_ik|, i >= k, first index on ties (as the sequential search)
+      double best = -1.0;
+      int pr = n;
+      for (int i = k + t; i < n; i += 32) {
+        double v = fabs(A[i * n + k]);
+        if (v > best) {
+          best = v;
+          pr = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int op = __shfl_xor_sync(0xffffffffu, pr, o);
+        if (ob > best || (ob == best && op < pr)) {
+          best = ob;
+          pr = op;
+        }
+      }
+      if (t == 0) {
+        s_pr = pr;
+        s_best = best;
+        piv[k] = pr;
+      }
+    }
+    __syncthreads();
+    if (s_best == 0.0) {
+      if (t == 0) *status = 1;
+      return;
+    }
+    const int pr = s_pr;
+    if (pr != k)
+      for (int j = t; j < 2 * n; j += kGjThreads) {
+        double* M = j < n ? A : X;
+        int c = j < n ? j : j - n;
+        double tmp = M[k * n + c];
+        M[k * n + c] = M[pr * n + c];
+        M[pr * n + c] = tmp;
+      }
+    __syncthreads();
+    for (int i = t; i < n; i += kGjThreads) L[i] = i == k ? 0.0 : __ddiv_rn(A[i * n + k], A[k * n + k]);
+    __syncthreads();
+    // every row but k: columns k+1.. of A and all of X
+    const int wa = n - k - 1, w = wa + n;
+    for (int e = t; e < n * w; e += kGjThreads) {
+      int i = e / w, j = e % w;
+      if (i == k) continue;
+      if (j < wa) {
+        int c = k + 1 + j;
+        A[i * n + c] = __dsub_rn(A[i * n + c], __dmul_rn(L[i], A[k * n + c]));
+      } else {
+        int c = j - wa;
+        X[i * n + c] = __dsub_rn(X[i * n + c], __dmul_rn(L[i], X[k * n + c]));
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < n * n; e += kGjThreads) {
+    int i = e / n, c = e % n;
+    double v = __ddiv_rn(X[e], A[i * n + i]);
+    inv[e] = v;
+    invT[c * n + i] = v;
+  }
+}
+
 void launch_dense_inverse(int n, double* a, int* piv, double* inv, double* invT, int* status, cudaStream_t s) {
+  if (n <= kGjMax) {
+    size_t smem = (size_t)(2 * n * n + n) * sizeof(double);
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_dense_inverse_gj, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)((size_t)(2 * kGjMax * kGjMax + kGjMax) * sizeof(double)));
+    MGD_CUDA(attr);
+    k_dense_inverse_gj<<<1, kGjThreads, smem, s>>>(n, a, piv, inv, invT, status);
+    MGD_LAUNCH_CHECK();
+    return;
+  }
   k_dense_inverse<<<1, 128, 0, s>>>(n, a, piv, inv, invT, status);
   MGD_LAUNCH_CHECK();
 }
