@@ -1002,7 +1002,7 @@ static void autotune(VBatch<T>& vb, bool trans, cudaStream_t s) {
     MGD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     return ms;
   };
-  const int candA[] = {FMT_SELL, FMT_SELL2, FMT_CSR1, FMT_CSR2, FMT_CSR4, FMT_CSR8};
+  const int candA[] = {FMT_SELL, FMT_SELL2, FMT_SELL4, FMT_CSR1, FMT_CSR2, FMT_CSR4, FMT_CSR8};
   const int candRP[] = {FMT_CSR1, FMT_CSR2, FMT_CSR4, FMT_CSR8};
   for (int l = 0; l < vb.depth; ++l) {
     auto& lp = plan[l];
@@ -1022,7 +1022,7 @@ static void autotune(VBatch<T>& vb, bool trans, cudaStream_t s) {
       best = 1e30f;
       int pick = lp.fmtGS;
       for (int f : candA) {
-        if (f == FMT_SELL2 || (f == FMT_SELL && !lp.gs_sell)) continue;
+        if (f == FMT_SELL2 || f == FMT_SELL4 || (f == FMT_SELL && !lp.gs_sell)) continue;
         lp.fmtGS = f;
         float ms = time_it([&] { run_gs_down<T>(lp, s); });
         if (ms < best) {

@@ -69,62 +69,66 @@ __global__ void __launch_bounds__(kThreads) k_post(const LDesc<T>* __restrict__ 
   if (valid && lane == 0) d->x[row] = d->xt[row] + di * (d->b[row] - s);
 }
 
-// SELL2 forms of PRE and POST: each thread smooths the same lane of two
-// adjacent 32-row slices, so twice the loads are in flight per thread (the
-// row sums are those of the SELL kernels)
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_pre_s2(const LDesc<T>* __restrict__ descs) {
+// Multi-slice forms of PRE and POST (FMT_SELL2, FMT_SELL4): each thread smooths
+// the same lane of K adjacent 32-row slices, so K rows' loads are in flight per
+// thread (the row sums are those of the SELL kernels)
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) k_pre_sk(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   int w = g >> 5, lane = g & 31;
   int n = d->n;
-  if (w * 64 >= n) return;  // the whole warp is past the last row
-  int r0 = w * 64 + lane, r1 = r0 + 32;
-  bool v0 = r0 < n, v1 = r1 < n;
-  RowPre<T, kPre> R0, R1;
-  row_load<T, FMT_SELL, kPre>(R0, r0, 0, v0, nullptr, nullptr, nullptr, d->sptr, d->sci, d->svpre);
-  row_load<T, FMT_SELL, kPre>(R1, r1, 0, v1, nullptr, nullptr, nullptr, d->sptr, d->sci, d->svpre);
-  T di0 = v0 ? d->dinv[r0] : T(0), di1 = v1 ? d->dinv[r1] : T(0);
+  if (w * 32 * K >= n) return;  // the whole warp is past the last row
+  RowPre<T, kPre> R[K];
+  T di[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    int r = (w * K + q) * 32 + lane;
+    row_load<T, FMT_SELL, kPre>(R[q], r, 0, r < n, nullptr, nullptr, nullptr, d->sptr, d->sci, d->svpre);
+    di[q] = r < n ? d->dinv[r] : T(0);
+  }
   MGD_PDL_WAIT();
   MGD_SKIP_INACTIVE(d);
   const T* b = d->b;
   XPlain<T> xf{b};
-  T s0 = row_finish<T, FMT_SELL, kPre>(R0, v0, nullptr, nullptr, d->sci, d->svpre, xf);
-  T s1 = row_finish<T, FMT_SELL, kPre>(R1, v1, nullptr, nullptr, d->sci, d->svpre, xf);
-  if (v0) {
-    T bi = b[r0];
-    d->xt[r0] = di0 * bi;
-    d->r[r0] = bi - s0;
-  }
-  if (v1) {
-    T bi = b[r1];
-    d->xt[r1] = di1 * bi;
-    d->r[r1] = bi - s1;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    int r = (w * K + q) * 32 + lane;
+    T s = row_finish<T, FMT_SELL, kPre>(R[q], r < n, nullptr, nullptr, d->sci, d->svpre, xf);
+    if (r < n) {
+      T bi = b[r];
+      d->xt[r] = di[q] * bi;
+      d->r[r] = bi - s;
+    }
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_post_s2(const LDesc<T>* __restrict__ descs) {
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) k_post_sk(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   int w = g >> 5, lane = g & 31;
   int n = d->n;
-  if (w * 64 >= n) return;
-  int r0 = w * 64 + lane, r1 = r0 + 32;
-  bool v0 = r0 < n, v1 = r1 < n;
-  RowPre<T, kPre> R0, R1;
-  row_load<T, FMT_SELL, kPre>(R0, r0, 0, v0, nullptr, nullptr, nullptr, d->sptr, d->sci, d->sv);
-  row_load<T, FMT_SELL, kPre>(R1, r1, 0, v1, nullptr, nullptr, nullptr, d->sptr, d->sci, d->sv);
-  T di0 = v0 ? d->dinv[r0] : T(0), di1 = v1 ? d->dinv[r1] : T(0);
+  if (w * 32 * K >= n) return;
+  RowPre<T, kPre> R[K];
+  T di[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    int r = (w * K + q) * 32 + lane;
+    row_load<T, FMT_SELL, kPre>(R[q], r, 0, r < n, nullptr, nullptr, nullptr, d->sptr, d->sci, d->sv);
+    di[q] = r < n ? d->dinv[r] : T(0);
+  }
   MGD_PDL_WAIT();
   MGD_SKIP_INACTIVE(d);
   XPlain<T> xf{d->xt};
-  T s0 = row_finish<T, FMT_SELL, kPre>(R0, v0, nullptr, nullptr, d->sci, d->sv, xf);
-  T s1 = row_finish<T, FMT_SELL, kPre>(R1, v1, nullptr, nullptr, d->sci, d->sv, xf);
-  if (v0) d->x[r0] = d->xt[r0] + di0 * (d->b[r0] - s0);
-  if (v1) d->x[r1] = d->xt[r1] + di1 * (d->b[r1] - s1);
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    int r = (w * K + q) * 32 + lane;
+    T s = row_finish<T, FMT_SELL, kPre>(R[q], r < n, nullptr, nullptr, d->sci, d->sv, xf);
+    if (r < n) d->x[r] = d->xt[r] + di[q] * (d->b[r] - s);
+  }
 }
 
 // RESTRICT: bc = R r ; PROLONG: xt += P xc  (CSR, TPR threads per row)
@@ -218,15 +222,21 @@ void launch_phase(int phase, int fmtA, int fmtRP, const LDesc<T>* d_descs, int n
   switch (phase) {
     case PH_PRE:
       if (fmtA == FMT_SELL2)
-        launch_k(k_pre_s2<T>, dim3(cdiv((long long)cdiv(maxrows, 64) * 32, kThreads), ndesc), dim3(kThreads), 0, s,
-                 d_descs);
+        launch_k(k_pre_sk<T, 2>, dim3(cdiv((long long)cdiv(maxrows, 64) * 32, kThreads), ndesc), dim3(kThreads), 0,
+                 s, d_descs);
+      else if (fmtA == FMT_SELL4)
+        launch_k(k_pre_sk<T, 4>, dim3(cdiv((long long)cdiv(maxrows, 128) * 32, kThreads), ndesc), dim3(kThreads), 0,
+                 s, d_descs);
       else
         MGD_DISPATCH_FMT(k_pre, fmtA, maxrows, ndesc, s, d_descs);
       break;
     case PH_POST:
       if (fmtA == FMT_SELL2)
-        launch_k(k_post_s2<T>, dim3(cdiv((long long)cdiv(maxrows, 64) * 32, kThreads), ndesc), dim3(kThreads), 0, s,
-                 d_descs);
+        launch_k(k_post_sk<T, 2>, dim3(cdiv((long long)cdiv(maxrows, 64) * 32, kThreads), ndesc), dim3(kThreads), 0,
+                 s, d_descs);
+      else if (fmtA == FMT_SELL4)
+        launch_k(k_post_sk<T, 4>, dim3(cdiv((long long)cdiv(maxrows, 128) * 32, kThreads), ndesc), dim3(kThreads), 0,
+                 s, d_descs);
       else
         MGD_DISPATCH_FMT(k_post, fmtA, maxrows, ndesc, s, d_descs);
       break;
@@ -330,7 +340,7 @@ void launch_gs_sweep(int fmt, const LDesc<T>* d, int nd, int maxrows, int t, int
 template <typename T>
 void launch_gs_resid(int fmtA, const LDesc<T>* d, int nd, int maxrows, cudaStream_t s) {
   if (nd <= 0 || maxrows <= 0) return;
-  if (fmtA == FMT_SELL2) fmtA = FMT_SELL;  // the two-slice form exists for the l1-Jacobi phases only
+  if (fmtA == FMT_SELL2 || fmtA == FMT_SELL4) fmtA = FMT_SELL;  // multi-slice forms: l1-Jacobi phases only
   MGD_DISPATCH_FMT(k_gs_resid, fmtA, maxrows, nd, s, d);
   MGD_LAUNCH_CHECK();
 }
