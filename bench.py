@@ -40,6 +40,24 @@ def _dist():
     return ws, rank, local
 
 
+def _barrier():
+    """Barrier over the ranks of an initialised process group (no-op alone)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def _max_over_ranks(v, device):
+    """The largest of the ranks' values (each replica's step time; the job's time is the slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1):
+        return v
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -142,10 +160,7 @@ def run_ours(args):
         x, it, rr = step()
     torch.cuda.synchronize()
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    barrier = _barrier
 
     clocks = ClockSampler(local, enabled=not args.no_clocks)
     # the dominant level-0 kernels are bracketed by CUDA events during the first
@@ -172,12 +187,7 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     launches = mgdamg.kernel_launches() - l0
-    ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = _max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
     # V-cycle GB/s over every V-cycle kernel: one more (untimed) step with all V-cycle classes bracketed
     slv.profile(0b11)
     step()
