@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -358,6 +359,20 @@ def kernel_source_sha256():
     return h.hexdigest()
 
 
+def _host_cpu():
+    """Host CPU model and logical core count (the oracle uses one core)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
 def cpu_baseline(args, sysm, gpu_iters):
     """The FP64 oracle on the same workload, single-threaded C on one host core."""
     from oracle import oracle as orc
@@ -376,7 +391,7 @@ def cpu_baseline(args, sysm, gpu_iters):
     return {"value": round((t1 - t0) + solve, 4), "unit": "s", "cores": 1, "kind": "oracle",
             "sample": (f"full oracle setup + FGMRES solve of the same system ({it} iterations)" if full else
                        f"full oracle setup + {it} FGMRES iterations scaled to {gpu_iters}"),
-            "setup_s": round(t1 - t0, 4), "iters": it, "converged": full}
+            "setup_s": round(t1 - t0, 4), "iters": it, "converged": full, "host": _host_cpu()}
 
 
 def run_reference(args):
@@ -419,7 +434,8 @@ def run_reference(args):
                    "precond": args.kind, "interpolation": "extended+i" if args.interp else "classical modified"},
         "cpu_baseline": {"value": round(v, 4), "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": f"per step: full oracle setup + {args.ref_iters} FGMRES iterations, "
-                                   f"scaled to the {full_its} iterations of the full solve"},
+                                   f"scaled to the {full_its} iterations of the full solve",
+                         "host": _host_cpu()},
         "e2e": {"value": round(v, 4), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
