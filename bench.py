@@ -195,6 +195,8 @@ def run_ours(args):
     vcycles = slv.total_cycles()   # V-cycles of one solve (counted since its setup)
     n1, t1, by1 = slv.profile_read(1)
     slv.profile(0)
+    # preconditioner bandwidth: 100 applies back to back (graph replays), no per-kernel events
+    pms, pby = slv.precond_bench(b, 100)
     st = slv.stats()
     xg = x
     relres = rr
@@ -296,6 +298,8 @@ def run_ours(args):
         "setup_ms": round(statistics.median(setup_ms), 3),
         "solve_ms": round(statistics.median(solve_ms), 3),
         "vcycle_gbs": round(vgbs, 1) if vgbs else None,
+        "precond_gbs_back_to_back": round(pby / (pms * 1e-3) / 1e9, 1) if pms > 0 else None,
+        "precond_ms_per_apply": round(pms, 4),
         "roofline": {"bound": "hbm", "kernel": "level-0 l1-Jacobi smoothing + residual (k_pre/k_post)",
                      "achieved": round(ach, 1) if ach else None, "peak": peak, "unit": "GB/s",
                      "frac": round(ach / peak, 4) if ach else None, "traffic": traffic,

@@ -151,6 +151,17 @@ int mgd_grad_values(mgd_ctx *c, const double *d_x, const double *d_lambda, doubl
 /* One application z = M^{-1} v of the preconditioner (d_v[n], d_z[n]). */
 int mgd_precond_apply(mgd_ctx *c, const double *d_v, double *d_z);
 
+/* Measurement service (Section 4's preconditioner applied back to back, as
+ * the V-cycle bandwidth of the timing plan needs): z = M^{-1} v applied
+ * `count` times on the context's stream with no synchronisation between
+ * applies (graph replays when use_graph), timed by two CUDA events.
+ * *ms_per_apply = elapsed / count; *bytes_per_apply = the algorithmic bytes
+ * of one apply (its V-cycles and block updates, as mgd_stats.precond_bytes).
+ * d_v[n], d_z[n] device buffers.  MGD_EINVAL for count < 1 or NULL pointers,
+ * MGD_ESTATE before setup. */
+int mgd_precond_bench(mgd_ctx *c, const double *d_v, double *d_z, int count, double *ms_per_apply,
+                      double *bytes_per_apply);
+
 /* Statistics of the current setup. */
 typedef struct mgd_stats {
   int kind, G, N, n, nnz;

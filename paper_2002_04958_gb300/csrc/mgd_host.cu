@@ -2721,6 +2721,36 @@ int mgd_precond_apply(mgd_ctx* c, const double* d_v, double* d_z) {
   });
 }
 
+int mgd_precond_bench(mgd_ctx* c, const double* d_v, double* d_z, int count, double* ms_per_apply,
+                      double* bytes_per_apply) {
+  return guarded(c, [&]() -> int {
+    if (!c->ready) throw Error{MGD_ESTATE, "no setup"};
+    if (!d_v || !d_z || count < 1 || !ms_per_apply || !bytes_per_apply) throw Error{MGD_EINVAL, "invalid arguments"};
+    cudaEvent_t e0, e1;
+    MGD_CUDA(cudaEventCreate(&e0));
+    MGD_CUDA(cudaEventCreate(&e1));
+    float ms = 0.0f;
+    try {
+      precond_apply(c, d_v, d_z, false);  // warm
+      MGD_CUDA(cudaEventRecord(e0, c->s));
+      for (int k = 0; k < count; ++k) precond_apply(c, d_v, d_z, false);
+      MGD_CUDA(cudaEventRecord(e1, c->s));
+      MGD_CUDA(cudaEventSynchronize(e1));
+      MGD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    } catch (...) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->prof.harvest();
+    *ms_per_apply = (double)ms / count;
+    *bytes_per_apply = c->st.precond_bytes;
+    return MGD_OK;
+  });
+}
+
 int mgd_get_stats(mgd_ctx* c, mgd_stats* s) {
   if (!c || !s) return MGD_EINVAL;
   *s = c->st;

@@ -25,7 +25,7 @@ ENTRY_POINTS = ["mgd_opts_default", "mgd_create", "mgd_setup", "mgd_update_value
                 "mgd_solve_transpose", "mgd_grad_values", "mgd_precond_apply", "mgd_get_stats", "mgd_get_history",
                 "mgd_op_info", "mgd_level_info", "mgd_level_export", "mgd_block_vector", "mgd_coupling_dropped",
                 "mgd_profile_enable", "mgd_profile_read", "mgd_kernel_launches", "mgd_last_error", "mgd_destroy", "mgd_plan_info",
-                "mgd_setup_phases", "mgd_op_cycles", "mgd_level_keys",
+                "mgd_setup_phases", "mgd_op_cycles", "mgd_level_keys", "mgd_precond_bench",
                 "mgd_relres_noalloc"]
 
 
@@ -80,6 +80,7 @@ def lib():
             "mgd_op_info": (I, [P, I, pI, pI, pI, pI, pI]),
             "mgd_level_info": (I, [P, I, I, pI, pI, pI, pI]),
             "mgd_op_cycles": (I, [P, I, pLL]),
+            "mgd_precond_bench": (I, [P, P, P, I, pD, pD]),
             "mgd_level_keys": (I, [P, I, I, pI, P]),
             "mgd_level_export": (I, [P, I, I, P, P, P, P, P, P, P]),
             "mgd_block_vector": (I, [P, I, I, I, P]),
@@ -236,6 +237,15 @@ class Solver:
         self._order()
         self._check(lib().mgd_precond_apply(self.h, _ptr(v), _ptr(z)))
         return z
+
+    def precond_bench(self, v, count=100):
+        """(ms per apply, algorithmic bytes per apply) of `count` preconditioner applies back to back."""
+        v = v.to(device="cuda", dtype=self.torch.float64).contiguous()
+        z = self.torch.empty_like(v)
+        ms, by = C.c_double(), C.c_double()
+        self._order()
+        self._check(lib().mgd_precond_bench(self.h, _ptr(v), _ptr(z), int(count), C.byref(ms), C.byref(by)))
+        return ms.value, by.value
 
     def stats(self):
         s = MgdStats()

@@ -305,3 +305,17 @@ def test_resident_arnoldi_matches_streaming(gpu, orc, kind, case):
     assert itr == ito
     x2, it2, _, _ = slv.solve(b, tol=1e-8)      # run to run: the same bits
     assert it2 == itr and torch.equal(x2, xr)
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(batched=1, use_graph=1)], ids=["eager", "graph"])
+def test_precond_bench_matches_apply(gpu, opts):
+    s = _system(CASES[3])
+    slv = gpu.Solver(**opts).setup_system(s, "bd")
+    v = torch.from_numpy(np.random.default_rng(9).standard_normal(s.n))
+    z = slv.precond_apply(v)
+    ms, by = slv.precond_bench(v, 20)
+    assert ms > 0 and by == pytest.approx(slv.stats()["precond_bytes"])
+    z2 = slv.precond_apply(v)   # the repeated applies left the solver as it was
+    assert torch.equal(z, z2)
+    with pytest.raises(gpu.MgdError):
+        slv.precond_bench(v, 0)
