@@ -244,7 +244,8 @@ void launch_phase(int phase, int fmtA, int fmtRP, const LDesc<T>* d_descs, int n
     case PH_PROLONG: MGD_DISPATCH_FMT(k_prolong, rp, maxrows, ndesc, s, d_descs); break;
     case PH_JAC1: launch_k(k_jac1<T>, dim3(dim3(cdiv(maxrows, kThreads), ndesc)), dim3(kThreads), 0, s, d_descs); break;
     case PH_COARSE:
-      launch_k(k_coarse<T>, dim3(dim3(1, ndesc)), dim3(kThreads), sizeof(double) * maxrows, s, d_descs);
+      // one 1024-thread CTA per subsystem: a warp per row of the dense inverse
+      launch_k(k_coarse<T>, dim3(dim3(1, ndesc)), dim3(1024), sizeof(double) * maxrows, s, d_descs);
       break;
   }
   MGD_LAUNCH_CHECK();
