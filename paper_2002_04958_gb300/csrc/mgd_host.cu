@@ -465,7 +465,11 @@ static bool coarsen_pass(SetupCtx& sc, const Csr& A, int lid, Scratch* keep, Pas
     P.nnz = read_int(P.rp + n, s);
     P.ci = keep ? keep->alloc<int>(P.nnz) : ar.alloc<int>(P.nnz);
     P.v = keep ? keep->alloc<double>(P.nnz) : ar.alloc<double>(P.nnz);
-    launch_interp_fill(n, A.rp, A.ci, A.v, S, CF, cidx, P.rp, P.ci, P.v, s);
+    double* dg = tmp.alloc<double>(n);
+    launch_diag_extract(n, A.rp, A.ci, A.v, dg, s);
+    int* wi = tmp.alloc<int>((size_t)A.nnz + P.nnz);
+    double* wd = tmp.alloc<double>((size_t)A.nnz + n);
+    launch_interp_fill(n, A.nnz, A.rp, A.ci, A.v, S, CF, cidx, P.rp, P.nnz, P.ci, P.v, dg, wi, wd, s);
   }
   pt_int.stop();
   out.CF = CF;

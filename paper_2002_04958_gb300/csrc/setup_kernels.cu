@@ -624,78 +624,6 @@ __device__ __forceinline__ bool opp_sign(double akm, double akk) { return akk > 
 // F neighbours k distribute a_ik abar_kj / sum_{m in C_i} abar_km, or are lumped
 // into the diagonal with the weak neighbours when that sum is zero;
 // w_ij = -num_j / (a_ii + sum_W a_in).
-__global__ void k_interp_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S,
-                              const signed char* CF, const int* cidx, const int* prp, int* pci, double* pv) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int base = prp[i];
-  if (CF[i] == 1) {
-    pci[base] = cidx[i];
-    pv[base] = 1.0;
-    return;
-  }
-  int len = prp[i + 1] - base;
-  if (len == 0) return;
-  int t = 0;
-  double diag = 0.0;
-  for (int p = rp[i]; p < rp[i + 1]; ++p) {
-    int j = ci[p];
-    if (j == i) diag = v[p];
-    if (S[p] && CF[j] == 1) {
-      pci[base + t] = j;
-      pv[base + t] = v[p];
-      ++t;
-    }
-  }
-  for (int p = rp[i]; p < rp[i + 1]; ++p) {
-    int k = ci[p];
-    if (k == i) continue;
-    double aik = v[p];
-    if (S[p] && CF[k] == 1) continue;
-    if (S[p] && CF[k] == -1) {
-      double akk = 0.0;
-      for (int q = rp[k]; q < rp[k + 1]; ++q)
-        if (ci[q] == k) akk = v[q];
-      double denom = 0.0;
-      for (int q = rp[k]; q < rp[k + 1]; ++q) {
-        int m = ci[q];
-        for (int s = 0; s < len; ++s)
-          if (pci[base + s] == m) {
-            if (opp_sign(v[q], akk)) denom = __dadd_rn(denom, v[q]);
-            break;
-          }
-      }
-      if (denom == 0.0) {
-        diag = __dadd_rn(diag, aik);
-      } else {
-        for (int q = rp[k]; q < rp[k + 1]; ++q) {
-          int m = ci[q];
-          for (int s = 0; s < len; ++s)
-            if (pci[base + s] == m) {
-              if (opp_sign(v[q], akk)) {
-                double prod = __dmul_rn(aik, v[q]);
-                pv[base + s] = __dadd_rn(pv[base + s], __ddiv_rn(prod, denom));
-              }
-              break;
-            }
-        }
-      }
-    } else {
-      diag = __dadd_rn(diag, aik);
-    }
-  }
-  for (int s = 0; s < len; ++s) {
-    pv[base + s] = (diag != 0.0) ? __ddiv_rn(-pv[base + s], diag) : 0.0;
-    pci[base + s] = cidx[pci[base + s]];
-  }
-}
-
-void launch_interp_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S,
-                        const signed char* CF, const int* cidx, const int* prp, int* pci, double* pv,
-                        cudaStream_t s) {
-  k_interp_fill<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, S, CF, cidx, prp, pci, pv);
-  MGD_LAUNCH_CHECK();
-}
 
 // ------------------------------------------------------------------ extended+i interpolation
 // (De Sterck, Falgout, Nolting, Yang 2008): the interpolatory set of an F point
@@ -869,6 +797,117 @@ __global__ void k_exti_value(int nnzp, const int* prowof, const int* prp, const 
   double diag = diagv[i];
   pci[e] = cidx[l];
   pv[e] = (diag != 0.0) ? __ddiv_rn(-num, diag) : 0.0;
+}
+
+// Classical modified interpolation values in passes that keep the operand
+// order of the row-sequential definition (so its bits): the strong C
+// neighbours of each F row are written in row order (sorted: CSR columns are
+// sorted), then a denominator per strong-F entry of A, the lumped diagonal per
+// row, the value of each entry of P, and last the fine-to-coarse column map.
+__global__ void k_cl_set(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF,
+                         const int* cidx, const int* prp, int* pci, double* pv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int base = prp[i];
+  if (CF[i] == 1) {
+    pci[base] = cidx[i];
+    pv[base] = 1.0;
+    return;
+  }
+  int t = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (S[p] && CF[ci[p]] == 1) pci[base + t++] = ci[p];  // fine index until the last pass
+}
+
+__global__ void k_cl_denom(int nnz, const int* rowof, const int* rp, const int* ci, const double* v, const uint8_t* S,
+                           const signed char* CF, const int* prp, const int* pci, const double* dg, double* den) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nnz) return;
+  int i = rowof[p], k = ci[p];
+  if (CF[i] == 1 || k == i || !(S[p] && CF[k] == -1)) return;
+  const int* L = pci + prp[i];
+  int nl = prp[i + 1] - prp[i];
+  double akk = dg[k];
+  double denom = 0.0;
+  for (int q = rp[k]; q < rp[k + 1]; ++q)
+    if (find_sorted(L, nl, ci[q]) >= 0 && opp_sign(v[q], akk)) denom = __dadd_rn(denom, v[q]);
+  den[p] = denom;
+}
+
+__global__ void k_cl_diag(int n, const int* rp, const int* ci, const double* v, const uint8_t* S,
+                          const signed char* CF, const int* prp, const double* den, double* diagv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || CF[i] == 1 || prp[i + 1] == prp[i]) return;
+  double diag = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (ci[p] == i) diag = v[p];
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int k = ci[p];
+    if (k == i) continue;
+    if (S[p] && CF[k] == 1) continue;
+    if (S[p] && CF[k] == -1) {
+      if (den[p] == 0.0) diag = __dadd_rn(diag, v[p]);
+    } else {
+      diag = __dadd_rn(diag, v[p]);  // weak neighbours: lumped
+    }
+  }
+  diagv[i] = diag;
+}
+
+__global__ void k_cl_value(int nnzp, const int* prowof, const int* rp, const int* ci, const double* v,
+                           const uint8_t* S, const signed char* CF, const int* pci, const double* dg,
+                           const double* den, const double* diagv, double* pv) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnzp) return;
+  int i = prowof[e];
+  if (CF[i] == 1) return;
+  int m = pci[e];
+  double num = 0.0;
+  int pd = find_col(rp, ci, i, m);
+  if (pd >= 0) num = v[pd];
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int k = ci[p];
+    if (k == i || !(S[p] && CF[k] == -1)) continue;
+    double denom = den[p];
+    if (denom == 0.0) continue;
+    int q = find_col(rp, ci, k, m);
+    if (q >= 0 && opp_sign(v[q], dg[k])) num = __dadd_rn(num, __ddiv_rn(__dmul_rn(v[p], v[q]), denom));
+  }
+  double diag = diagv[i];
+  pv[e] = (diag != 0.0) ? __ddiv_rn(-num, diag) : 0.0;
+}
+
+__global__ void k_cl_columns(int nnzp, const int* prowof, const signed char* CF, const int* cidx, int* pci) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nnzp && CF[prowof[e]] != 1) pci[e] = cidx[pci[e]];
+}
+
+void launch_interp_fill(int n, int nnz, const int* rp, const int* ci, const double* v, const uint8_t* S,
+                        const signed char* CF, const int* cidx, const int* prp, int nnzp, int* pci, double* pv,
+                        const double* dg, int* work_i, double* work_d, cudaStream_t s) {
+  // work_i: nnz + nnzp ints (row of each entry of A, of P); work_d: nnz + n doubles
+  int* rowof = work_i;
+  int* prowof = work_i + nnz;
+  double* den = work_d;
+  double* diagv = work_d + nnz;
+  k_cl_set<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, S, CF, cidx, prp, pci, pv);
+  MGD_LAUNCH_CHECK();
+  k_row_of<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, rowof);
+  MGD_LAUNCH_CHECK();
+  k_row_of<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, prp, prowof);
+  MGD_LAUNCH_CHECK();
+  if (nnz > 0) {
+    k_cl_denom<<<cdiv(nnz, kThreads), kThreads, 0, s>>>(nnz, rowof, rp, ci, v, S, CF, prp, pci, dg, den);
+    MGD_LAUNCH_CHECK();
+  }
+  k_cl_diag<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, S, CF, prp, den, diagv);
+  MGD_LAUNCH_CHECK();
+  if (nnzp > 0) {
+    k_cl_value<<<cdiv(nnzp, kThreads), kThreads, 0, s>>>(nnzp, prowof, rp, ci, v, S, CF, pci, dg, den, diagv, pv);
+    MGD_LAUNCH_CHECK();
+    k_cl_columns<<<cdiv(nnzp, kThreads), kThreads, 0, s>>>(nnzp, prowof, CF, cidx, pci);
+    MGD_LAUNCH_CHECK();
+  }
 }
 
 void launch_exti_ub(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF, const int* scount,
