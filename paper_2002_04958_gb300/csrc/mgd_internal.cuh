@@ -354,9 +354,9 @@ void launch_perm_rows_fill(int n, const int* perm, const int* rp, const int* ci,
                            int* pci, double* pv, cudaStream_t s);
 void launch_interp_count(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF, int* cnt,
                          int* isc, cudaStream_t s);
-void launch_interp_fill(int n, const int* rp, const int* ci, const double* v, const uint8_t* S,
-                        const signed char* CF, const int* cidx, const int* prp, int* pci, double* pv,
-                        cudaStream_t s);
+void launch_interp_fill(int n, int nnz, const int* rp, const int* ci, const double* v, const uint8_t* S,
+                        const signed char* CF, const int* cidx, const int* prp, int nnzp, int* pci, double* pv,
+                        const double* dg, int* work_i, double* work_d, cudaStream_t s);
 void launch_exti_ub(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF, const int* scount,
                     int* ub, cudaStream_t s);
 void launch_exti_list(int n, const int* rp, const int* ci, const uint8_t* S, const signed char* CF,
