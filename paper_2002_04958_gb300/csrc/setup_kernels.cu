@@ -1461,17 +1461,21 @@ __global__ void __launch_bounds__(kGjThreads) k_dense_inverse_gj(int n, const do
     __syncthreads();
     for (int i = t; i < n; i += kGjThreads) L[i] = i == k ? 0.0 : __ddiv_rn(A[i * n + k], A[k * n + k]);
     __syncthreads();
-    // every row but k: columns k+1.. of A and all of X
+    // every row but k: columns k+1.. of A and all of X (32 x 32 threads: rows by
+    // thread row, columns by lane)
     const int wa = n - k - 1, w = wa + n;
-    for (int e = t; e < n * w; e += kGjThreads) {
-      int i = e / w, j = e % w;
+    const int ty = t >> 5, tx = t & 31;
+    for (int i = ty; i < n; i += kGjThreads / 32) {
       if (i == k) continue;
-      if (j < wa) {
-        int c = k + 1 + j;
-        A[i * n + c] = __dsub_rn(A[i * n + c], __dmul_rn(L[i], A[k * n + c]));
-      } else {
-        int c = j - wa;
-        X[i * n + c] = __dsub_rn(X[i * n + c], __dmul_rn(L[i], X[k * n + c]));
+      const double li = L[i];
+      for (int j = tx; j < w; j += 32) {
+        if (j < wa) {
+          int c = k + 1 + j;
+          A[i * n + c] = __dsub_rn(A[i * n + c], __dmul_rn(li, A[k * n + c]));
+        } else {
+          int c = j - wa;
+          X[i * n + c] = __dsub_rn(X[i * n + c], __dmul_rn(li, X[k * n + c]));
+        }
       }
     }
     __syncthreads();
