@@ -1,8 +1,12 @@
 """Parity at the full workload sizes, in the launch configuration the bench
 uses (autotuned layouts): the C/F splittings, interpolation and coarse
 operators of every hierarchy bit-exact with the oracle, the FGMRES iteration
-count of the FP64 solve equal to the oracle's (config 2), the FP32-V-cycle
-count within +-1, and the true residual checked independently on the host."""
+count of the FP64 solve equal to the oracle's (configs 2 and 3; for the 3D
+system the oracle's solve is stored under golden/), the FP32-V-cycle count
+within +-1, and the true residual checked independently on the host."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -77,3 +81,32 @@ def test_config2_full_size_iterations(gpu, orc):
     xm, itm, rrm, rcm = mixed.solve(torch.from_numpy(s.b), tol=1e-8)
     assert rcm == 0 and abs(itm - ito) <= 1
     assert np.linalg.norm(s.b - s.scipy() @ xm.cpu().numpy()) <= 1.0000001e-8 * np.linalg.norm(s.b)
+
+
+def test_config3_full_size_hierarchies_iterations_residual(gpu, orc):
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_fgmres_G20_96x96x96_schur2.json")) as f:
+        rec = json.load(f)
+    s = I.preset(3)                      # G = 20, 96 x 96 x 96, 19,464,192 unknowns
+    assert s.n == rec["n"] and s.nnz == rec["nnz"]
+    Ao = orc.csr_of_system(s)
+    ob = orc.Block(Ao, s.G, s.N, "schur2")
+    exact = gpu.Solver(batched=1, use_graph=1, autotune=1).setup_system(s, "schur2")
+    assert _compare_all_levels(exact, ob, orc, "schur2") >= 22 * 5
+    v = np.random.default_rng(2).standard_normal(s.n)
+    z = exact.precond_apply(torch.from_numpy(v)).cpu().numpy()
+    zo = ob.apply(v)
+    assert np.linalg.norm(z - zo) <= 1e-11 * np.linalg.norm(zo)
+    del ob, Ao
+    x, it, rr, rc = exact.solve(torch.from_numpy(s.b), tol=1e-8)
+    assert rc == 0 and it == rec["iterations"] and rr == pytest.approx(rec["relres"], rel=1e-5)
+    xg = x.cpu().numpy()
+    assert abs(np.linalg.norm(xg) - rec["x_norm2"]) <= 1e-10 * rec["x_norm2"]
+    idx = np.asarray(rec["sample_index"])
+    assert np.max(np.abs(xg[idx] - np.asarray(rec["sample_x"]))) <= 1e-10 * rec["x_norm2"]
+    del exact, x
+    # the bench's launch configuration: FP32 V-cycles inside the FP64 FGMRES
+    mixed = gpu.Solver(precision=1, batched=1, use_graph=1, autotune=1).setup_system(s, "schur2")
+    xm, itm, rrm, rcm = mixed.solve(torch.from_numpy(s.b), tol=1e-8)
+    assert rcm == 0 and abs(itm - rec["iterations"]) <= 1
+    res = np.linalg.norm(s.b - s.scipy() @ xm.cpu().numpy()) / np.linalg.norm(s.b)
+    assert res <= 1.0000001e-8 and res == pytest.approx(rrm, rel=1e-6)
