@@ -1020,7 +1020,74 @@ void launch_spgemm_ub(int n, const int* xrp, const int* xci, const int* yrp, int
   MGD_LAUNCH_CHECK();
 }
 
-// One warp per output row, in shared memory for rows with at most
+// One thread per output row, for rows whose result has at most kThrSlots
+// columns: the products are taken in expansion order (k along row i of X,
+// then row k of Y) and each is either added to the entry of its column --
+// __dadd_rn(sum so far, product) -- or inserted as a new entry of a sorted
+// list in shared memory.  Each column's sum thus runs over its products left
+// to right in expansion order, the first product initialising it: the result
+// of the stable sort + run sums below.  Rows with more columns, or more than
+// kThrMaxProducts products, are listed for the warp kernel.
+constexpr int kThrSlots = 32;
+constexpr int kThrRows = 128;
+constexpr int kThrMaxProducts = 1024;
+
+__global__ void __launch_bounds__(kThrRows) k_spgemm_thread(int n, const int* xrp, const int* xci, const double* xv,
+                                                            const int* yrp, const int* yci, const double* yv,
+                                                            const long long* off, int* tc, double* tv, int* cnt,
+                                                            int* wrows, int* nw) {
+  __shared__ int s_c[kThrSlots][kThrRows];
+  __shared__ double s_v[kThrSlots][kThrRows];
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * kThrRows + t;
+  if (i >= n) return;
+  const long long b = off[i];
+  const int L = (int)(off[i + 1] - b);
+  bool over = L > kThrMaxProducts;
+  int u = 0;  // columns so far, ascending in s_c[0 .. u)
+  const int xe = over ? xrp[i] : xrp[i + 1];
+  for (int p = xrp[i]; p < xe && !over; ++p) {
+    const int k = xci[p];
+    const double x = xv[p];
+    const int ye = yrp[k + 1];
+    for (int q = yrp[k]; q < ye; ++q) {
+      const int c = yci[q];
+      const double pr = __dmul_rn(x, yv[q]);
+      int lo = 0, hi = u;  // first entry with column >= c
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_c[mid][t] < c) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo < u && s_c[lo][t] == c) {
+        s_v[lo][t] = __dadd_rn(s_v[lo][t], pr);
+        continue;
+      }
+      if (u == kThrSlots) {
+        over = true;
+        break;
+      }
+      for (int m = u; m > lo; --m) {
+        s_c[m][t] = s_c[m - 1][t];
+        s_v[m][t] = s_v[m - 1][t];
+      }
+      s_c[lo][t] = c;
+      s_v[lo][t] = pr;
+      ++u;
+    }
+  }
+  if (over) {
+    wrows[atomicAdd(nw, 1)] = i;
+    return;
+  }
+  for (int m = 0; m < u; ++m) {
+    tc[b + m] = s_c[m][t];
+    tv[b + m] = s_v[m][t];
+  }
+  cnt[i] = u;
+}
+
+// One warp per listed output row, in shared memory for rows with at most
 // kWarpProducts products: products are expanded in order (k along row i of X,
 // then row k of Y), ranked by a stable counting sort on the column (ties keep
 // their expansion order), and each run of equal columns is summed left to
@@ -1032,17 +1099,10 @@ constexpr int kSpgWarps = 4;
 constexpr int kLongProducts = 8192;
 constexpr int kLongThreads = 1024;
 
-__global__ void __launch_bounds__(32 * kSpgWarps) k_spgemm_warp(int n, const int* xrp, const int* xci,
-                                                                const double* xv, const int* yrp, const int* yci,
-                                                                const double* yv, const long long* off, int* tc,
-                                                                double* tv, int* cnt, int* longrows, int* nlong) {
-  __shared__ int s_col[kSpgWarps][kWarpProducts];
-  __shared__ double s_val[kSpgWarps][kWarpProducts];
-  __shared__ int s_scol[kSpgWarps][kWarpProducts];
-  __shared__ double s_sval[kSpgWarps][kWarpProducts];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kSpgWarps + warp;
-  if (i >= n) return;  // whole warp
+__device__ __forceinline__ void spgemm_warp_row(int i, int lane, const int* xrp, const int* xci, const double* xv,
+                                                const int* yrp, const int* yci, const double* yv,
+                                                const long long* off, int* tc, double* tv, int* cnt, int* longrows,
+                                                int* nlong, int* col, double* val, int* scol, double* sval) {
   const long long b = off[i];
   const int L = (int)(off[i + 1] - b);
   if (L > kWarpProducts && L <= kLongProducts) {
@@ -1091,10 +1151,6 @@ __global__ void __launch_bounds__(32 * kSpgWarps) k_spgemm_warp(int n, const int
     cnt[i] = (int)(w - b);
     return;
   }
-  int* col = s_col[warp];
-  double* val = s_val[warp];
-  int* scol = s_scol[warp];
-  double* sval = s_sval[warp];
   // expansion: lane t takes entry t of a 32-entry chunk of row i of X; a warp
   // prefix sum of the Y row lengths places each lane's products, so the
   // expansion order (k along row i, then row k of Y) is unchanged
@@ -1154,6 +1210,23 @@ __global__ void __launch_bounds__(32 * kSpgWarps) k_spgemm_warp(int n, const int
   }
   if (lane == 0) cnt[i] = base;
 }
+
+__global__ void __launch_bounds__(32 * kSpgWarps) k_spgemm_warp(const int* xrp, const int* xci, const double* xv,
+                                                                const int* yrp, const int* yci, const double* yv,
+                                                                const long long* off, int* tc, double* tv, int* cnt,
+                                                                const int* wrows, const int* nw, int* longrows,
+                                                                int* nlong) {
+  __shared__ int s_col[kSpgWarps][kWarpProducts];
+  __shared__ double s_val[kSpgWarps][kWarpProducts];
+  __shared__ int s_scol[kSpgWarps][kWarpProducts];
+  __shared__ double s_sval[kSpgWarps][kWarpProducts];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nrows = *nw;
+  for (int w = blockIdx.x * kSpgWarps + warp; w < nrows; w += gridDim.x * kSpgWarps)
+    spgemm_warp_row(wrows[w], lane, xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt, longrows, nlong, s_col[warp],
+                    s_val[warp], s_scol[warp], s_sval[warp]);
+}
+
 
 // One block per listed row (kWarpProducts < L <= kLongProducts): products
 // expanded in order into shared memory with the key (column << 32 | position),
@@ -1253,11 +1326,19 @@ __global__ void __launch_bounds__(kLongThreads) k_spgemm_long(const int* xrp, co
 void launch_spgemm_expand(int n, const int* xrp, const int* xci, const double* xv, const int* yrp,
                           const int* yci, const double* yv, const long long* off, int* tc, double* tv, int* cnt,
                           int* work, cudaStream_t s) {
-  // work: n + 1 ints (list of long rows, then their count)
+  // work: 2n + 2 ints (list of long rows, their count, list of the warp
+  // kernel's rows, their count)
   int* nlong = work + n;
+  int* wrows = work + n + 1;
+  int* nw = work + 2 * n + 1;
   MGD_CUDA(cudaMemsetAsync(nlong, 0, sizeof(int), s));
-  k_spgemm_warp<<<cdiv(n, kSpgWarps), 32 * kSpgWarps, 0, s>>>(n, xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt, work,
-                                                               nlong);
+  MGD_CUDA(cudaMemsetAsync(nw, 0, sizeof(int), s));
+  if (n <= 0) return;
+  k_spgemm_thread<<<cdiv(n, kThrRows), kThrRows, 0, s>>>(n, xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt, wrows, nw);
+  MGD_LAUNCH_CHECK();
+  // the listed rows, a grid-stride loop over the list (its length stays on the device)
+  k_spgemm_warp<<<152 * 8, 32 * kSpgWarps, 0, s>>>(xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt, wrows, nw, work,
+                                                    nlong);
   MGD_LAUNCH_CHECK();
   static const size_t smem = (size_t)kLongProducts * (sizeof(unsigned long long) + sizeof(double));
   static const cudaError_t attr =
