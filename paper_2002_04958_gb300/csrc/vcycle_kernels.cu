@@ -19,7 +19,10 @@ namespace mgd {
 // Each phase kernel loads its rows' operator entries (and the smoother
 // diagonal) before the dependency wait -- setup-time data -- and gathers the
 // vector its predecessor wrote only after it.
-constexpr int kPre = 4;  // entries per lane loaded before the wait
+#ifndef MGD_KPRE
+#define MGD_KPRE 5
+#endif
+constexpr int kPre = MGD_KPRE;  // entries per lane loaded before the wait
 
 // PRE: xt = D^-1 b (zero initial guess), r = b - A xt = b - (A D^-1) b, using
 // the column-scaled copy of A so that each nonzero costs one multiply-add
