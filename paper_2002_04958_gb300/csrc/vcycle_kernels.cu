@@ -19,6 +19,11 @@ namespace mgd {
 // Each phase kernel loads its rows' operator entries (and the smoother
 // diagonal) before the dependency wait -- setup-time data -- and gathers the
 // vector its predecessor wrote only after it.
+// threads per CTA of the per-level V-cycle kernels
+#ifndef MGD_VTHREADS
+#define MGD_VTHREADS 256
+#endif
+constexpr int kVThreads = MGD_VTHREADS;
 #ifndef MGD_KPRE
 #define MGD_KPRE 5
 #endif
@@ -27,7 +32,7 @@ constexpr int kPre = MGD_KPRE;  // entries per lane loaded before the wait
 // PRE: xt = D^-1 b (zero initial guess), r = b - A xt = b - (A D^-1) b, using
 // the column-scaled copy of A so that each nonzero costs one multiply-add
 template <typename T, int FMT>
-__global__ void __launch_bounds__(kThreads) k_pre(const LDesc<T>* __restrict__ descs) {
+__global__ void __launch_bounds__(kVThreads) k_pre(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
   constexpr int TPR = FmtTraits<FMT>::tpr;
@@ -53,7 +58,7 @@ __global__ void __launch_bounds__(kThreads) k_pre(const LDesc<T>* __restrict__ d
 
 // POST: x = xt + D^-1 (b - A xt)
 template <typename T, int FMT>
-__global__ void __launch_bounds__(kThreads) k_post(const LDesc<T>* __restrict__ descs) {
+__global__ void __launch_bounds__(kVThreads) k_post(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
   constexpr int TPR = FmtTraits<FMT>::tpr;
@@ -76,7 +81,7 @@ __global__ void __launch_bounds__(kThreads) k_post(const LDesc<T>* __restrict__ 
 // the same lane of K adjacent 32-row slices, so K rows' loads are in flight per
 // thread (the row sums are those of the SELL kernels)
 template <typename T, int K>
-__global__ void __launch_bounds__(kThreads) k_pre_sk(const LDesc<T>* __restrict__ descs) {
+__global__ void __launch_bounds__(kVThreads) k_pre_sk(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -108,7 +113,7 @@ __global__ void __launch_bounds__(kThreads) k_pre_sk(const LDesc<T>* __restrict_
 }
 
 template <typename T, int K>
-__global__ void __launch_bounds__(kThreads) k_post_sk(const LDesc<T>* __restrict__ descs) {
+__global__ void __launch_bounds__(kVThreads) k_post_sk(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -136,7 +141,7 @@ __global__ void __launch_bounds__(kThreads) k_post_sk(const LDesc<T>* __restrict
 
 // RESTRICT: bc = R r ; PROLONG: xt += P xc  (CSR, TPR threads per row)
 template <typename T, int FMT>
-__global__ void __launch_bounds__(kThreads) k_restrict(const LDesc<T>* __restrict__ descs) {
+__global__ void __launch_bounds__(kVThreads) k_restrict(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
   constexpr int TPR = FmtTraits<FMT>::tpr;
@@ -155,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const LDesc<T>* __restric
 }
 
 template <typename T, int FMT>
-__global__ void __launch_bounds__(kThreads) k_prolong(const LDesc<T>* __restrict__ descs) {
+__global__ void __launch_bounds__(kVThreads) k_prolong(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
   constexpr int TPR = FmtTraits<FMT>::tpr;
@@ -206,15 +211,15 @@ __global__ void k_coarse(const LDesc<T>* __restrict__ descs) {
 
 #define MGD_DISPATCH_FMT(K, fmt, maxrows, ny, s, descs)                                        \
   do {                                                                                         \
-    auto g_ = [&](int tpr) { return dim3(cdiv((long long)(maxrows) * tpr + 32, kThreads), (ny)); }; \
+    auto g_ = [&](int tpr) { return dim3(cdiv((long long)(maxrows) * tpr + 32, kVThreads), (ny)); }; \
     switch (fmt) {                                                                             \
-      case FMT_SELL: launch_k(K<T, FMT_SELL>, dim3(g_(1)), dim3(kThreads), 0, s, descs); break;                  \
-      case FMT_CSR1: launch_k(K<T, FMT_CSR1>, dim3(g_(1)), dim3(kThreads), 0, s, descs); break;                  \
-      case FMT_CSR2: launch_k(K<T, FMT_CSR2>, dim3(g_(2)), dim3(kThreads), 0, s, descs); break;                  \
-      case FMT_CSR4: launch_k(K<T, FMT_CSR4>, dim3(g_(4)), dim3(kThreads), 0, s, descs); break;                  \
-      case FMT_CSR8: launch_k(K<T, FMT_CSR8>, dim3(g_(8)), dim3(kThreads), 0, s, descs); break;                  \
-      case FMT_CSR16: launch_k(K<T, FMT_CSR16>, dim3(g_(16)), dim3(kThreads), 0, s, descs); break;               \
-      default: launch_k(K<T, FMT_CSR32>, dim3(g_(32)), dim3(kThreads), 0, s, descs); break;                      \
+      case FMT_SELL: launch_k(K<T, FMT_SELL>, dim3(g_(1)), dim3(kVThreads), 0, s, descs); break;                  \
+      case FMT_CSR1: launch_k(K<T, FMT_CSR1>, dim3(g_(1)), dim3(kVThreads), 0, s, descs); break;                  \
+      case FMT_CSR2: launch_k(K<T, FMT_CSR2>, dim3(g_(2)), dim3(kVThreads), 0, s, descs); break;                  \
+      case FMT_CSR4: launch_k(K<T, FMT_CSR4>, dim3(g_(4)), dim3(kVThreads), 0, s, descs); break;                  \
+      case FMT_CSR8: launch_k(K<T, FMT_CSR8>, dim3(g_(8)), dim3(kVThreads), 0, s, descs); break;                  \
+      case FMT_CSR16: launch_k(K<T, FMT_CSR16>, dim3(g_(16)), dim3(kVThreads), 0, s, descs); break;               \
+      default: launch_k(K<T, FMT_CSR32>, dim3(g_(32)), dim3(kVThreads), 0, s, descs); break;                      \
     }                                                                                          \
   } while (0)
 
@@ -225,27 +230,27 @@ void launch_phase(int phase, int fmtA, int fmtRP, const LDesc<T>* d_descs, int n
   switch (phase) {
     case PH_PRE:
       if (fmtA == FMT_SELL2)
-        launch_k(k_pre_sk<T, 2>, dim3(cdiv((long long)cdiv(maxrows, 64) * 32, kThreads), ndesc), dim3(kThreads), 0,
+        launch_k(k_pre_sk<T, 2>, dim3(cdiv((long long)cdiv(maxrows, 64) * 32, kVThreads), ndesc), dim3(kVThreads), 0,
                  s, d_descs);
       else if (fmtA == FMT_SELL4)
-        launch_k(k_pre_sk<T, 4>, dim3(cdiv((long long)cdiv(maxrows, 128) * 32, kThreads), ndesc), dim3(kThreads), 0,
+        launch_k(k_pre_sk<T, 4>, dim3(cdiv((long long)cdiv(maxrows, 128) * 32, kVThreads), ndesc), dim3(kVThreads), 0,
                  s, d_descs);
       else
         MGD_DISPATCH_FMT(k_pre, fmtA, maxrows, ndesc, s, d_descs);
       break;
     case PH_POST:
       if (fmtA == FMT_SELL2)
-        launch_k(k_post_sk<T, 2>, dim3(cdiv((long long)cdiv(maxrows, 64) * 32, kThreads), ndesc), dim3(kThreads), 0,
+        launch_k(k_post_sk<T, 2>, dim3(cdiv((long long)cdiv(maxrows, 64) * 32, kVThreads), ndesc), dim3(kVThreads), 0,
                  s, d_descs);
       else if (fmtA == FMT_SELL4)
-        launch_k(k_post_sk<T, 4>, dim3(cdiv((long long)cdiv(maxrows, 128) * 32, kThreads), ndesc), dim3(kThreads), 0,
+        launch_k(k_post_sk<T, 4>, dim3(cdiv((long long)cdiv(maxrows, 128) * 32, kVThreads), ndesc), dim3(kVThreads), 0,
                  s, d_descs);
       else
         MGD_DISPATCH_FMT(k_post, fmtA, maxrows, ndesc, s, d_descs);
       break;
     case PH_RESTRICT: MGD_DISPATCH_FMT(k_restrict, rp, maxrows, ndesc, s, d_descs); break;
     case PH_PROLONG: MGD_DISPATCH_FMT(k_prolong, rp, maxrows, ndesc, s, d_descs); break;
-    case PH_JAC1: launch_k(k_jac1<T>, dim3(dim3(cdiv(maxrows, kThreads), ndesc)), dim3(kThreads), 0, s, d_descs); break;
+    case PH_JAC1: launch_k(k_jac1<T>, dim3(dim3(cdiv(maxrows, kVThreads), ndesc)), dim3(kVThreads), 0, s, d_descs); break;
     case PH_COARSE:
       // one 1024-thread CTA per subsystem: a warp per row of the dense inverse
       launch_k(k_coarse<T>, dim3(dim3(1, ndesc)), dim3(1024), sizeof(double) * maxrows, s, d_descs);
@@ -278,7 +283,7 @@ __global__ void k_gs_first(const LDesc<T>* __restrict__ descs) {
 // rows; position q of the sweep is row perm[q]); the CSR formats read A's
 // rows through perm with TPR threads per row.
 template <typename T, int FMT>
-__global__ void __launch_bounds__(kThreads) k_gs_sweep(const LDesc<T>* __restrict__ descs, int t, int up) {
+__global__ void __launch_bounds__(kVThreads) k_gs_sweep(const LDesc<T>* __restrict__ descs, int t, int up) {
   MGD_PDL_ENTRY();
   const LDesc<T>* d = descs + blockIdx.y;
   MGD_SKIP_INACTIVE(d);
@@ -302,7 +307,7 @@ __global__ void __launch_bounds__(kThreads) k_gs_sweep(const LDesc<T>* __restric
 
 // r = b - A xt after the down sweeps (the level's A layout)
 template <typename T, int FMT>
-__global__ void __launch_bounds__(kThreads) k_gs_resid(const LDesc<T>* __restrict__ descs) {
+__global__ void __launch_bounds__(kVThreads) k_gs_resid(const LDesc<T>* __restrict__ descs) {
   MGD_PDL_TRIGGER();
   const LDesc<T>* d = descs + blockIdx.y;
   constexpr int TPR = FmtTraits<FMT>::tpr;
@@ -323,20 +328,20 @@ __global__ void __launch_bounds__(kThreads) k_gs_resid(const LDesc<T>* __restric
 template <typename T>
 void launch_gs_first(const LDesc<T>* d, int nd, int maxrows, cudaStream_t s) {
   if (nd <= 0 || maxrows <= 0) return;
-  launch_k(k_gs_first<T>, dim3(cdiv(maxrows, kThreads), nd), dim3(kThreads), 0, s, d);
+  launch_k(k_gs_first<T>, dim3(cdiv(maxrows, kVThreads), nd), dim3(kVThreads), 0, s, d);
   MGD_LAUNCH_CHECK();
 }
 
 template <typename T>
 void launch_gs_sweep(int fmt, const LDesc<T>* d, int nd, int maxrows, int t, int up, cudaStream_t s) {
   if (nd <= 0 || maxrows <= 0) return;
-  auto g = [&](int tpr) { return dim3(cdiv((long long)maxrows * tpr + 32, kThreads), nd); };
+  auto g = [&](int tpr) { return dim3(cdiv((long long)maxrows * tpr + 32, kVThreads), nd); };
   switch (fmt) {
-    case FMT_SELL: launch_k(k_gs_sweep<T, FMT_SELL>, g(1), dim3(kThreads), 0, s, d, t, up); break;
-    case FMT_CSR1: launch_k(k_gs_sweep<T, FMT_CSR1>, g(1), dim3(kThreads), 0, s, d, t, up); break;
-    case FMT_CSR2: launch_k(k_gs_sweep<T, FMT_CSR2>, g(2), dim3(kThreads), 0, s, d, t, up); break;
-    case FMT_CSR4: launch_k(k_gs_sweep<T, FMT_CSR4>, g(4), dim3(kThreads), 0, s, d, t, up); break;
-    default: launch_k(k_gs_sweep<T, FMT_CSR8>, g(8), dim3(kThreads), 0, s, d, t, up); break;
+    case FMT_SELL: launch_k(k_gs_sweep<T, FMT_SELL>, g(1), dim3(kVThreads), 0, s, d, t, up); break;
+    case FMT_CSR1: launch_k(k_gs_sweep<T, FMT_CSR1>, g(1), dim3(kVThreads), 0, s, d, t, up); break;
+    case FMT_CSR2: launch_k(k_gs_sweep<T, FMT_CSR2>, g(2), dim3(kVThreads), 0, s, d, t, up); break;
+    case FMT_CSR4: launch_k(k_gs_sweep<T, FMT_CSR4>, g(4), dim3(kVThreads), 0, s, d, t, up); break;
+    default: launch_k(k_gs_sweep<T, FMT_CSR8>, g(8), dim3(kVThreads), 0, s, d, t, up); break;
   }
   MGD_LAUNCH_CHECK();
 }
