@@ -1078,9 +1078,12 @@ struct InvOp {
 };
 
 struct Step {
-  enum { PRODUCE, INVERT, CONSUME, BLOCKRESID } type;
+  // CONSPROD: a CONSUME (descs, nd) fused with the PRODUCE after it (descs2, nd2)
+  enum { PRODUCE, INVERT, CONSUME, BLOCKRESID, CONSPROD } type;
   void* descs = nullptr;  // device descriptors
   int nd = 0;
+  void* descs2 = nullptr;
+  int nd2 = 0;
   int len = 0;            // vector length of produce/consume
   std::vector<int> ops;   // INVERT
   int batch = -1;         // index into batches when batched
@@ -1510,6 +1513,13 @@ static void run_step(mgd_ctx* c, const Step& st, bool trans) {
         c->prof.end(id, 4, st.bytes, c->s);
         break;
       }
+      case Step::CONSPROD: {
+        int id = c->prof.begin(c->s, 4);
+        launch_consume_produce<T>((const ConsumeDesc<T>*)st.descs, st.nd, (const ProduceDesc<T>*)st.descs2, st.nd2,
+                                  st.len, c->io, c->s);
+        c->prof.end(id, 4, st.bytes, c->s);
+        break;
+      }
       case Step::INVERT:
         run_invert<T>(c, st, trans);
         break;
@@ -1723,6 +1733,23 @@ static void build_program(mgd_ctx* c) {
       break;
     }
   }
+  // a CONSUME and the PRODUCE right after it run as one elementwise kernel
+  std::vector<Step> fused;
+  for (size_t i = 0; i < S.size(); ++i) {
+    if (i + 1 < S.size() && S[i].type == Step::CONSUME && S[i + 1].type == Step::PRODUCE && S[i].batch == -1 &&
+        S[i + 1].batch == -1 && S[i].len == S[i + 1].len) {
+      Step f = S[i];
+      f.type = Step::CONSPROD;
+      f.descs2 = S[i + 1].descs;
+      f.nd2 = S[i + 1].nd;
+      f.bytes = S[i].bytes + S[i + 1].bytes;
+      fused.push_back(f);
+      ++i;
+      continue;
+    }
+    fused.push_back(S[i]);
+  }
+  S = fused;
 }
 
 }  // namespace mgd

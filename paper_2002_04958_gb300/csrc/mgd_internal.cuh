@@ -416,6 +416,9 @@ void launch_produce(const ProduceDesc<T>* d, int nd, int N, const IOSlots* io, c
 template <typename T>
 void launch_consume(const ConsumeDesc<T>* d, int nd, int N, const IOSlots* io, cudaStream_t s);
 template <typename T>
+void launch_consume_produce(const ConsumeDesc<T>* cd, int ncd, const ProduceDesc<T>* pd, int npd, int N,
+                            const IOSlots* io, cudaStream_t s);
+template <typename T>
 void launch_jacobi(const JacDesc<T>* d, int nd, int N, cudaStream_t s);
 template <typename T>
 void launch_residual(int fmt, int n, const int* rp, const int* ci, const T* v, const int* sptr, const int* sci,

@@ -50,6 +50,51 @@ __global__ void k_consume(const ConsumeDesc<T>* __restrict__ ds, int N, const IO
   dst[k] = base ? base[k] + val : val;
 }
 
+// A CONSUME step followed by a PRODUCE step, fused: per element, every
+// consume descriptor, then every produce descriptor.  Both are elementwise,
+// so a produce term that reads a vector the consume just wrote reads it back
+// at the same index in the same thread (the data pointers are not restrict:
+// the compiler keeps the store before the load).
+template <typename T>
+__global__ void k_consume_produce(const ConsumeDesc<T>* __restrict__ cd, int ncd, const ProduceDesc<T>* __restrict__ pd,
+                                  int npd, int N, const IOSlots* __restrict__ io) {
+  MGD_PDL_ENTRY();
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  for (int j = 0; j < ncd; ++j) {
+    const ConsumeDesc<T>* d = cd + j;
+    double* dst = resolve(d->dst, io);
+    const double* base = resolve(d->base, io);
+    double val = d->s * (double)d->x[k];
+    dst[k] = base ? base[k] + val : val;
+  }
+  for (int j = 0; j < npd; ++j) {
+    const ProduceDesc<T>* d = pd + j;
+    const double* a = resolve(d->a, io);
+    double acc = a ? a[k] : 0.0;
+    int nt = d->nt;
+    for (int t = 0; t < nt; ++t) {
+      const double* w = resolve(d->w[t], io);
+      double term = w[k];
+      if (d->d[t]) term *= d->d[t][k];
+      acc += d->s[t] * term;
+    }
+    d->dst[k] = (T)acc;
+  }
+}
+
+template <typename T>
+void launch_consume_produce(const ConsumeDesc<T>* cd, int ncd, const ProduceDesc<T>* pd, int npd, int N,
+                            const IOSlots* io, cudaStream_t s) {
+  if (N <= 0) return;
+  launch_k(k_consume_produce<T>, dim3(cdiv(N, kThreads)), dim3(kThreads), 0, s, cd, ncd, pd, npd, N, io);
+  MGD_LAUNCH_CHECK();
+}
+template void launch_consume_produce<double>(const ConsumeDesc<double>*, int, const ProduceDesc<double>*, int, int,
+                                             const IOSlots*, cudaStream_t);
+template void launch_consume_produce<float>(const ConsumeDesc<float>*, int, const ProduceDesc<float>*, int, int,
+                                            const IOSlots*, cudaStream_t);
+
 template <typename T>
 __global__ void k_jacobi(const JacDesc<T>* __restrict__ ds, int N) {
   MGD_PDL_ENTRY();
