@@ -2093,15 +2093,13 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
   // validation
   {
     Scratch sc(s);
-    int* flags = sc.alloc<int>(3);
-    MGD_CUDA(cudaMemsetAsync(flags, 0, 3 * sizeof(int), s));
+    int* flags = sc.alloc<int>(4);
+    MGD_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), s));
     launch_validate(n, nnz, N, nc, rp, ci, v, flags, s);
-    int hf[3];
+    int hf[4];
     MGD_CUDA(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
     MGD_CUDA(cudaStreamSynchronize(s));
-    int r0 = read_int(rp, s);
-    int rn = read_int(rp + n, s);
-    if (r0 != 0 || rn != nnz) throw Error{MGD_EINVAL, "row pointer does not span [0, nnz]"};
+    if (hf[3]) throw Error{MGD_EINVAL, "row pointer does not span [0, nnz]"};
     if (hf[0]) throw Error{MGD_EINVAL, "column index out of range, unsorted or duplicated"};
     if (hf[1]) throw Error{MGD_EINVAL, "off-block entry couples different cells (D_ab must be diagonal)"};
     if (hf[2]) throw Error{MGD_EINVAL, "missing or non-positive diagonal entry"};
@@ -2157,8 +2155,17 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
     int* bci = c->ar.alloc<int>(tot);
     double* bv = c->ar.alloc<double>(tot);
     launch_block_fill(n, N, nc, c->A.rp, c->A.ci, c->A.v, brp, bci, bv, dtab, s);
-    std::vector<int> hbrp(n + 1);
-    MGD_CUDA(cudaMemcpyAsync(hbrp.data(), brp, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s));
+    // each block's row pointer is made on the device; only the nc + 1 block
+    // boundaries come back to the host
+    std::vector<int*> hrps(nc);
+    for (int a = 0; a < nc; ++a) hrps[a] = c->ar.alloc<int>(N + 1);
+    int** drps = sc.alloc<int*>(nc);
+    MGD_CUDA(cudaMemcpyAsync(drps, hrps.data(), sizeof(int*) * nc, cudaMemcpyHostToDevice, s));
+    launch_block_rowptr(N, nc, brp, drps, s);
+    int* bounds = sc.alloc<int>(nc + 1);
+    launch_block_bounds(N, nc, brp, bounds, s);
+    std::vector<int> hb(nc + 1);
+    MGD_CUDA(cudaMemcpyAsync(hb.data(), bounds, sizeof(int) * (nc + 1), cudaMemcpyDeviceToHost, s));
     MGD_CUDA(cudaStreamSynchronize(s));
     bd.Ab.resize(nc);
     bd.diag.resize(nc);
@@ -2166,15 +2173,10 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
       Csr B;
       B.n = N;
       B.m = N;
-      int off = hbrp[(size_t)a * N];
-      B.nnz = hbrp[(size_t)(a + 1) * N] - off;
-      B.rp = c->ar.alloc<int>(N + 1);
-      std::vector<int> lrp(N + 1);
-      for (int k = 0; k <= N; ++k) lrp[k] = hbrp[(size_t)a * N + k] - off;
-      MGD_CUDA(cudaMemcpyAsync(B.rp, lrp.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, s));
-      B.ci = bci + off;
-      B.v = bv + off;
-      MGD_CUDA(cudaStreamSynchronize(s));
+      B.nnz = hb[a + 1] - hb[a];
+      B.rp = hrps[a];
+      B.ci = bci + hb[a];
+      B.v = bv + hb[a];
       bd.Ab[a] = B;
       bd.diag[a] = c->ar.alloc<double>(N);
       launch_diag_extract(N, B.rp, B.ci, B.v, bd.diag[a], s);

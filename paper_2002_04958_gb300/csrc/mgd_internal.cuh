@@ -321,6 +321,8 @@ int read_int(const int* d, cudaStream_t s);
 void launch_validate(int n, int nnz, int N, int nc, const int* rp, const int* ci, const double* v, int* flags,
                      cudaStream_t s);
 void launch_block_count(int n, int N, int nc, const int* rp, const int* ci, int* cnt, int* pairs, cudaStream_t s);
+void launch_block_rowptr(int N, int nc, const int* brp, int* const* rps, cudaStream_t s);
+void launch_block_bounds(int N, int nc, const int* brp, int* out, cudaStream_t s);
 void launch_block_fill(int n, int N, int nc, const int* rp, const int* ci, const double* v, const int* brp,
                        int* bci, double* bv, double** dtab, cudaStream_t s);
 void launch_diag_extract(int n, const int* rp, const int* ci, const double* v, double* d, cudaStream_t s);

@@ -143,13 +143,23 @@ int read_int(const int* d, cudaStream_t s) {
 // ------------------------------------------------------------------ validation and block extraction
 // flags[0]: bad column (out of range / unsorted / duplicate); flags[1]: coupling
 // not in the same cell; flags[2]: non-positive or missing diagonal
-__global__ void k_validate(int n, int N, int nc, const int* rp, const int* ci, const double* v, int* flags) {
+// flags: 0 column out of range / unsorted / duplicated, 1 off-block entry
+// outside its cell, 2 missing or non-positive diagonal, 3 row pointer not a
+// non-decreasing map onto [0, nnz] (the row's entries are then not read)
+__global__ void k_validate(int n, int nnz, int N, int nc, const int* rp, const int* ci, const double* v, int* flags) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (i == 0 && rp[0] != 0) atomicOr(&flags[3], 1);
+  if (i == n - 1 && rp[n] != nnz) atomicOr(&flags[3], 1);
+  const int rb = rp[i], re = rp[i + 1];
+  if (rb < 0 || re < rb || re > nnz) {
+    atomicOr(&flags[3], 1);
+    return;
+  }
   int a = i / N, k = i - a * N;
   int prev = -1;
   bool diag = false;
-  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+  for (int p = rb; p < re; ++p) {
     int j = ci[p];
     if (j < 0 || j >= n || j <= prev) atomicOr(&flags[0], 1);
     prev = j;
@@ -165,9 +175,7 @@ __global__ void k_validate(int n, int N, int nc, const int* rp, const int* ci, c
 
 void launch_validate(int n, int nnz, int N, int nc, const int* rp, const int* ci, const double* v, int* flags,
                      cudaStream_t s) {
-  (void)nnz;
-  (void)nc;
-  k_validate<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, N, nc, rp, ci, v, flags);
+  k_validate<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, nnz, N, nc, rp, ci, v, flags);
   MGD_LAUNCH_CHECK();
 }
 
@@ -215,6 +223,32 @@ __global__ void k_block_fill(int n, int N, int nc, const int* rp, const int* ci,
 void launch_block_fill(int n, int N, int nc, const int* rp, const int* ci, const double* v, const int* brp,
                        int* bci, double* bv, double** dtab, cudaStream_t s) {
   k_block_fill<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, N, nc, rp, ci, v, brp, bci, bv, dtab);
+  MGD_LAUNCH_CHECK();
+}
+
+// row pointers of every diagonal block from the block-major row pointer brp
+// of the concatenated blocks: rp_a[k] = brp[a N + k] - brp[a N]
+__global__ void k_block_rowptr(int N, int nc, const int* brp, int* const* rps) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)nc * (N + 1)) return;
+  int a = (int)(g / (N + 1)), k = (int)(g % (N + 1));
+  rps[a][k] = brp[(long long)a * N + k] - brp[(long long)a * N];
+}
+
+void launch_block_rowptr(int N, int nc, const int* brp, int* const* rps, cudaStream_t s) {
+  long long tot = (long long)nc * (N + 1);
+  k_block_rowptr<<<cdiv(tot, kThreads), kThreads, 0, s>>>(N, nc, brp, rps);
+  MGD_LAUNCH_CHECK();
+}
+
+// the block boundaries brp[a N], a = 0 .. nc
+__global__ void k_block_bounds(int N, int nc, const int* brp, int* out) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a <= nc) out[a] = brp[(long long)a * N];
+}
+
+void launch_block_bounds(int N, int nc, const int* brp, int* out, cudaStream_t s) {
+  k_block_bounds<<<cdiv(nc + 1, kThreads), kThreads, 0, s>>>(N, nc, brp, out);
   MGD_LAUNCH_CHECK();
 }
 

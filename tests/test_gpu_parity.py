@@ -246,6 +246,18 @@ def test_edge_cases(gpu):
     with pytest.raises(MgdError):
         gpu.Solver().setup(s.G, s.N, torch.from_numpy(s.rowptr), torch.from_numpy(badc_sorted),
                            torch.from_numpy(s.val), "bd")
+    # row pointers: last entry short of nnz, and a decreasing pair (every
+    # entry the validation reads stays inside the arrays)
+    for k in ["short", "decreasing"]:
+        badr = s.rowptr.copy()
+        if k == "short":
+            badr[-1] -= 1
+        else:
+            badr[5], badr[6] = badr[6], badr[5]
+        with pytest.raises(MgdError) as e:
+            gpu.Solver().setup(s.G, s.N, torch.from_numpy(badr), torch.from_numpy(s.col), torch.from_numpy(s.val),
+                               "amg")
+        assert e.value.code == 1 and "row pointer" in str(e.value), k
 
 
 def test_solve_host_buffers(gpu, orc):
