@@ -408,8 +408,7 @@ static bool coarsen_pass(SetupCtx& sc, const Csr& A, int lid, Scratch* keep, Pas
   launch_count_st(n, A.rp, A.ci, S, cnt, s);
   int* strp = tmp.alloc<int>(n + 1);
   exclusive_scan(cnt, strp, n, s);
-  int nst = read_int(strp + n, s);
-  int* stci = tmp.alloc<int>(nst);
+  int* stci = tmp.alloc<int>(A.nnz);  // at most every entry is strong: no read-back of the count
   int* cur = tmp.alloc<int>(n);
   MGD_CUDA(cudaMemsetAsync(cur, 0, sizeof(int) * n, s));
   launch_fill_st(n, A.rp, A.ci, S, strp, cur, stci, s);
@@ -434,6 +433,18 @@ static bool coarsen_pass(SetupCtx& sc, const Csr& A, int lid, Scratch* keep, Pas
   launch_interp_count(n, A.rp, A.ci, S, CF, pcnt, isc, s);
   int* cidx = tmp.alloc<int>(n + 1);
   exclusive_scan(isc, cidx, n, s);
+  // extended+i: upper bounds of the distance-two interpolatory sets, read
+  // back with the coarse count in one synchronisation
+  int* ub = nullptr;
+  long long* off = nullptr;
+  long long tot = 0;
+  if (o.interp_type == 1) {
+    ub = tmp.alloc<int>(n);
+    launch_exti_ub(n, A.rp, A.ci, S, CF, pcnt, ub, s);
+    off = tmp.alloc<long long>(n + 1);
+    launch_offsets64(ub, off, n, s);
+    MGD_CUDA(cudaMemcpyAsync(&tot, off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  }
   int nc = read_int(cidx + n, s);
   if (nc == 0 || nc == n) return false;
   Csr P;
@@ -441,13 +452,6 @@ static bool coarsen_pass(SetupCtx& sc, const Csr& A, int lid, Scratch* keep, Pas
   P.m = nc;
   P.rp = keep ? keep->alloc<int>(n + 1) : ar.alloc<int>(n + 1);
   if (o.interp_type == 1) {  // extended+i: distance-two interpolatory sets
-    int* ub = tmp.alloc<int>(n);
-    launch_exti_ub(n, A.rp, A.ci, S, CF, pcnt, ub, s);
-    long long* off = tmp.alloc<long long>(n + 1);
-    launch_offsets64(ub, off, n, s);
-    long long tot = 0;
-    MGD_CUDA(cudaMemcpyAsync(&tot, off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    MGD_CUDA(cudaStreamSynchronize(s));
     int* list = tmp.alloc<int>(tot);
     int* len = tmp.alloc<int>(n);
     launch_exti_list(n, A.rp, A.ci, S, CF, off, list, len, s);
@@ -2453,9 +2457,9 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
   c->ready = true;
 }
 
-// Right-preconditioned FGMRES(m) with classical Gram-Schmidt applied twice
-// (CGS2); the small Hessenberg problem and its Givens rotations are solved on
-// the host in FP64 from one device-to-host copy per iteration.
+// Right-preconditioned FGMRES(m) (Saad 1993) with modified Gram-Schmidt
+// Arnoldi on the device; the small Hessenberg problem and its Givens rotations
+// are solved on the host in FP64 from one device-to-host copy per iteration.
 static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans, int* iters, double* relres) {
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = c->s;

@@ -141,8 +141,6 @@ int read_int(const int* d, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ validation and block extraction
-// flags[0]: bad column (out of range / unsorted / duplicate); flags[1]: coupling
-// not in the same cell; flags[2]: non-positive or missing diagonal
 // flags: 0 column out of range / unsorted / duplicated, 1 off-block entry
 // outside its cell, 2 missing or non-positive diagonal, 3 row pointer not a
 // non-decreasing map onto [0, nnz] (the row's entries are then not read)
