@@ -208,6 +208,10 @@ def run_ours(args):
     h_b = torch.from_numpy(sysm.b).pin_memory()
     h_x = torch.zeros(sysm.n, dtype=torch.float64).pin_memory()
     d_rp, d_ci, d_va = torch.empty_like(rp), torch.empty_like(ci), torch.empty_like(va)
+    # the adjoint step also returns the value gradient: x goes back to the
+    # device for the transposed solve, the gradient comes to the host
+    d_x = torch.empty(sysm.n, dtype=torch.float64, device=dev) if args.adjoint else None
+    h_g = torch.empty(sysm.nnz, dtype=torch.float64).pin_memory() if args.adjoint else None
     e2e_ms = []
     for k in range(0 if args.no_e2e else max(2, args.steps // 2) + 1):
         torch.cuda.synchronize()
@@ -218,11 +222,18 @@ def run_ours(args):
         slv.setup(sysm.G, sysm.N, d_rp, d_ci, d_va, args.kind)
         h_x.zero_()
         slv.solve_host_ptr(h_b.data_ptr(), h_x.data_ptr(), tol=args.tol)
+        if args.adjoint:
+            d_x.copy_(h_x, non_blocking=True)
+            lam_e, _, _ = slv.solve_transpose(2.0 * d_x, tol=args.tol)
+            h_g.copy_(slv.grad_values(d_x, lam_e), non_blocking=True)
         torch.cuda.synchronize()
         if k > 0:
             e2e_ms.append((time.perf_counter() - t_a) * 1e3)
     h2d = sysm.rowptr.nbytes + sysm.col.nbytes + sysm.val.nbytes + sysm.b.nbytes + sysm.n * 8
     d2h = sysm.n * 8
+    if args.adjoint:
+        h2d += sysm.n * 8
+        d2h += sysm.nnz * 8
 
     # variants for context (one solve each, outside the timed region)
     variants = {}

@@ -77,7 +77,10 @@ typedef struct mgd_opts {
   int precision;          /* 0: FP64 V-cycles; 1: FP32 V-cycles (storage and arithmetic) inside FP64 FGMRES */
   int batched;            /* 1: independent V-cycles of a stage run as one launch per level and phase */
   int use_graph;          /* 1: the preconditioner apply is replayed from a captured CUDA graph */
-  int autotune;           /* 1: time sparse-kernel variants per level at setup and keep the fastest */
+  int autotune;           /* 1: time sparse-kernel variants per level at setup and keep the fastest; the
+                             decisions are cached per process by hierarchy shape and, when the environment
+                             variable MGD_TUNE_CACHE names a file, read from and written to that file, so
+                             that another process (a profiler run, the next job) runs the same plan */
   int keep_transpose;     /* 1: keep A_l^T per level so that mgd_solve_transpose can run */
   int fuse_rows;          /* levels below level 0 whose subsystems all have <= fuse_rows rows run, with every
                              coarser level, in one thread-block-cluster launch per V-cycle; 0: chosen by the

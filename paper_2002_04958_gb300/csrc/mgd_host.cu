@@ -10,11 +10,16 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <cstdlib>
+#include <fstream>
 #include <map>
+#include <sstream>
 #include <memory>
 #include <string>
 #include <thread>
 #include <vector>
+
+#include <unistd.h>
 
 #include "../../include/mgdamg.h"
 #include "mgd_internal.cuh"
@@ -1800,6 +1805,87 @@ struct TuneResult {
 static std::mutex g_tune_mu;
 static std::map<std::vector<long long>, TuneResult> g_tune_cache;
 
+// With the environment variable MGD_TUNE_CACHE naming a file, the decisions
+// also persist across processes: the file is read at the first lookup and
+// rewritten (through a per-process temporary file and a rename) after every
+// new decision.  One line per entry, fields separated by '|': the key, fmtA,
+// fmtR, fmtP, fmtGS, then tail_level and tail_cs.  Lines that do not parse
+// are skipped.  Callers hold g_tune_mu.
+static bool g_tune_loaded = false;
+
+static const char* tune_file() {
+  const char* p = std::getenv("MGD_TUNE_CACHE");
+  return p && *p ? p : nullptr;
+}
+
+template <typename V>
+static bool parse_ints(const std::string& f, std::vector<V>& out) {
+  std::istringstream is(f);
+  long long x;
+  out.clear();
+  while (is >> x) out.push_back((V)x);
+  return is.eof();
+}
+
+static void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = tune_file();
+  if (!path) return;
+  std::ifstream in(path);
+  std::string line;
+  while (std::getline(in, line)) {
+    std::vector<std::string> f;
+    std::string cur;
+    for (char ch : line) {
+      if (ch == '|') {
+        f.push_back(cur);
+        cur.clear();
+      } else {
+        cur.push_back(ch);
+      }
+    }
+    f.push_back(cur);
+    if (f.size() != 6) continue;
+    std::vector<long long> key;
+    TuneResult r;
+    std::vector<int> tail;
+    if (!parse_ints(f[0], key) || key.empty() || !parse_ints(f[1], r.fmtA) || !parse_ints(f[2], r.fmtR) ||
+        !parse_ints(f[3], r.fmtP) || !parse_ints(f[4], r.fmtGS) || !parse_ints(f[5], tail) || tail.size() != 2)
+      continue;
+    r.tail_level = tail[0];
+    r.tail_cs = tail[1];
+    g_tune_cache[key] = r;
+  }
+}
+
+static void tune_save_locked() {
+  const char* path = tune_file();
+  if (!path) return;
+  std::string tmp = std::string(path) + ".tmp." + std::to_string((long long)getpid());
+  {
+    std::ofstream out(tmp, std::ios::trunc);
+    if (!out) return;
+    auto put = [&](const auto& v) {
+      for (size_t i = 0; i < v.size(); ++i) out << (i ? " " : "") << v[i];
+    };
+    for (const auto& kv : g_tune_cache) {
+      put(kv.first);
+      out << '|';
+      put(kv.second.fmtA);
+      out << '|';
+      put(kv.second.fmtR);
+      out << '|';
+      put(kv.second.fmtP);
+      out << '|';
+      put(kv.second.fmtGS);
+      out << '|' << kv.second.tail_level << ' ' << kv.second.tail_cs << '\n';
+    }
+    if (!out) return;
+  }
+  std::rename(tmp.c_str(), path);
+}
+
 template <typename T>
 static std::vector<long long> tune_key(const VBatch<T>& vb, bool trans, int fuse_rows, bool graph) {
   std::vector<long long> k{(long long)sizeof(T), vb.depth, trans ? 1 : 0, fuse_rows, graph ? 1 : 0};
@@ -1937,6 +2023,7 @@ static void build_batches(mgd_ctx* c) {
     std::vector<long long> key = tune_key<T>(vb, false, c->o.fuse_rows, c->o.use_graph != 0 && c->s != nullptr);
     if (c->o.autotune) {
       std::lock_guard<std::mutex> lk(g_tune_mu);
+      tune_load_locked();
       auto it = g_tune_cache.find(key);
       if (it != g_tune_cache.end() && (int)it->second.fmtA.size() == vb.depth) {
         for (int l = 0; l < vb.depth; ++l) {
@@ -1989,6 +2076,7 @@ static void build_batches(mgd_ctx* c) {
       r.tail_cs = vb.tail_cs;
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tune_cache[key] = r;
+      tune_save_locked();
     }
   }
 }
@@ -2375,6 +2463,7 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
   bool mono_cached = false;
   if (o.autotune) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
     auto it = g_tune_cache.find(mkey);
     if (it != g_tune_cache.end() && !it->second.fmtA.empty()) {
       c->fmtMono = it->second.fmtA[0];
@@ -2407,6 +2496,7 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
     r.tail_level = 0;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[mkey] = r;
+    tune_save_locked();
   }
   capture_graph(c);
   MGD_CUDA(cudaStreamSynchronize(s));

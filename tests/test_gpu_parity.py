@@ -331,3 +331,38 @@ def test_precond_bench_matches_apply(gpu, opts):
     assert torch.equal(z, z2)
     with pytest.raises(gpu.MgdError):
         slv.precond_bench(v, 0)
+
+
+_PLAN_SCRIPT = """
+import json, sys
+sys.path.insert(0, sys.argv[1])
+from paper_2002_04958_gb300 import inputs, mgdamg
+s = inputs.make_system(2, (37, 29), multigroup=True)
+slv = mgdamg.Solver(autotune=1, batched=1, use_graph=1).setup_system(s, "schur2")
+print(json.dumps(slv.plan()))
+"""
+
+
+def test_tune_cache_file(gpu, tmp_path):
+    # autotuner decisions written by one process are read back by another,
+    # which then runs the same plan; lines that do not parse are skipped
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    path = tmp_path / "tune.txt"
+    env = dict(os.environ, MGD_TUNE_CACHE=str(path))
+
+    def run():
+        p = subprocess.run([sys.executable, "-c", _PLAN_SCRIPT, root], env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert p.returncode == 0, p.stderr[-2000:]
+        return json.loads(p.stdout.strip().splitlines()[-1])
+
+    first = run()
+    lines = path.read_text().splitlines()
+    assert lines and all(len(ln.split("|")) == 6 for ln in lines)
+    path.write_text("not a cache line\n" + "\n".join(lines) + "\n")
+    second = run()
+    assert second == first
