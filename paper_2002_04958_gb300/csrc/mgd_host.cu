@@ -262,7 +262,9 @@ static Csr spgemm(Arena& a, const Csr& X, const Csr& Y, cudaStream_t s, Scratch*
   launch_spgemm_ub(n, X.rp, X.ci, Y.rp, ub, s);
   long long* off = sc.alloc<long long>(n + 1);
   launch_offsets64(ub, off, n, s);
-  const long long total = read_ll(off + n, s);
+  long long total = 0;
+  MGD_CUDA(cudaMemcpyAsync(&total, off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  MGD_CUDA(cudaStreamSynchronize(s));
   int* tc = sc.alloc<int>(total);
   double* tv = sc.alloc<double>(total);
   int* cnt = sc.alloc<int>(n);
@@ -436,8 +438,8 @@ static bool coarsen_pass(SetupCtx& sc, const Csr& A, int lid, Scratch* keep, Pas
   launch_interp_count(n, A.rp, A.ci, S, CF, pcnt, isc, s);
   int* cidx = tmp.alloc<int>(n + 1);
   exclusive_scan(isc, cidx, n, s);
-  // extended+i: upper bounds of the distance-two interpolatory sets, queued
-  // with the coarse count so that both come back after one wait
+  // extended+i: upper bounds of the distance-two interpolatory sets, read
+  // back with the coarse count in one synchronisation
   int* ub = nullptr;
   long long* off = nullptr;
   long long tot = 0;
@@ -446,9 +448,9 @@ static bool coarsen_pass(SetupCtx& sc, const Csr& A, int lid, Scratch* keep, Pas
     launch_exti_ub(n, A.rp, A.ci, S, CF, pcnt, ub, s);
     off = tmp.alloc<long long>(n + 1);
     launch_offsets64(ub, off, n, s);
-    tot = read_ll(off + n, s);
+    MGD_CUDA(cudaMemcpyAsync(&tot, off + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
   }
-  int nc = read_int(cidx + n, s);  // no work queued since: no wait
+  int nc = read_int(cidx + n, s);
   if (nc == 0 || nc == n) return false;
   Csr P;
   P.n = n;

@@ -317,7 +317,6 @@ struct InnerCtl {
 // ------------------------------------------------------------------ setup launchers (setup_kernels.cu)
 void exclusive_scan(const int* in, int* out, int n, cudaStream_t s);  // out[0..n], out[n] = total
 int read_int(const int* d, cudaStream_t s);
-long long read_ll(const long long* d, cudaStream_t s);
 
 void launch_validate(int n, int nnz, int N, int nc, const int* rp, const int* ci, const double* v, int* flags,
                      cudaStream_t s);

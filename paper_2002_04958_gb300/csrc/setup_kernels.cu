@@ -133,46 +133,11 @@ void launch_offsets64(const int* cnt, long long* off, int n, cudaStream_t s) {
   scan_rec<long long>(ext, off, n + 1, s, sc);
 }
 
-// Single counters come back through a small pinned buffer per host thread (a
-// pageable destination adds a staging copy to every read-back); the buffer is
-// freed when the thread exits.
-namespace {
-struct PinnedWord {
-  long long* p = nullptr;
-  bool tried = false;
-  ~PinnedWord() {
-    if (p) cudaFreeHost(p);
-  }
-  long long* get() {
-    if (!tried) {
-      tried = true;
-      if (cudaMallocHost(&p, 64) != cudaSuccess) {
-        cudaGetLastError();
-        p = nullptr;
-      }
-    }
-    return p;
-  }
-};
-thread_local PinnedWord tl_word;
-}  // namespace
-
 int read_int(const int* d, cudaStream_t s) {
-  long long* pin = tl_word.get();
   int h = 0;
-  int* dst = pin ? reinterpret_cast<int*>(pin) : &h;
-  MGD_CUDA(cudaMemcpyAsync(dst, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MGD_CUDA(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s));
   MGD_CUDA(cudaStreamSynchronize(s));
-  return pin ? *dst : h;
-}
-
-long long read_ll(const long long* d, cudaStream_t s) {
-  long long* pin = tl_word.get();
-  long long h = 0;
-  long long* dst = pin ? pin : &h;
-  MGD_CUDA(cudaMemcpyAsync(dst, d, sizeof(long long), cudaMemcpyDeviceToHost, s));
-  MGD_CUDA(cudaStreamSynchronize(s));
-  return *dst;
+  return h;
 }
 
 // ------------------------------------------------------------------ validation and block extraction
