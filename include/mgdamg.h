@@ -249,6 +249,23 @@ int mgd_plan_info(mgd_ctx *c, int batch, int level, int *nbatches, int *depth, i
  * preconditioner is launched. */
 int mgd_profile_enable(mgd_ctx *c, int mask);
 int mgd_profile_read(mgd_ctx *c, int cls, long long *launches, double *ms, double *bytes);
+/* The algorithmic FP64 lane operations of the launches class cls recorded
+ * (same classes and synchronisation as mgd_profile_read): one per nonzero and
+ * two per row for the l1-Jacobi smoothing + residual kernels (k_pre, k_post),
+ * one more per row for a stalled coarsest level's first sweep; zero for
+ * FP32 V-cycles, Gauss-Seidel levels and the other kernels.  Together with
+ * mgd_fp64_issue_rate it places the level-0 kernels against the FP64 issue
+ * limit, which on GB300 is as low as the HBM limit for one multiply-add per
+ * 12 bytes.  MGD_EINVAL for a bad class or a null output. */
+int mgd_profile_read_fp64(mgd_ctx *c, int cls, double *fp64_ops);
+/* Measures the device's FP64 multiply-add rate on `stream` (the current
+ * device; a CUDA stream handle or NULL): two launches of 4 x SMs blocks of 512
+ * threads, each thread running four independent chains of 4096 fused
+ * multiply-adds, the second launch timed with CUDA events.  Writes lane
+ * operations per second (every lane active) to *lane_ops_per_s.  Needs no
+ * context; allocates ~2.5 MB stream-ordered and frees it.  MGD_EINVAL for a
+ * null output, MGD_ECUDA when a CUDA call fails. */
+int mgd_fp64_issue_rate(void *stream, double *lane_ops_per_s);
 
 /* Largest n accepted by mgd_relres_noalloc (its fixed work array holds n
  * doubles plus 1216 partial sums: about 4 MiB per GPU, kept until exit). */

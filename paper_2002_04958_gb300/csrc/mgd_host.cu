@@ -48,14 +48,15 @@ struct Profiler {
     int cls;
     cudaEvent_t a, b;
     double bytes;
-    int detail;  // second class (per level and phase), -1 if none
+    int detail;   // second class (per level and phase), -1 if none
+    double fp64;  // algorithmic FP64 lane operations of the bracketed launches
   };
   static constexpr int kClasses = 512;
   std::vector<Pair> pending, graph_pairs;
   bool graph_replayed = false;
   std::vector<cudaEvent_t> pool;
   long long n[kClasses] = {0};
-  double ms[kClasses] = {0}, bytes[kClasses] = {0};
+  double ms[kClasses] = {0}, bytes[kClasses] = {0}, fp64[kClasses] = {0};
   int next_detail = -1;  // detail class of the next begin()
   cudaEvent_t get() {
     if (!pool.empty()) {
@@ -79,11 +80,11 @@ struct Profiler {
     cudaEvent_t a = get();
     record(a, s);
     auto& v = capturing ? graph_pairs : pending;
-    v.push_back({cls, a, nullptr, 0.0, next_detail});
+    v.push_back({cls, a, nullptr, 0.0, next_detail, 0.0});
     next_detail = -1;
     return (int)v.size() - 1;
   }
-  void end(int id, int cls, double by, cudaStream_t s) {
+  void end(int id, int cls, double by, cudaStream_t s, double f64 = 0.0) {
     if (id < 0) return;
     cudaEvent_t b = get();
     record(b, s);
@@ -91,6 +92,7 @@ struct Profiler {
     v[id].cls = cls;
     v[id].b = b;
     v[id].bytes = by;
+    v[id].fp64 = f64;
   }
   void add(const Pair& p) {
     float e = 0;
@@ -98,10 +100,12 @@ struct Profiler {
     n[p.cls]++;
     ms[p.cls] += e;
     bytes[p.cls] += p.bytes;
+    fp64[p.cls] += p.fp64;
     if (p.detail >= 0 && p.detail < kClasses) {
       n[p.detail]++;
       ms[p.detail] += e;
       bytes[p.detail] += p.bytes;
+      fp64[p.detail] += p.fp64;
     }
   }
   // call after the stream has been synchronised
@@ -133,7 +137,7 @@ struct Profiler {
     graph_replayed = false;
     for (int k = 0; k < kClasses; ++k) {
       n[k] = 0;
-      ms[k] = bytes[k] = 0;
+      ms[k] = bytes[k] = fp64[k] = 0;
     }
   }
   ~Profiler() {
@@ -660,6 +664,9 @@ struct VBatch {
     int fmtA = FMT_SELL, fmtR = FMT_CSR4, fmtP = FMT_CSR1;
     double bytes_pre = 0, bytes_post = 0, bytes_restrict = 0, bytes_prolong = 0, bytes_coarse = 0, bytes_jac = 0;
     double bytes_post_cj = 0;  // post-smoothing of the stalled coarsest levels
+    // algorithmic FP64 lane operations (one per nonzero, two per row; FP64
+    // values and l1-Jacobi levels only): the FP64 issue roofline of level 0
+    double fp64_pre = 0, fp64_post = 0, fp64_cj = 0;
     // Gauss-Seidel levels: sweep steps and, per step, the largest class over the subsystems
     bool gs = false;
     int nkmax = 0, fmtGS = FMT_CSR4;  // sweep layout; SELL only where the sweep-ordered copy exists
@@ -783,6 +790,10 @@ static void build_plan(Arena& ar, VBatch<T>& vb, bool trans, cudaStream_t s) {
         } else {
           lp.bytes_pre += sp_bytes(nnz, n, sv) + 4.0 * sv * n;
           lp.bytes_post += sp_bytes(nnz, n, sv) + 4.0 * sv * n;
+          if (sv == 8) {  // k_pre: a multiply-add per nonzero, xt = D^-1 b, r = b - s; k_post likewise
+            lp.fp64_pre += (double)nnz + 2.0 * n;
+            lp.fp64_post += (double)nnz + 2.0 * n;
+          }
         }
         lp.bytes_restrict += sp_bytes(lv.R.nnz, lv.nc, sv) + (double)sv * (n + lv.nc);
         lp.bytes_prolong += sp_bytes(lv.P.nnz, n, sv) + (double)sv * (lv.nc + 2 * n);
@@ -795,6 +806,7 @@ static void build_plan(Arena& ar, VBatch<T>& vb, bool trans, cudaStream_t s) {
         lp.maxcj = std::max<int>(lp.maxcj, (int)n);
         lp.bytes_jac += 3.0 * sv * n;
         lp.bytes_post_cj += sp_bytes(nnz, n, sv) + 4.0 * sv * n;
+        if (sv == 8) lp.fp64_cj += (double)nnz + 3.0 * n;
       }
     }
     auto upload = [&](std::vector<LDesc<T>>& v, LDesc<T>*& dst) {
@@ -840,7 +852,7 @@ static void run_vbatch(VBatch<T>& vb, bool trans, cudaStream_t s, Profiler& prof
       int id = prof.begin(s, l == 0 ? 0 : 1);
       if (lp.gs) run_gs_down<T>(lp, s);
       else launch_phase<T>(PH_PRE, lp.fmtA, lp.fmtR, lp.d_down, lp.ndown, lp.maxn, s);
-      prof.end(id, l == 0 ? 0 : 1, lp.bytes_pre, s);
+      prof.end(id, l == 0 ? 0 : 1, lp.bytes_pre, s, lp.gs ? 0.0 : lp.fp64_pre);
       prof.next_detail = 16 + 4 * l + 1;
       id = prof.begin(s, 1);
       launch_phase<T>(PH_RESTRICT, lp.fmtA, lp.fmtR, lp.d_down, lp.ndown, lp.maxnc, s);
@@ -857,7 +869,7 @@ static void run_vbatch(VBatch<T>& vb, bool trans, cudaStream_t s, Profiler& prof
       int id = prof.begin(s, l == 0 ? 0 : 1);
       launch_phase<T>(PH_JAC1, lp.fmtA, lp.fmtR, lp.d_cjac, lp.ncjac, lp.maxcj, s);
       launch_phase<T>(PH_POST, lp.fmtA, lp.fmtR, lp.d_cjac, lp.ncjac, lp.maxcj, s);
-      prof.end(id, l == 0 ? 0 : 1, lp.bytes_jac + lp.bytes_post_cj, s);
+      prof.end(id, l == 0 ? 0 : 1, lp.bytes_jac + lp.bytes_post_cj, s, lp.fp64_cj);
     }
   }
   if (tail) {
@@ -877,7 +889,7 @@ static void run_vbatch(VBatch<T>& vb, bool trans, cudaStream_t s, Profiler& prof
     id = prof.begin(s, l == 0 ? 0 : 1);
     if (lp.gs) run_gs_up<T>(lp, s);
     else launch_phase<T>(PH_POST, lp.fmtA, lp.fmtP, lp.d_down, lp.ndown, lp.maxn, s);
-    prof.end(id, l == 0 ? 0 : 1, lp.bytes_post, s);
+    prof.end(id, l == 0 ? 0 : 1, lp.bytes_post, s, lp.gs ? 0.0 : lp.fp64_post);
   }
 }
 
@@ -3036,6 +3048,30 @@ int mgd_profile_read(mgd_ctx* c, int cls, long long* launches, double* ms, doubl
     if (bytes) *bytes = by;
     return MGD_OK;
   });
+}
+
+int mgd_profile_read_fp64(mgd_ctx* c, int cls, double* fp64_ops) {
+  return guarded(c, [&]() -> int {
+    if (cls < 0 || cls >= Profiler::kClasses || !fp64_ops) throw Error{MGD_EINVAL, "bad class or null output"};
+    MGD_CUDA(cudaStreamSynchronize(c->s));
+    c->prof.harvest();
+    double f = c->prof.fp64[cls];
+    if (cls == 1) f += c->prof.fp64[0];
+    *fp64_ops = f;
+    return MGD_OK;
+  });
+}
+
+int mgd_fp64_issue_rate(void* stream, double* lane_ops_per_s) {
+  if (!lane_ops_per_s) return MGD_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  try {
+    *lane_ops_per_s = measure_fp64_rate(s);
+  } catch (const Error&) {
+    cudaGetLastError();
+    return MGD_ECUDA;
+  }
+  return MGD_OK;
 }
 
 const char* mgd_last_error(mgd_ctx* c) { return c ? c->err.c_str() : "null context"; }

@@ -317,6 +317,8 @@ struct InnerCtl {
 // ------------------------------------------------------------------ setup launchers (setup_kernels.cu)
 void exclusive_scan(const int* in, int* out, int n, cudaStream_t s);  // out[0..n], out[n] = total
 int read_int(const int* d, cudaStream_t s);
+// FP64 multiply-add lane operations per second of the whole device (measured)
+double measure_fp64_rate(cudaStream_t s);
 
 void launch_validate(int n, int nnz, int N, int nc, const int* rp, const int* ci, const double* v, int* flags,
                      cudaStream_t s);

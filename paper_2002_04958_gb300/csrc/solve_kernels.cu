@@ -2,6 +2,7 @@
 // the block-level updates of the block preconditioners (Sections 3.3-3.4),
 // generic SpMV / residual, and the FGMRES vector work.  All are HBM-bound
 // streaming or sparse kernels.
+#include "../../include/mgdamg.h"
 #include "mgd_internal.cuh"
 #include "row_dot.cuh"
 
@@ -94,6 +95,47 @@ template void launch_consume_produce<double>(const ConsumeDesc<double>*, int, co
                                              const IOSlots*, cudaStream_t);
 template void launch_consume_produce<float>(const ConsumeDesc<float>*, int, const ProduceDesc<float>*, int, int,
                                             const IOSlots*, cudaStream_t);
+
+// FP64 issue-rate reference: four independent multiply-add chains per thread
+// and enough warps to fill every SM; the peak of the FP64 roofline (lane
+// operations per second with every lane active)
+__global__ void __launch_bounds__(512) k_fp64_rate(int iters, double* out) {
+  double a = 1.0 + threadIdx.x * 1e-9, b = 0.999999, c0 = 1e-7, c1 = 2e-7, c2 = 3e-7, c3 = 4e-7;
+  for (int i = 0; i < iters; ++i) {
+    c0 = fma(a, b, c0);
+    c1 = fma(a, b, c1);
+    c2 = fma(a, b, c2);
+    c3 = fma(a, b, c3);
+  }
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = c0 + c1 + c2 + c3;
+}
+
+double measure_fp64_rate(cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  MGD_CUDA(cudaGetDevice(&dev));
+  MGD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int threads = 512, blocks = 4 * nsm, iters = 4096;
+  double* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.f;
+  cudaError_t e = cudaMallocAsync(&out, sizeof(double) * blocks * threads, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    k_fp64_rate<<<blocks, threads, 0, s>>>(iters, out);  // warm-up
+    cudaEventRecord(e0, s);
+    k_fp64_rate<<<blocks, threads, 0, s>>>(iters, out);
+    cudaEventRecord(e1, s);
+    e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  }
+  if (out) cudaFreeAsync(out, s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess || ms <= 0.f) throw Error{MGD_ECUDA, "FP64 rate measurement failed"};
+  return (double)blocks * threads * iters * 4.0 / (ms * 1e-3);
+}
 
 template <typename T>
 __global__ void k_jacobi(const JacDesc<T>* __restrict__ ds, int N) {

@@ -26,7 +26,7 @@ ENTRY_POINTS = ["mgd_opts_default", "mgd_create", "mgd_setup", "mgd_update_value
                 "mgd_op_info", "mgd_level_info", "mgd_level_export", "mgd_block_vector", "mgd_coupling_dropped",
                 "mgd_profile_enable", "mgd_profile_read", "mgd_kernel_launches", "mgd_last_error", "mgd_destroy", "mgd_plan_info",
                 "mgd_setup_phases", "mgd_op_cycles", "mgd_level_keys", "mgd_precond_bench",
-                "mgd_relres_noalloc"]
+                "mgd_relres_noalloc", "mgd_profile_read_fp64", "mgd_fp64_issue_rate"]
 
 
 class MgdOpts(C.Structure):
@@ -87,6 +87,8 @@ def lib():
             "mgd_coupling_dropped": (I, [P, I, I]),
             "mgd_profile_enable": (I, [P, I]),
             "mgd_profile_read": (I, [P, I, pLL, pD, pD]),
+            "mgd_profile_read_fp64": (I, [P, I, pD]),
+            "mgd_fp64_issue_rate": (I, [P, pD]),
             "mgd_kernel_launches": (C.c_longlong, []),
             "mgd_relres_noalloc": (I, [I, P, P, P, P, P, P, P]),
             "mgd_plan_info": (I, [P, I, I, pI, pI, pI, pI, pI, pI, pI, pI]),
@@ -132,6 +134,17 @@ def relres_noalloc(rowptr, col, val, b, x, out, stream=None):
 
 def kernel_launches():
     return lib().mgd_kernel_launches()
+
+
+def fp64_issue_rate(stream=None):
+    """FP64 multiply-add lane operations per second of the current device (measured)."""
+    import torch
+    st = stream or torch.cuda.current_stream()
+    r = C.c_double()
+    rc = lib().mgd_fp64_issue_rate(C.c_void_p(st.cuda_stream), C.byref(r))
+    if rc != 0:
+        raise MgdError(rc, "mgd_fp64_issue_rate failed")
+    return r.value
 
 
 def _ptr(t):
@@ -286,6 +299,12 @@ class Solver:
         """V-cycles applied by every inverse since setup."""
         return sum(self.op_cycles(k) for k in range(self.stats()["n_ops"]))
 
+    def level_info(self, op, l):
+        """Sizes of level l of operator op: rows, nonzeros, nonzeros of P, coarse rows."""
+        n, nnz, nnzp, ncoarse = (C.c_int() for _ in range(4))
+        self._check(lib().mgd_level_info(self.h, op, l, C.byref(n), C.byref(nnz), C.byref(nnzp), C.byref(ncoarse)))
+        return dict(n=n.value, nnz=nnz.value, nnzp=nnzp.value, ncoarse=ncoarse.value)
+
     def level(self, op, l):
         """Host copies of level l of operator op: A (rp, ci, v), CF, P (rp, ci, v)."""
         n, nnz, nnzp, ncoarse = (C.c_int() for _ in range(4))
@@ -349,6 +368,12 @@ class Solver:
         nl, ms, by = C.c_longlong(), C.c_double(), C.c_double()
         self._check(lib().mgd_profile_read(self.h, cls, C.byref(nl), C.byref(ms), C.byref(by)))
         return nl.value, ms.value, by.value
+
+    def profile_read_fp64(self, cls):
+        """Algorithmic FP64 lane operations of the launches class cls recorded."""
+        f = C.c_double()
+        self._check(lib().mgd_profile_read_fp64(self.h, cls, C.byref(f)))
+        return f.value
 
     def close(self):
         if getattr(self, "h", None):

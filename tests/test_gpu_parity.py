@@ -366,3 +366,39 @@ def test_tune_cache_file(gpu, tmp_path):
     path.write_text("not a cache line\n" + "\n".join(lines) + "\n")
     second = run()
     assert second == first
+
+
+def test_fp64_accounting_and_issue_rate(gpu):
+    # the FP64 roofline inputs: a measured device rate and the algorithmic FP64
+    # lane operations of the level-0 l1-Jacobi kernels (none in FP32 V-cycles)
+    rate = gpu.fp64_issue_rate()
+    assert 1e10 < rate < 1e14
+    s = _system(CASES[2])
+    b = torch.from_numpy(s.b)
+    for prec in (0, 1):
+        slv = gpu.Solver(precision=prec, batched=1).setup_system(s, "bd")
+        slv.profile(1)
+        slv.solve(b)
+        n0, _, _ = slv.profile_read(0)
+        f0 = slv.profile_read_fp64(0)
+        slv.profile(0)
+        assert n0 > 0
+        if prec == 1:
+            assert f0 == 0.0
+        else:
+            # one V-cycle per subsystem and apply: k_pre + k_post at level 0,
+            # (nnz + 2 n) lane operations each; a one-level hierarchy with a
+            # Jacobi coarsest solve (nnz + 3 n); Jacobi inverses and dense
+            # coarsest solves none
+            per_apply = 0.0
+            for k in range(slv.stats()["n_ops"]):
+                info = slv.op_info(k)
+                if info["use_jacobi"]:
+                    continue
+                li = slv.level_info(k, 0)
+                if info["nlevels"] > 1:
+                    per_apply += 2.0 * (li["nnz"] + 2.0 * li["n"])
+                elif not info["coarse_lu"]:
+                    per_apply += li["nnz"] + 3.0 * li["n"]
+            assert per_apply > 0
+            assert f0 == pytest.approx(slv.stats()["last_iters"] * per_apply, rel=1e-12)
