@@ -19,7 +19,7 @@ def _declared():
     with open(os.path.join(ROOT, "include", "mgdamg.h")) as f:
         src = f.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mgd_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(mgd_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(built):
