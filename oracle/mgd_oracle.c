@@ -1543,7 +1543,7 @@ int or_fgmres(const or_csr *A0, or_block *M, int transpose, const double *b, dou
   double *y = (double *)xcalloc((size_t)m, sizeof(double));
   double *r = (double *)xmalloc((size_t)n * sizeof(double));
   double *w = (double *)xmalloc((size_t)n * sizeof(double));
-  int it = 0, status = 1;
+  int it = 0, status = 1, broke = 0;
 #define Hm(i, j) H[(size_t)(i) * m + (j)]
   for (;;) {
     residual(A, b, x, r);
@@ -1555,6 +1555,14 @@ int or_fgmres(const or_csr *A0, or_block *M, int transpose, const double *b, dou
     }
     if (beta <= tol * bnorm) {
       status = 0;
+      break;
+    }
+    /* an Arnoldi breakdown (h_{j+1,j} = 0) with a nonsingular Hessenberg
+       matrix gives the exact solution of the preconditioned system; when the
+       true residual still misses the tolerance, restarting from the same
+       data cannot do better: report the breakdown */
+    if (broke) {
+      status = 2;
       break;
     }
     if (it >= maxit) {
@@ -1605,7 +1613,17 @@ int or_fgmres(const or_csr *A0, or_block *M, int transpose, const double *b, dou
       g[j] = cs[j] * g[j];
       if (hist) hist[it - 1] = fabs(g[j + 1]) / bnorm;
       ++j;
+      if (hn == 0.0) broke = 1;
       if (fabs(g[j]) <= tol * bnorm || hn == 0.0 || it >= maxit || !isfinite(g[j])) break;
+    }
+    /* a zero on the diagonal of the rotated Hessenberg matrix: the least-squares
+       problem is singular (breakdown without a solution); x keeps its value */
+    int singular = 0;
+    for (int i = 0; i < j; ++i)
+      if (Hm(i, i) == 0.0) singular = 1;
+    if (singular) {
+      status = 2;
+      break;
     }
     /* y = H(0:j,0:j)^{-1} g(0:j); x += Z y */
     for (int i = j - 1; i >= 0; --i) {

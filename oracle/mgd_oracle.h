@@ -127,7 +127,10 @@ const double *or_block_vec(const or_block *B, int which, int comp); /* 0: p_alph
 const or_csr *or_block_Ac(const or_block *B);
 void or_block_free(or_block *B);
 
-/* right-preconditioned FGMRES(m), Section 2 / 4; M == NULL means identity */
+/* right-preconditioned FGMRES(m), Section 2 / 4; M == NULL means identity.
+   Returns 0 converged, 1 iteration cap, 2 Arnoldi breakdown that left the
+   tolerance unmet (or a singular least-squares problem: x unchanged),
+   3 non-finite residual. */
 int or_fgmres(const or_csr *A, or_block *M, int transpose, const double *b, double *x,
               double tol, int restart, int maxit, int *iters, double *relres, double *hist);
 

@@ -330,6 +330,41 @@ def test_fgmres_restart_and_edge_cases(orc):
     assert st == 1 and it == 3
 
 
+def test_fgmres_breakdown_and_nan_statuses(orc):
+    """Arnoldi breakdown h_{j+1,j} = 0 (Section 2, GMRES(m)): with a
+    nonsingular Hessenberg matrix the iterate is the exact solution (happy
+    breakdown); with a singular one (A v_0 = 0) there is no solution in the
+    Krylov space, status 2, and x keeps its value; a NaN in b gives status 3."""
+    n = 6
+    A2 = sp.csr_matrix(2.0 * sp.eye(n))
+    A2.sort_indices()
+    Ao = orc.Csr.from_scipy(A2)
+    b = np.zeros(n)
+    b[4] = 1.0
+    x, it, rr, st, _ = orc.fgmres(Ao, b, None, tol=1e-8)
+    assert st == 0 and it == 1 and rr == 0.0 and np.array_equal(x, b / 2)
+    L = sp.kron(sp.eye(n // 2), sp.csr_matrix(np.array([[1.0, -1.0], [-1.0, 1.0]]))).tocsr()
+    L.sort_indices()
+    Lo = orc.Csr.from_scipy(L)
+    x, it, rr, st, _ = orc.fgmres(Lo, np.ones(n), None, tol=1e-8)
+    assert st == 2 and it == 1 and not x.any() and rr == 1.0
+    bn = np.ones(n)
+    bn[2] = np.nan
+    x, it, rr, st, _ = orc.fgmres(Ao, bn, None, tol=1e-8)
+    assert st == 3 and it == 0
+    # singular A = I_3 (x) [[1, 1], [1, 1]] with an AMG preconditioner whose only
+    # level is relaxed (no strong connections, coarsening stalls above
+    # max_coarse = 1): M v_0 = v_0 for the null vector v_0, so A M v_0 = 0
+    S = sp.kron(sp.eye(n // 2), sp.csr_matrix(np.ones((2, 2)))).tocsr()
+    S.sort_indices()
+    So = orc.Csr.from_scipy(S)
+    M = orc.Block(So, 1, 2, "amg", orc.opts(max_coarse=1))
+    b0 = np.zeros(n)
+    b0[0], b0[1] = 1.0, -1.0
+    x, it, rr, st, _ = orc.fgmres(So, b0, M, tol=1e-8)
+    assert st == 2 and it == 1 and not x.any()
+
+
 # ---------------------------------------------------------------- adjoint
 def test_adjoint_gradient_dense_and_fd(orc):
     s = I.make_system(4, (4, 4), multigroup=True)
