@@ -91,6 +91,7 @@ void or_default_opts(or_opts *o) {
   o->interp_type = 0;
   o->smoother = 0;
   o->agg_levels = 0;
+  o->opt4_steps = 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -1019,7 +1020,7 @@ struct or_block {
   double **p;        /* PCTL p_a */
   or_csr *Ac;        /* PCTL coarse operator, Eq. 3.3 */
   int ninv, nmatvec; /* counts of the last apply (Table 1) */
-  double *t1, *t2, *t3, *t4;
+  double *t1, *t2, *t3, *t4, *t5, *t6;
 };
 
 static int diag_pos(const or_csr *A, int i) {
@@ -1172,6 +1173,8 @@ or_block *or_block_setup(const or_csr *A, int G, int N, int kind, const or_opts 
   B->t2 = (double *)xcalloc((size_t)A->n + 1, sizeof(double));
   B->t3 = (double *)xcalloc((size_t)A->n + 1, sizeof(double));
   B->t4 = (double *)xcalloc((size_t)A->n + 1, sizeof(double));
+  B->t5 = (double *)xcalloc((size_t)N + 1, sizeof(double));
+  B->t6 = (double *)xcalloc((size_t)N + 1, sizeof(double));
   B->dropped = (int *)xcalloc((size_t)nc * nc, sizeof(int));
   if (kind == OR_AMG) {
     inv_t *iv = &B->inv[OP_MONO][0];
@@ -1233,7 +1236,13 @@ or_block *or_block_setup(const or_csr *A, int G, int N, int kind, const or_opts 
       inv_build(B, OP_A, I, csr_copy(B->Ab[I]), cycles_for(B, OP_A, I));
       or_csr *CE = diag_modified(B->Ab[E], DV(E, I), DV(I, E), B->diag[I]);
       double *dCE = diag_of(CE);
-      inv_build(B, OP_CE, E, CE, cycles_for(B, OP_CE, E));
+      if (o->opt4_steps > 0) {
+        /* option #4: C_E^{-1} by the recurrence on A_E and A_I; C_E-hat only gives C_g-hat its diagonal */
+        or_csr_free(CE);
+        inv_build(B, OP_A, E, csr_copy(B->Ab[E]), cycles_for(B, OP_A, E));
+      } else {
+        inv_build(B, OP_CE, E, CE, cycles_for(B, OP_CE, E));
+      }
       for (int g = 0; g < G; ++g)
         inv_build(B, OP_CG, g, diag_modified(B->Ab[g], DV(g, E), DV(E, g), dCE), cycles_for(B, OP_CG, g));
       free(dCE);
@@ -1244,7 +1253,10 @@ or_block *or_block_setup(const or_csr *A, int G, int N, int kind, const or_opts 
       inv_build(B, OP_A, E, csr_copy(B->Ab[E]), cycles_for(B, OP_A, E));
       for (int g = 0; g < G; ++g)
         inv_build(B, OP_SG, g, diag_modified(B->Ab[g], DV(g, E), DV(E, g), B->diag[E]), cycles_for(B, OP_SG, g));
-      inv_build(B, OP_SI, I, diag_modified(B->Ab[I], DV(I, E), DV(E, I), B->diag[E]), cycles_for(B, OP_SI, I));
+      if (o->opt4_steps > 0) /* option #4: S_I^{-1} by the recurrence on A_I and A_E */
+        inv_build(B, OP_A, I, csr_copy(B->Ab[I]), cycles_for(B, OP_A, I));
+      else
+        inv_build(B, OP_SI, I, diag_modified(B->Ab[I], DV(I, E), DV(E, I), B->diag[E]), cycles_for(B, OP_SI, I));
       break;
     }
     case OR_PCTL: {
@@ -1339,6 +1351,22 @@ static void hacc(int N, const double *d, const double *v, double *t) {
   for (int k = 0; k < N; ++k) t[k] = t[k] + d[k] * v[k];
 }
 
+/* option #4 (Section 3.5): w = S^{-1} q for S = A_a - D_ab A_b^{-1} D_ba, approximated by
+   K = opt4_steps steps of w^(0) = 0, w^(k+1) = A_a^{-1}(q + D_ab A_b^{-1} D_ba w^(k)).
+   The first step is w^(1) = A_a^{-1} q (its inner term is zero). */
+static void opt4_apply(or_block *B, int a, int b, const double *q, double *w, or_inv_cb cb, void *ctx) {
+  int N = B->N, nc = B->nc;
+  const double *dab = B->d[a * nc + b], *dba = B->d[b * nc + a];
+  double *s = B->t5, *u = B->t6;
+  inv_apply(B, OP_A, a, q, w, cb, ctx);
+  for (int k = 1; k < B->o.opt4_steps; ++k) {
+    for (int i = 0; i < N; ++i) s[i] = dba ? dba[i] * w[i] : 0.0;
+    inv_apply(B, OP_A, b, s, u, cb, ctx);
+    for (int i = 0; i < N; ++i) s[i] = dab ? q[i] + dab[i] * u[i] : q[i];
+    inv_apply(B, OP_A, a, s, w, cb, ctx);
+  }
+}
+
 void or_block_apply(or_block *B, const double *v, double *z, or_inv_cb cb, void *ctx) {
   int G = B->G, N = B->N, nc = B->nc, E = G, I = G + 1;
   double **d = B->d;
@@ -1370,7 +1398,10 @@ void or_block_apply(or_block *B, const double *v, double *z, or_inv_cb cb, void 
       inv_apply(B, OP_A, I, BLK(v, I), wIs, cb, ctx);
       /* 2: w_E* = C_E^{-1}(b_E - D_EI w_I*) */
       hsub(N, BLK(v, E), DV(E, I), wIs, t);
-      inv_apply(B, OP_CE, E, t, wEs, cb, ctx);
+      if (B->o.opt4_steps > 0)
+        opt4_apply(B, E, I, t, wEs, cb, ctx);
+      else
+        inv_apply(B, OP_CE, E, t, wEs, cb, ctx);
       /* 3: w_g = C_g^{-1}(b_g - D_gE w_E*) */
       for (int g = 0; g < G; ++g) {
         hsub(N, BLK(v, g), DV(g, E), wEs, t);
@@ -1379,7 +1410,10 @@ void or_block_apply(or_block *B, const double *v, double *z, or_inv_cb cb, void 
       /* 4: w_E = w_E* - C_E^{-1} sum_g D_Eg w_g */
       for (int k = 0; k < N; ++k) t[k] = 0.0;
       for (int g = 0; g < G; ++g) hacc(N, DV(E, g), BLK(z, g), t);
-      inv_apply(B, OP_CE, E, t, u, cb, ctx);
+      if (B->o.opt4_steps > 0)
+        opt4_apply(B, E, I, t, u, cb, ctx);
+      else
+        inv_apply(B, OP_CE, E, t, u, cb, ctx);
       for (int k = 0; k < N; ++k) BLK(z, E)[k] = wEs[k] - u[k];
       /* 5: w_I = w_I* - A_I^{-1} D_IE w_E */
       for (int k = 0; k < N; ++k) t[k] = 0.0;
@@ -1396,7 +1430,10 @@ void or_block_apply(or_block *B, const double *v, double *z, or_inv_cb cb, void 
         inv_apply(B, OP_SG, g, t, BLK(z, g), cb, ctx);
       }
       hsub(N, BLK(v, I), DV(I, E), wEs, t);
-      inv_apply(B, OP_SI, I, t, BLK(z, I), cb, ctx);
+      if (B->o.opt4_steps > 0)
+        opt4_apply(B, I, E, t, BLK(z, I), cb, ctx);
+      else
+        inv_apply(B, OP_SI, I, t, BLK(z, I), cb, ctx);
       /* 3: w_E = w_E* - A_E^{-1}(sum_g D_Eg w_g + D_EI w_I) */
       for (int k = 0; k < N; ++k) t[k] = 0.0;
       for (int g = 0; g < G; ++g) hacc(N, DV(E, g), BLK(z, g), t);
@@ -1504,6 +1541,8 @@ void or_block_free(or_block *B) {
   free(B->t2);
   free(B->t3);
   free(B->t4);
+  free(B->t5);
+  free(B->t6);
   free(B);
 }
 

@@ -45,6 +45,11 @@ typedef struct or_opts {
   int agg_levels;         /* levels, from the finest, coarsened aggressively (Section 3.1): a second PMIS
                              pass on the Galerkin operator of the first, which is not kept as a level;
                              P = P1 P2 (two-stage interpolation).  0: none (default) */
+  int opt4_steps;         /* option #4 (Section 3.5), 0: off.  K > 0: the Schur complement whose inner
+                             inverse is one block -- S_I = A_I - D_IE A_E^{-1} D_EI (Schur2) and
+                             C_E = A_E - D_EI A_I^{-1} D_IE (Schur1) -- is inverted by K steps of
+                             w^(0) = 0, w^(k+1) = A_a^{-1}(q + D_ab A_b^{-1} D_ba w^(k)), with A_a^{-1},
+                             A_b^{-1} by option #1/#2 (or #3 under inner_mode); forward apply only */
 } or_opts;
 
 /* preconditioner kinds */

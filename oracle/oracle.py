@@ -40,7 +40,7 @@ class Opts(C.Structure):
                 ("nvcyc_group", C.c_int), ("nvcyc_E", C.c_int), ("nvcyc_I", C.c_int),
                 ("nvcyc_other", C.c_int), ("jacobi_sweeps", C.c_int), ("adaptive", C.c_int),
                 ("seed", C.c_uint64), ("inner_mode", C.c_int), ("interp_type", C.c_int),
-                ("smoother", C.c_int), ("agg_levels", C.c_int)]
+                ("smoother", C.c_int), ("agg_levels", C.c_int), ("opt4_steps", C.c_int)]
 
 
 INV_CB = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
