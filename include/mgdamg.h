@@ -46,10 +46,14 @@ enum {
   MGD_OK = 0,
   MGD_EINVAL = 1,      /* bad argument, size, layout, unsorted/duplicate columns, non-positive diagonal */
   MGD_ENOCONV = 2,     /* iteration cap reached; x holds the last iterate */
-  MGD_EBREAKDOWN = 3,  /* Arnoldi breakdown before the tolerance was met */
+  MGD_EBREAKDOWN = 3,  /* Arnoldi breakdown (h_{j+1,j} = 0) and the tolerance still unmet, or a singular
+                          Hessenberg least-squares problem (x then keeps its value) */
   MGD_ESINGULAR = 4,   /* zero pivot in the coarsest-level elimination */
   MGD_ENAN = 5,        /* non-finite residual */
-  MGD_ETIMEOUT = 6,    /* a device-side bounded wait ran out */
+  MGD_ETIMEOUT = 6,    /* reserved, never returned: no kernel of this library waits on a flag that
+                          another launch writes; its grid-wide barriers run in cooperative launches,
+                          whose co-residency the runtime guarantees, and every device-controlled loop
+                          has a trip cap */
   MGD_ECUDA = 7,       /* CUDA runtime error */
   MGD_ENOMEM = 8,      /* device allocation failed */
   MGD_ESTATE = 9       /* call out of order (e.g. solve before setup) */
@@ -107,6 +111,12 @@ typedef struct mgd_opts {
   int arnoldi_resident;   /* 1 (default): each FGMRES orthogonalisation runs as one cooperative grid that keeps the
                              new Krylov vector in shared memory (one block per SM; used when n fits, else 0);
                              0: one streaming kernel per basis vector.  Same modified Gram-Schmidt either way */
+  int opt4_steps;         /* option #4 (Section 3.5).  0 (default): off.  K in 1..1000: the Schur complement
+                             whose inner inverse is one block -- S_I = A_I - D_IE A_E^-1 D_EI of Schur2 and
+                             C_E = A_E - D_EI A_I^-1 D_IE of Schur1 -- is inverted by K steps of
+                             w(0) = 0, w(k+1) = A_a^-1 (q + D_ab A_b^-1 D_ba w(k)), with the AMG inverses
+                             (option #2) of the plain blocks A_a, A_b in place of S_I-hat / C_E-hat.  Forward
+                             apply only (the transposed solve is AMG/BD only) */
 } mgd_opts;
 
 /* Fill *o with the defaults listed above.  Returns MGD_EINVAL if o is NULL. */
@@ -120,7 +130,7 @@ int mgd_create(mgd_ctx **out, const mgd_opts *o, void *stream);
 /* Setup phase (Section 3.1 setup; Sections 3.3-3.6 block operators):
  * G groups, N cells, n = (G+2)*N unknowns, nnz entries; d_rowptr[n+1],
  * d_colidx[nnz], d_vals[nnz] on the device.  Validates the layout (MGD_EINVAL
- * on failure), extracts the blocks and couplings, applies the adaptive rules
+ * on failure; MGD_ENAN when a value is not finite),  extracts the blocks and couplings, applies the adaptive rules
  * when opts.adaptive, builds every AMG hierarchy on the device (strength,
  * PMIS, classical modified interpolation, Galerkin RAP, l1 diagonals, dense
  * coarsest inverse) and prepares the solve.  Replaces any previous setup. */
@@ -134,7 +144,10 @@ int mgd_update_values(mgd_ctx *c, const double *d_vals);
 /* Solve A x = b by FGMRES(restart) preconditioned on the right, stopping when
  * ||b - A x||_2 <= tol ||b||_2 (Section 4).  d_b[n] in, d_x[n] in: initial
  * guess, out: solution.  *iters = preconditioner applications, *relres = final
- * true relative residual.  Returns MGD_ENOCONV if max_it is reached. */
+ * true relative residual.  Returns MGD_ENOCONV if max_it is reached,
+ * MGD_ENAN when a residual norm is not finite (e.g. a NaN in b or in the
+ * values), MGD_EBREAKDOWN as described with the status codes; a happy
+ * breakdown that meets the tolerance returns MGD_OK. */
 int mgd_solve(mgd_ctx *c, const double *d_b, double tol, double *d_x, int *iters, double *relres);
 
 /* As mgd_solve with host buffers h_b[n], h_x[n] (x: initial guess in,
@@ -273,24 +286,28 @@ int mgd_fp64_issue_rate(void *stream, double *lane_ops_per_s);
 
 /* True relative residual without any device allocation.  The paper has no
  * counterpart: this is a service for callers that cannot call cudaMalloc
- * (an application whose allocator owns the device, a loop with a fixed
- * memory footprint, code that is assembling a CUDA graph).
+ * (an application whose allocator owns the device, a loop with a fixed,
+ * audited memory footprint).
  *
  * Computes r = b - A x for the CSR matrix d_rowptr[n+1], d_colidx, d_vals
- * (device pointers, any sparsity) and d_b[n], d_x[n], and writes
- * d_out[0] = ||r||_2, d_out[1] = ||b||_2, d_out[2] = ||r||_2 / ||b||_2
- * (0 when b = 0) into the caller's device buffer d_out[3].  This is the
- * quantity mgd_solve reports as *relres.  Work runs on `stream` (a
- * cudaStream_t, NULL = legacy default stream) and is complete on return.
+ * (device pointers, any sparsity, int32 indices, FP64 values; not checked on
+ * the device) and d_b[n], d_x[n], and writes d_out[0] = ||r||_2,
+ * d_out[1] = ||b||_2, d_out[2] = ||r||_2 / ||b||_2 (0 when b = 0) into the
+ * caller's device buffer d_out[3].  This is the quantity mgd_solve reports
+ * as *relres.  Work runs on `stream` (a cudaStream_t, NULL = legacy default
+ * stream); the call synchronises that stream before it returns.
  *
  * Work space is one fixed device array inside the library, not memory from
- * cudaMalloc: no call allocates or frees device memory.  n < 1 or
- * n > MGD_NOALLOC_MAX_N returns MGD_EINVAL; a CUDA error returns MGD_ECUDA.
- * The first call on each device looks up that array's device address (once
- * per device, with that device current); make that first call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * (other streams, other threads) race and must be serialised by the caller.
- * Nothing from an earlier call is read back. */
+ * cudaMalloc.  CUDA loads device code lazily by default, so the first call
+ * on a device may make the driver load this code and reserve the array
+ * (about 4 MiB); after that no call allocates or frees device memory.
+ * n < 1 or n > MGD_NOALLOC_MAX_N, or a null pointer, returns MGD_EINVAL; a
+ * CUDA error of this call's launches returns MGD_ECUDA (an error left
+ * pending by earlier work is cleared first, not reported).  The first call
+ * on each device looks up that array's device address (once per device, with
+ * that device current).  All calls share the array: calls that overlap on the
+ * GPU (other streams, other threads) race and must be serialised by the
+ * caller.  Nothing from an earlier call is read back. */
 int mgd_relres_noalloc(int n, const int *d_rowptr, const int *d_colidx, const double *d_vals, const double *d_b,
                        const double *d_x, double *d_out, void *stream);
 

@@ -1157,6 +1157,7 @@ struct mgd_ctx {
   std::vector<mgd::VBatch<float>> vb32;
   mgd::IOSlots* io = nullptr;
   double *wEs = nullptr, *wIs = nullptr, *rfull = nullptr;
+  double *t4a = nullptr, *t4b = nullptr;  // option #4 work vectors (N)
   // FGMRES storage
   double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *hbuf = nullptr, *partial = nullptr,
          *ybuf = nullptr, *xtmp = nullptr, *btmp = nullptr;
@@ -1625,16 +1626,42 @@ static void build_program(mgd_ctx* c) {
       break;
     }
     case MGD_SCHUR1: {
-      // ops: 0 = A_I, 1 = C_E, 2.. = C_g
+      // ops: 0 = A_I, 1 = C_E (option #4: A_E), 2.. = C_g
       int oAI = 0, oCE = 1;
+      const int K4 = c->o.opt4_steps;
       std::vector<std::tuple<const double*, PRef, double>> t;
+      // option #4 for C_E = A_E - D_EI A_I^-1 D_IE: q = base + sum(qterms); the
+      // first step is w = A_E^-1 q, each further one t = A_I^-1 (D_IE w),
+      // w = A_E^-1 (q + D_EI t); the last result goes to (dst, dbase, ds)
+      auto opt4_CE = [&](PRef qbase, std::vector<std::tuple<const double*, PRef, double>> qterms, PRef dst,
+                         PRef dbase, double ds) {
+        produce1(oCE, qbase, qterms);
+        push_invert(S, {oCE});
+        for (int k = 1; k < K4; ++k) {
+          consume1(oCE, ABS(c->t4a), NUL(), 1.0);                           // w(k)
+          std::vector<std::tuple<const double*, PRef, double>> ti;
+          if (D(I, E)) ti.emplace_back(D(I, E), ABS(c->t4a), 1.0);
+          produce1(oAI, NUL(), ti);
+          push_invert(S, {oAI});
+          consume1(oAI, ABS(c->t4b), NUL(), 1.0);                           // A_I^-1 D_IE w(k)
+          auto qt = qterms;
+          if (D(E, I)) qt.emplace_back(D(E, I), ABS(c->t4b), 1.0);
+          produce1(oCE, qbase, qt);
+          push_invert(S, {oCE});
+        }
+        consume1(oCE, dst, dbase, ds);
+      };
       produce1(oAI, VIN(blk(I)), {});                                       // 1
       push_invert(S, {oAI});
       consume1(oAI, ABS(c->wIs), NUL(), 1.0);
       if (D(E, I)) t.emplace_back(D(E, I), ABS(c->wIs), -1.0);               // 2
-      produce1(oCE, VIN(blk(E)), t);
-      push_invert(S, {oCE});
-      consume1(oCE, ABS(c->wEs), NUL(), 1.0);
+      if (K4 > 0) {
+        opt4_CE(VIN(blk(E)), t, ABS(c->wEs), NUL(), 1.0);
+      } else {
+        produce1(oCE, VIN(blk(E)), t);
+        push_invert(S, {oCE});
+        consume1(oCE, ABS(c->wEs), NUL(), 1.0);
+      }
       std::vector<ProduceDesc<T>> pv;                                        // 3
       std::vector<ConsumeDesc<T>> cv;
       std::vector<int> gs;
@@ -1651,9 +1678,13 @@ static void build_program(mgd_ctx* c) {
       t.clear();                                                             // 4
       for (int g = 0; g < G; ++g)
         if (D(E, g)) t.emplace_back(D(E, g), ZOUT(blk(g)), 1.0);
-      produce1(oCE, NUL(), t);
-      push_invert(S, {oCE});
-      consume1(oCE, ZOUT(blk(E)), ABS(c->wEs), -1.0);
+      if (K4 > 0) {
+        opt4_CE(NUL(), t, ZOUT(blk(E)), ABS(c->wEs), -1.0);
+      } else {
+        produce1(oCE, NUL(), t);
+        push_invert(S, {oCE});
+        consume1(oCE, ZOUT(blk(E)), ABS(c->wEs), -1.0);
+      }
       t.clear();                                                             // 5
       if (D(I, E)) t.emplace_back(D(I, E), ZOUT(blk(E)), 1.0);
       produce1(oAI, NUL(), t);
@@ -1686,6 +1717,21 @@ static void build_program(mgd_ctx* c) {
       push_produce<T>(c, S, pv, N);
       push_invert(S, gs);
       push_consume<T>(c, S, cv, N);
+      // option #4 for S_I = A_I - D_IE A_E^-1 D_EI: the step above is w(1) =
+      // A_I^-1 q (op G+1 holds A_I); each further step t = A_E^-1 (D_EI w(k)),
+      // w(k+1) = A_I^-1 (q + D_IE t), with q = b_I - D_IE w_E* rebuilt from v
+      for (int k = 1; k < c->o.opt4_steps; ++k) {
+        std::vector<std::tuple<const double*, PRef, double>> te;
+        if (D(E, I)) te.emplace_back(D(E, I), ZOUT(blk(I)), 1.0);
+        produce1(oAE, NUL(), te);
+        push_invert(S, {oAE});
+        consume1(oAE, ABS(c->t4a), NUL(), 1.0);
+        auto qt = t;
+        if (D(I, E)) qt.emplace_back(D(I, E), ABS(c->t4a), 1.0);
+        produce1(oSI, VIN(blk(I)), qt);
+        push_invert(S, {oSI});
+        consume1(oSI, ZOUT(blk(I)), NUL(), 1.0);
+      }
       t.clear();                                                             // 3
       for (int g = 0; g < G; ++g)
         if (D(E, g)) t.emplace_back(D(E, g), ZOUT(blk(g)), 1.0);
@@ -2197,15 +2243,16 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
   // validation
   {
     Scratch sc(s);
-    int* flags = sc.alloc<int>(4);
-    MGD_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), s));
+    int* flags = sc.alloc<int>(5);
+    MGD_CUDA(cudaMemsetAsync(flags, 0, 5 * sizeof(int), s));
     launch_validate(n, nnz, N, nc, rp, ci, v, flags, s);
-    int hf[4];
+    int hf[5];
     MGD_CUDA(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
     MGD_CUDA(cudaStreamSynchronize(s));
     if (hf[3]) throw Error{MGD_EINVAL, "row pointer does not span [0, nnz]"};
     if (hf[0]) throw Error{MGD_EINVAL, "column index out of range, unsorted or duplicated"};
     if (hf[1]) throw Error{MGD_EINVAL, "off-block entry couples different cells (D_ab must be diagonal)"};
+    if (hf[4]) throw Error{MGD_ENAN, "a matrix value is not finite"};
     if (hf[2]) throw Error{MGD_EINVAL, "missing or non-positive diagonal entry"};
   }
   // keep a copy of the monolithic operator
@@ -2226,6 +2273,8 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
   PhaseTimer pt_blk(&c->phases, SP_BLOCKS);
   c->wEs = c->ar.alloc<double>(N, true);
   c->wIs = c->ar.alloc<double>(N, true);
+  c->t4a = c->ar.alloc<double>(N, true);
+  c->t4b = c->ar.alloc<double>(N, true);
   c->rfull = c->ar.alloc<double>(n, true);
   c->io = c->ar.alloc<IOSlots>(1, true);
   c->ops.clear();
@@ -2314,14 +2363,20 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
         Csr CE = diag_modified(c, bd.Ab[E], D(E, I), D(I, E), bd.diag[I]);
         double* dCE = c->ar.alloc<double>(N);
         launch_diag_extract(N, CE.rp, CE.ci, CE.v, dCE, s);
-        add_op(c, OP_CE, E, CE);
+        if (o.opt4_steps > 0)  // option #4: C_E^-1 by the recurrence on A_E and A_I (C_E-hat gives C_g-hat its diagonal)
+          add_op(c, OP_A, E, csr_copy(c->ar, bd.Ab[E], s));
+        else
+          add_op(c, OP_CE, E, CE);
         for (int g = 0; g < G; ++g) add_op(c, OP_CG, g, diag_modified(c, bd.Ab[g], D(g, E), D(E, g), dCE));
         break;
       }
       case MGD_SCHUR2:
         add_op(c, OP_A, E, csr_copy(c->ar, bd.Ab[E], s));
         for (int g = 0; g < G; ++g) add_op(c, OP_SG, g, diag_modified(c, bd.Ab[g], D(g, E), D(E, g), bd.diag[E]));
-        add_op(c, OP_SI, I, diag_modified(c, bd.Ab[I], D(I, E), D(E, I), bd.diag[E]));
+        if (o.opt4_steps > 0)  // option #4: S_I^-1 by the recurrence on A_I and A_E
+          add_op(c, OP_A, I, csr_copy(c->ar, bd.Ab[I], s));
+        else
+          add_op(c, OP_SI, I, diag_modified(c, bd.Ab[I], D(I, E), D(E, I), bd.diag[E]));
         break;
       case MGD_PCTL:
         for (int a = 0; a < nc; ++a) add_op(c, OP_A, a, csr_copy(c->ar, bd.Ab[a], s));
@@ -2593,6 +2648,7 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   auto Hm = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
   int it = 0, status = MGD_ENOCONV;
+  bool broke = false;  // an Arnoldi breakdown ended the previous cycle
   for (;;) {
     int id = c->prof.begin(s, 2);
     launch_resid_f64(c->fmtMono, n, A.rp, A.ci, A.v, AS.sptr, AS.ci, AS.v, b, x, c->r, s);
@@ -2607,6 +2663,13 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
       status = MGD_OK;
       break;
     }
+    // h_{j+1,j} = 0 with a nonsingular Hessenberg matrix gives the exact
+    // solution of the preconditioned system; if the true residual still misses
+    // the tolerance, a restart from the same data cannot do better
+    if (broke) {
+      status = MGD_EBREAKDOWN;
+      break;
+    }
     if (it >= c->o.max_it) {
       status = MGD_ENOCONV;
       break;
@@ -2618,7 +2681,6 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int j = 0;
-    bool breakdown = false;
     while (j < m) {
       double* vj = c->V + (size_t)j * n;
       double* zj = c->Z + (size_t)j * n;
@@ -2662,10 +2724,19 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
       g[j] = cs[j] * g[j];
       c->hist.push_back(std::fabs(g[j + 1]) / bnorm);
       ++j;
-      if (hn == 0.0) breakdown = true;
+      if (hn == 0.0) broke = true;
       if (std::fabs(g[j]) <= tol * bnorm || hn == 0.0 || it >= c->o.max_it || !std::isfinite(g[j])) break;
     }
-    (void)breakdown;
+    // a zero on the diagonal of the rotated Hessenberg matrix: the small
+    // least-squares problem is singular, no solution in this Krylov space;
+    // x keeps its value
+    bool singular = false;
+    for (int i = 0; i < j; ++i)
+      if (Hm(i, i) == 0.0) singular = true;
+    if (singular) {
+      status = MGD_EBREAKDOWN;
+      break;
+    }
     for (int i = j - 1; i >= 0; --i) {
       double sum = g[i];
       for (int k = i + 1; k < j; ++k) sum -= Hm(i, k) * y[k];
@@ -2683,6 +2754,7 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
   if (status != MGD_OK) {
     if (status == MGD_ENOCONV) c->err = "iteration cap reached";
     if (status == MGD_ENAN) c->err = "non-finite residual";
+    if (status == MGD_EBREAKDOWN) c->err = "Arnoldi breakdown without reaching the tolerance";
   }
   return status;
 }
@@ -2722,6 +2794,7 @@ int mgd_opts_default(mgd_opts* o) {
   o->smoother = 0;
   o->agg_levels = 0;
   o->arnoldi_resident = 1;
+  o->opt4_steps = 0;
   return MGD_OK;
 }
 
@@ -2737,7 +2810,8 @@ int mgd_create(mgd_ctx** out, const mgd_opts* o, void* stream) {
       q.precision < 0 || q.precision > 1 || q.inner_mode < 0 || q.inner_mode > 1 || q.inner_maxit < 1 ||
       q.inner_maxit > 100000 || !(q.inner_tol >= 0.0) || q.nvcyc_group > 1000 || q.nvcyc_E > 1000 ||
       q.nvcyc_I > 1000 || q.nvcyc_other > 1000 || q.jacobi_sweeps > 1000 || q.smoother < 0 || q.smoother > 1 ||
-      q.agg_levels < 0 || q.agg_levels > q.max_levels || q.arnoldi_resident < 0 || q.arnoldi_resident > 1) {
+      q.agg_levels < 0 || q.agg_levels > q.max_levels || q.arnoldi_resident < 0 || q.arnoldi_resident > 1 ||
+      q.opt4_steps < 0 || q.opt4_steps > 1000) {
     delete c;
     return MGD_EINVAL;
   }

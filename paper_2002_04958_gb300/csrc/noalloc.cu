@@ -3,8 +3,8 @@
 //
 // Who needs this: code that must not call cudaMalloc once it is running --
 // for example a host application whose memory manager owns the whole device
-// after start-up, a solver loop with a fixed, audited memory footprint, or a
-// caller that is in the middle of building work for a CUDA graph.  The other
+// after start-up, or a solver loop with a fixed, audited memory footprint.
+// The other
 // entry points of this library allocate their work space at setup; this one
 // keeps its work space (the residual vector and the partial sums of the two
 // norms) in a fixed array that lives in the library's device image instead.
@@ -15,6 +15,10 @@
 // different host threads) race on it and give wrong results; serialise them.
 // The contents left by the previous call are never read: every element used
 // by a call is written by that call first.
+//
+// CUDA loads a library's device code lazily by default, so the first call on
+// a device may make the driver load this file's module, and with it reserve
+// the array; from then on no call allocates or frees device memory.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -134,6 +138,9 @@ extern "C" int mgd_relres_noalloc(int n, const int* d_rowptr, const int* d_colid
   double* part = scratch + MGD_NOALLOC_MAX_N;
   int nb = (n + kThreadsNA - 1) / kThreadsNA;
   if (nb > 4096) nb = 4096;
+  // an error left pending by earlier, unrelated work would otherwise be
+  // reported as a failure of this call's launches
+  (void)cudaGetLastError();
   k_na_residual<<<nb, kThreadsNA, 0, s>>>(n, d_rowptr, d_colidx, d_vals, d_b, d_x, r);
   k_na_partials<<<kParts, kThreadsNA, 0, s>>>(n, r, d_b, part);
   k_na_final<<<1, kThreadsNA, 0, s>>>(part, d_out);

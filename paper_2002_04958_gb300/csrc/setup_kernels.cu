@@ -143,7 +143,8 @@ int read_int(const int* d, cudaStream_t s) {
 // ------------------------------------------------------------------ validation and block extraction
 // flags: 0 column out of range / unsorted / duplicated, 1 off-block entry
 // outside its cell, 2 missing or non-positive diagonal, 3 row pointer not a
-// non-decreasing map onto [0, nnz] (the row's entries are then not read)
+// non-decreasing map onto [0, nnz] (the row's entries are then not read),
+// 4 a value that is not finite
 __global__ void k_validate(int n, int nnz, int N, int nc, const int* rp, const int* ci, const double* v, int* flags) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -163,6 +164,7 @@ __global__ void k_validate(int n, int nnz, int N, int nc, const int* rp, const i
     prev = j;
     int b = j / N;
     if (b != a && j - b * N != k) atomicOr(&flags[1], 1);
+    if (!isfinite(v[p])) atomicOr(&flags[4], 1);
     if (j == i) {
       diag = true;
       if (!(v[p] > 0.0)) atomicOr(&flags[2], 1);

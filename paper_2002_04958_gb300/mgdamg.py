@@ -38,7 +38,8 @@ class MgdOpts(C.Structure):
                 ("restart", C.c_int), ("max_it", C.c_int), ("precision", C.c_int), ("batched", C.c_int),
                 ("use_graph", C.c_int), ("autotune", C.c_int), ("keep_transpose", C.c_int),
                 ("fuse_rows", C.c_int), ("interp_type", C.c_int), ("pdl", C.c_int), ("inner_mode", C.c_int),
-                ("smoother", C.c_int), ("agg_levels", C.c_int), ("arnoldi_resident", C.c_int)]
+                ("smoother", C.c_int), ("agg_levels", C.c_int), ("arnoldi_resident", C.c_int),
+                ("opt4_steps", C.c_int)]
 
 
 class MgdStats(C.Structure):
@@ -125,11 +126,48 @@ NOALLOC_MAX_N = 1 << 19
 
 def relres_noalloc(rowptr, col, val, b, x, out, stream=None):
     """||b - A x||, ||b|| and their ratio into the device tensor out[3], with no
-    device allocation inside the library (see mgd_relres_noalloc)."""
+    device allocation inside the library (see mgd_relres_noalloc).
+
+    The library reads these buffers through raw pointers without checking
+    them on the device, so everything that would make it read out of bounds
+    is checked here first: int32 rowptr (n+1) and col, float64 val, b (n),
+    x (n) and out (>= 3), all contiguous and on one CUDA device, and nnz =
+    rowptr[-1] entries in col and val.  The call runs with that device current
+    and, unless `stream` is given, on that device's current stream."""
     import torch
-    st = stream or torch.cuda.current_stream()
-    return lib().mgd_relres_noalloc(rowptr.numel() - 1, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b), _ptr(x),
-                                    _ptr(out), C.c_void_p(st.cuda_stream))
+    named = {"rowptr": rowptr, "col": col, "val": val, "b": b, "x": x, "out": out}
+    for k, t in named.items():
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"relres_noalloc: {k} must be a torch.Tensor")
+        want = torch.int32 if k in ("rowptr", "col") else torch.float64
+        if t.dtype != want:
+            raise TypeError(f"relres_noalloc: {k} must be {want}, got {t.dtype}")
+        if t.dim() != 1 or not t.is_contiguous():
+            raise ValueError(f"relres_noalloc: {k} must be a contiguous 1-D tensor")
+    n = rowptr.numel() - 1
+    if n < 1 or n > NOALLOC_MAX_N:
+        raise ValueError(f"relres_noalloc: n = {n} outside [1, {NOALLOC_MAX_N}]")
+    if b.numel() != n or x.numel() != n:
+        raise ValueError(f"relres_noalloc: b and x need n = {n} entries, got {b.numel()} and {x.numel()}")
+    if out.numel() < 3:
+        raise ValueError("relres_noalloc: out needs 3 entries")
+    for k, t in named.items():
+        if not t.is_cuda:
+            raise ValueError(f"relres_noalloc: {k} must be a CUDA tensor")
+    dev = rowptr.device
+    for k, t in named.items():
+        if t.device != dev:
+            raise ValueError(f"relres_noalloc: {k} is on {t.device}, rowptr on {dev}")
+    nnz = int(rowptr[-1].item())
+    if int(rowptr[0].item()) != 0 or nnz > col.numel() or nnz > val.numel():
+        raise ValueError(f"relres_noalloc: rowptr[0] must be 0 and rowptr[-1] = {nnz} <= len(col), len(val)")
+    if nnz > 0 and (int(col.min().item()) < 0 or int(col.max().item()) >= n
+                    or bool((rowptr[1:] < rowptr[:-1]).any().item())):
+        raise ValueError("relres_noalloc: rowptr must be non-decreasing and columns in [0, n)")
+    with torch.cuda.device(dev):
+        st = stream or torch.cuda.current_stream(dev)
+        return lib().mgd_relres_noalloc(n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b), _ptr(x), _ptr(out),
+                                        C.c_void_p(st.cuda_stream))
 
 
 def kernel_launches():

@@ -22,7 +22,7 @@ from oracle import oracle as orc                   # noqa: E402
 from paper_2002_04958_gb300 import inputs as I     # noqa: E402
 
 OUT = os.path.join(HERE, "oracle_fgmres_G20_96x96x96_schur2.json")
-N_SAMPLES = 64
+N_SAMPLES = 256
 
 
 def main():
@@ -31,11 +31,12 @@ def main():
     ob = orc.Block(Ao, s.G, s.N, "schur2")
     xo, ito, rro, sto, _ = orc.fgmres(Ao, s.b, ob, tol=1e-8)
     assert sto == 0
-    idx = np.sort(np.random.default_rng(3).choice(s.n, N_SAMPLES, replace=False))
+    rng = np.random.default_rng(3)
+    idx = np.sort(np.concatenate([rng.choice(s.n, N_SAMPLES - 1, replace=False), [int(np.argmax(np.abs(xo)))]]))
     rec = {
         "workload": I.PRESET_NAMES[3], "n": int(s.n), "nnz": int(s.nnz), "tol": 1e-8,
         "iterations": int(ito), "relres": float(rro),
-        "x_norm2": float(np.linalg.norm(xo)),
+        "x_norm2": float(np.linalg.norm(xo)), "x_max_abs": float(np.abs(xo).max()),
         "sample_index": [int(i) for i in idx],
         "sample_x": [float(xo[i]) for i in idx],
         "written_by": "python tests/golden/make_oracle_fgmres_G20_96x96x96.py",

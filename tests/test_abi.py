@@ -40,7 +40,8 @@ def test_opts_defaults_and_struct_layout(built):
     assert o.restart == 30 and o.nvcyc_group == 1 and o.precision == 0
     assert o.inner_mode == 0 and o.inner_maxit == 100
     # the ctypes mirror has the C struct's size: the library writes every field
-    assert C.sizeof(mgdamg.MgdOpts) == 144 and C.sizeof(mgdamg.MgdStats) == 112
+    assert C.sizeof(mgdamg.MgdOpts) == 152 and C.sizeof(mgdamg.MgdStats) == 112
+    assert o.opt4_steps == 0
     assert mgdamg.lib().mgd_kernel_launches() >= 0
     assert mgdamg.lib().mgd_opts_default(None) == 1
 
@@ -80,3 +81,37 @@ def test_struct_layout_matches_c_compiler(tmp_path):
         assert offs[k] == getattr(mgdamg.MgdOpts, f).offset, f
     for k, f in enumerate(sfields):
         assert offs[len(fields) + k] == getattr(mgdamg.MgdStats, f).offset, f
+
+
+def test_relres_noalloc_binding_rejects_bad_arguments():
+    """The allocation-free residual reads raw pointers without device-side
+    checks; the binding rejects, before any library call, the mistakes that
+    would make it read out of bounds."""
+    torch = pytest.importorskip("torch")
+    from paper_2002_04958_gb300 import mgdamg
+    n = 8
+    rp = torch.arange(n + 1, dtype=torch.int32)
+    ci = torch.arange(n, dtype=torch.int32)
+    v = torch.ones(n, dtype=torch.float64)
+    b = torch.ones(n, dtype=torch.float64)
+    x = torch.ones(n, dtype=torch.float64)
+    out = torch.zeros(3, dtype=torch.float64)
+    f = mgdamg.relres_noalloc
+    with pytest.raises(TypeError, match="rowptr must be torch.int32"):
+        f(rp.to(torch.int64), ci, v, b, x, out)          # torch.from_numpy of an int64 index array
+    with pytest.raises(TypeError, match="col must be torch.int32"):
+        f(rp, ci.to(torch.int64), v, b, x, out)
+    with pytest.raises(TypeError, match="val must be torch.float64"):
+        f(rp, ci, v.float(), b, x, out)
+    with pytest.raises(TypeError, match="must be a torch.Tensor"):
+        f(rp, ci, v, b.numpy(), x, out)
+    with pytest.raises(ValueError, match="contiguous"):
+        f(rp, ci, v, torch.ones(2 * n, dtype=torch.float64)[::2], x, out)
+    with pytest.raises(ValueError, match="b and x need n"):
+        f(rp, ci, v, b, torch.ones(n + 1, dtype=torch.float64), out)
+    with pytest.raises(ValueError, match="out needs 3"):
+        f(rp, ci, v, b, x, torch.zeros(2, dtype=torch.float64))
+    with pytest.raises(ValueError, match="outside"):
+        f(torch.zeros(1, dtype=torch.int32), ci, v, b[:0], x[:0], out)
+    with pytest.raises(ValueError, match="must be a CUDA tensor"):
+        f(rp, ci, v, b, x, out)                           # all host tensors

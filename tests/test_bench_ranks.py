@@ -64,3 +64,24 @@ def test_reference_arm_other_ranks_exit_without_work():
                         "--warmup", "3"], env=env, capture_output=True, text=True, timeout=120)
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_reference_arm_line_on_the_small_workload():
+    # the oracle as the reference arm on the 3,072-unknown workload: one JSON
+    # line with the contract's keys, the same config dict as the GPU arm's
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "0",
+                        "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=300,
+                       env=dict(os.environ, RANK="0", LOCAL_RANK="0", WORLD_SIZE="1"))
+    assert p.returncode == 0, p.stderr
+    d = json.loads(p.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["unit"] == "s" and d["higher_is_better"] is False
+    assert d["value"] > 0 and d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    from paper_2002_04958_gb300 import inputs
+    args = argparse.Namespace(config=0, kind="amg", interp=0, tol=1e-8, nvcyc="1,1,1", inner=0, smoother=0,
+                              agg=0, precision=0, batched=1, graph=1)
+    assert d["config"] == json.loads(json.dumps(bench._config(args, inputs.preset(0), 1)))
+    assert d["metric"] == bench.METRIC

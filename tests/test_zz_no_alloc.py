@@ -1,6 +1,6 @@
 """mgd_relres_noalloc: the residual check for callers that cannot allocate
-device memory (an application allocator that owns the device, a fixed
-memory footprint, graph assembly).  Its result must equal the true relative
+device memory (an application allocator that owns the device, a fixed,
+audited memory footprint).  Its result must equal the true relative
 residual that mgd_solve reports, call after call, although its work space is
 a fixed array inside the library instead of cudaMalloc'd memory.
 
@@ -45,6 +45,18 @@ def test_noalloc_relres_matches_solve_twice(lib):
         assert o[1] == pytest.approx(np.linalg.norm(s.b), rel=1e-12)
         assert o[0] == pytest.approx(o[2] * o[1], rel=1e-14)
     assert np.array_equal(outs[0], outs[1])
+    # the property the entry point exists for: after the first call on this
+    # device (which may load the module), calls allocate no device memory
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    alloc0 = torch.cuda.memory_allocated(dev)
+    out = torch.full((3,), -1.0, dtype=torch.float64, device=dev)
+    for _ in range(5):
+        assert lib.relres_noalloc(rp, ci, va, b, x, out) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(dev)[0] == free0
+    assert torch.cuda.memory_allocated(dev) == alloc0
+    assert out[2].item() == pytest.approx(rr, rel=1e-10)
     # a different input right after: nothing of the previous call leaks in
     out = torch.zeros(3, dtype=torch.float64, device=dev)
     assert lib.relres_noalloc(rp, ci, va, b, torch.zeros_like(x), out) == 0
@@ -59,4 +71,11 @@ def test_noalloc_rejects_oversize(lib):
     v = torch.zeros(1, dtype=torch.float64, device=dev)
     b = torch.zeros(n, dtype=torch.float64, device=dev)
     out = torch.zeros(3, dtype=torch.float64, device=dev)
-    assert lib.relres_noalloc(rp, ci, v, b, b, out) == 1
+    # the binding refuses before the call; the library itself refuses too
+    with pytest.raises(ValueError, match="outside"):
+        lib.relres_noalloc(rp, ci, v, b, b, out)
+    import ctypes as C
+    p = lambda t: C.c_void_p(t.data_ptr())
+    rc = lib.lib().mgd_relres_noalloc(n, p(rp), p(ci), p(v), p(b), p(b), p(out),
+                                      C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 1
