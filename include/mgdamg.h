@@ -250,7 +250,9 @@ int mgd_plan_info(mgd_ctx *c, int batch, int level, int *nbatches, int *depth, i
  * off, -1 selects all) on the context's stream.  Classes: 0 = level-0
  * smoothing+residual kernels of the V-cycle, 1 = the other V-cycle kernels,
  * 2 = the FGMRES operator SpMV and residual, 3 = Arnoldi vector kernels,
- * 4 = block-level updates of the block preconditioners.  The read call
+ * 4 = block-level updates of the block preconditioners, 5 = the fused
+ * modified Gram-Schmidt steps of the streaming orthogonalisation alone
+ * (j+1 launches per Arnoldi step, 32 n bytes each; inside class 3).  The read call
  * synchronises the stream and returns, for class cls (cls = 1 also counts
  * class 0, i.e. every V-cycle kernel), the launch count, the summed device
  * time and the summed algorithmic bytes.  V-cycle launches are also counted

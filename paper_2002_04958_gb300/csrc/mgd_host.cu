@@ -1289,6 +1289,15 @@ static void finalize_op(mgd_ctx* c, InvOp& op, cudaStream_t st) {
   MGD_CUDA(cudaStreamSynchronize(st));
 }
 
+// worker threads of the concurrent hierarchy setup: at most MGD_SETUP_THREADS,
+// at most MGD_SETUP_OVERSUB per host core
+#ifndef MGD_SETUP_THREADS
+#define MGD_SETUP_THREADS 16
+#endif
+#ifndef MGD_SETUP_OVERSUB
+#define MGD_SETUP_OVERSUB 1
+#endif
+
 // Setup of independent operators runs concurrently: each worker thread owns a
 // CUDA stream and builds whole hierarchies, so the many small host round
 // trips of one hierarchy (scan totals, PMIS rounds) overlap with the others.
@@ -1298,7 +1307,8 @@ static void finalize_ops_parallel(mgd_ctx* c, size_t first, size_t last) {
   if (nops == 0) return;
   MGD_CUDA(cudaStreamSynchronize(c->s));
   unsigned hw = std::thread::hardware_concurrency();
-  size_t nthreads = std::min<size_t>(nops, std::max<unsigned>(1u, std::min<unsigned>(hw ? hw : 4, 16)));
+  size_t nthreads = std::min<size_t>(
+      nops, std::max<unsigned>(1u, std::min<unsigned>((hw ? hw : 4) * MGD_SETUP_OVERSUB, MGD_SETUP_THREADS)));
   if (nthreads <= 1) {
     for (size_t k = first; k < last; ++k) finalize_op<T>(c, c->ops[k], c->s);
     return;
@@ -2694,7 +2704,11 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
         launch_arnoldi_coop(c->arn_nb, n, c->V, n, nv, c->w, c->hbuf, c->hbuf + 64, c->partial,
                             c->V + (size_t)(j + 1) * n, s);
       } else {
-        launch_mgs(n, c->V, n, nv, c->w, c->hbuf, c->hbuf + 64, c->partial, c->partial + kDotBlocks, s);
+        // class 5: the j+1 fused Gram-Schmidt steps alone (32 n bytes each)
+        int sid = -1;
+        launch_mgs(
+            n, c->V, n, nv, c->w, c->hbuf, c->hbuf + 64, c->partial, c->partial + kDotBlocks, s,
+            [&] { sid = c->prof.begin(s, 5); }, [&] { c->prof.end(sid, 5, 32.0 * n * nv, s); });
         launch_scale_by_norm(n, c->w, c->hbuf + 64, c->V + (size_t)(j + 1) * n, s);
       }
       c->prof.end(aid, 3, 8.0 * n * (4.0 * nv + 2.0 + 2.0), s);

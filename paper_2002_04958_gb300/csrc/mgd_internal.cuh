@@ -1,6 +1,7 @@
 // mgd_internal.cuh -- internal structures and kernel launchers of the
 // sm_103a solver library (not part of the C ABI).
 #pragma once
+#include <functional>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -462,7 +463,8 @@ void launch_copy_f64(int n, const double* a, double* b, cudaStream_t s);
 constexpr int kDotBlocks = 608;  // 4 x 152 SMs
 // modified Gram-Schmidt of w against V[:, 0..nv-1]: h[i], *nrm2 = ||w||^2
 void launch_mgs(int n, const double* V, long long ldv, int nv, double* w, double* h, double* nrm2, double* pa,
-                double* pb, cudaStream_t s);
+                double* pb, cudaStream_t s, const std::function<void()>& steps_begin = {},
+                const std::function<void()>& steps_end = {});
 void launch_scale_by_norm(int n, const double* w, const double* nrm2, double* v, cudaStream_t s);
 // the same modified Gram-Schmidt pass plus the scaling, as one cooperative
 // grid of nb blocks with w in shared memory (nb from arnoldi_coop_blocks; part:

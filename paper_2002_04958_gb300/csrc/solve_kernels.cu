@@ -8,6 +8,8 @@
 
 #include <cooperative_groups.h>
 
+#include <functional>
+
 namespace mgd {
 
 namespace cg = cooperative_groups;
@@ -375,6 +377,104 @@ __global__ void __launch_bounds__(kThreads) k_mgs_step(int n, const double* __re
   }
 }
 
+// The same two kernels on 16-byte vectors: every thread keeps kMgsU pairs of
+// each stream in flight per trip (the scalar loop above has one element of
+// each, too few bytes in flight per SM to cover HBM latency).  Used when n is
+// even and every vector starts on a 16-byte boundary; the sums run in a fixed
+// order per (n, grid), so every run gives the same bits.
+constexpr int kMgsU = 2;
+
+__global__ void __launch_bounds__(kThreads) k_dot_partial2(int n2, const double2* __restrict__ a,
+                                                           const double2* __restrict__ b,
+                                                           double* __restrict__ partial) {
+  MGD_PDL_ENTRY();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  double s0 = 0.0, s1 = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride * kMgsU) {
+    double2 x[kMgsU], y[kMgsU];
+#pragma unroll
+    for (int u = 0; u < kMgsU; ++u) {
+      const long long k = i + u * stride;
+      if (k < n2) {
+        x[u] = a[k];
+        y[u] = b[k];
+      } else {
+        x[u] = make_double2(0.0, 0.0);
+        y[u] = x[u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kMgsU; ++u) {
+      s0 += x[u].x * y[u].x;
+      s1 += x[u].y * y[u].y;
+    }
+  }
+  double s = s0 + s1;
+  __shared__ double sh[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[k];
+    partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_mgs_step2(int n2, const double2* __restrict__ vi,
+                                                        const double2* __restrict__ vnext, double2* __restrict__ w,
+                                                        const double* __restrict__ pin, int nb,
+                                                        double* __restrict__ pout, double* __restrict__ hout) {
+  MGD_PDL_ENTRY();
+  const double h = block_sum_partials(pin, nb);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *hout = h;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  double s0 = 0.0, s1 = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride * kMgsU) {
+    double2 ww[kMgsU], a[kMgsU], c[kMgsU];
+#pragma unroll
+    for (int u = 0; u < kMgsU; ++u) {
+      const long long k = i + u * stride;
+      if (k < n2) {
+        ww[u] = w[k];
+        a[u] = __ldcs(vi + k);
+        c[u] = vnext ? vnext[k] : make_double2(0.0, 0.0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kMgsU; ++u) {
+      const long long k = i + u * stride;
+      if (k < n2) {
+        double2 r;
+        r.x = ww[u].x - h * a[u].x;
+        r.y = ww[u].y - h * a[u].y;
+        w[k] = r;
+        if (vnext) {
+          s0 += c[u].x * r.x;
+          s1 += c[u].y * r.y;
+        } else {
+          s0 += r.x * r.x;
+          s1 += r.y * r.y;
+        }
+      }
+    }
+  }
+  double s = s0 + s1;
+  __shared__ double sh[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[k];
+    pout[blockIdx.x] = t;
+  }
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
 __global__ void k_sum_partials(const double* __restrict__ partial, int nb, double* __restrict__ out) {
   MGD_PDL_ENTRY();
   double r = block_sum_partials(partial, nb);
@@ -385,18 +485,32 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int nb, doubl
 // w orthogonalised in place, *nrm2 = ||w||^2.  pa / pb: partial buffers of
 // kDotBlocks entries each (ping-pong).
 void launch_mgs(int n, const double* V, long long ldv, int nv, double* w, double* h, double* nrm2, double* pa,
-                double* pb, cudaStream_t s) {
+                double* pb, cudaStream_t s, const std::function<void()>& steps_begin,
+                const std::function<void()>& steps_end) {
   int nb = std::min(kDotBlocks, std::max(1, cdiv(n, kThreads)));
-  launch_k(k_dot_partial, dim3(nb), dim3(kThreads), 0, s, n, V, w, pa);
+  // 16-byte vectors when every basis vector and w start on a 16-byte boundary
+  const bool vec = (n % 2 == 0) && (ldv % 2 == 0) && aligned16(V) && aligned16(w);
+  const int n2 = n / 2;
+  if (vec)
+    launch_k(k_dot_partial2, dim3(nb), dim3(kThreads), 0, s, n2, (const double2*)V, (const double2*)w, pa);
+  else
+    launch_k(k_dot_partial, dim3(nb), dim3(kThreads), 0, s, n, V, w, pa);
   MGD_LAUNCH_CHECK();
   double* pin = pa;
   double* pout = pb;
+  if (steps_begin) steps_begin();
   for (int i = 0; i < nv; ++i) {
     const double* vnext = i + 1 < nv ? V + (long long)(i + 1) * ldv : nullptr;
-    launch_k(k_mgs_step, dim3(nb), dim3(kThreads), 0, s, n, V + (long long)i * ldv, vnext, w, pin, nb, pout, h + i);
+    if (vec)
+      launch_k(k_mgs_step2, dim3(nb), dim3(kThreads), 0, s, n2, (const double2*)(V + (long long)i * ldv),
+               (const double2*)vnext, (double2*)w, pin, nb, pout, h + i);
+    else
+      launch_k(k_mgs_step, dim3(nb), dim3(kThreads), 0, s, n, V + (long long)i * ldv, vnext, w, pin, nb, pout,
+               h + i);
     MGD_LAUNCH_CHECK();
     std::swap(pin, pout);
   }
+  if (steps_end) steps_end();
   launch_k(k_sum_partials, dim3(1), dim3(kThreads), 0, s, pin, nb, nrm2);
   MGD_LAUNCH_CHECK();
 }
@@ -515,8 +629,38 @@ void launch_arnoldi_coop(int nb, int n, const double* V, long long ldv, int nv, 
   MGD_LAUNCH_CHECK();
 }
 
+// the same on 16-byte vectors, kMgsU pairs per thread and trip (n even, both vectors 16-byte aligned)
+__global__ void __launch_bounds__(kThreads) k_scale_by_norm2(int n2, const double2* __restrict__ w,
+                                                             const double* __restrict__ nrm2,
+                                                             double2* __restrict__ v) {
+  MGD_PDL_ENTRY();
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) {
+    double h = sqrt(*nrm2);
+    s_inv = h != 0.0 ? 1.0 / h : 0.0;
+  }
+  __syncthreads();
+  const double r = s_inv;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride * kMgsU) {
+    double2 a[kMgsU];
+#pragma unroll
+    for (int u = 0; u < kMgsU; ++u)
+      if (i + u * stride < n2) a[u] = w[i + u * stride];
+#pragma unroll
+    for (int u = 0; u < kMgsU; ++u)
+      if (i + u * stride < n2) v[i + u * stride] = make_double2(a[u].x * r, a[u].y * r);
+  }
+}
+
 void launch_scale_by_norm(int n, const double* w, const double* nrm2, double* v, cudaStream_t s) {
-  launch_k(k_scale_by_norm, dim3(cdiv(n, kThreads)), dim3(kThreads), 0, s, n, w, nrm2, v);
+  if (n % 2 == 0 && aligned16(w) && aligned16(v)) {
+    const int n2 = n / 2;
+    const int nb = std::min(4 * kDotBlocks, std::max(1, cdiv(n2, kThreads * kMgsU)));
+    launch_k(k_scale_by_norm2, dim3(nb), dim3(kThreads), 0, s, n2, (const double2*)w, nrm2, (double2*)v);
+  } else {
+    launch_k(k_scale_by_norm, dim3(cdiv(n, kThreads)), dim3(kThreads), 0, s, n, w, nrm2, v);
+  }
   MGD_LAUNCH_CHECK();
 }
 

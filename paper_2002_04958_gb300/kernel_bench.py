@@ -23,6 +23,7 @@ if ROOT not in sys.path:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--dims", default=None, help="grid of the workload, e.g. 64,64,64 (default: the workload's)")
     ap.add_argument("--kind", default="amg")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--batched", type=int, default=0)
@@ -40,7 +41,7 @@ def main():
     from paper_2002_04958_gb300 import inputs, mgdamg
     from paper_2002_04958_gb300.build import build
     build()
-    s = inputs.preset(args.config)
+    s = inputs.preset(args.config, dims=[int(t) for t in args.dims.split(",")] if args.dims else None)
     slv = mgdamg.Solver(precision=args.precision, batched=args.batched, use_graph=args.graph,
                         autotune=0 if args.no_autotune else 1, interp_type=args.interp,
                         inner_mode=args.inner)
@@ -51,7 +52,8 @@ def main():
     for _ in range(args.applies):
         slv.precond_apply(v)
     torch.cuda.synchronize()
-    out = {"workload": inputs.PRESET_NAMES[args.config], "kind": args.kind, "n": s.n, "applies": args.applies}
+    out = {"workload": inputs.PRESET_NAMES[args.config], "dims": list(s.dims), "kind": args.kind, "n": s.n,
+           "applies": args.applies}
     if args.timing:
         for cls, name in [(0, "level0_smoothing"), (1, "vcycle_all"), (4, "block_updates")]:
             nl, ms, by = slv.profile_read(cls)

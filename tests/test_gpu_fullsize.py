@@ -159,9 +159,9 @@ def test_config4_adjoint_full_size(gpu):
     AMG, L = ||x||^2.  The forward iteration count at 1e-8 equals the stored
     oracle solve's; x, lambda = dL/db and dL/dvals from the torch.autograd
     Function (backward: FGMRES with the transposed V-cycle) match the stored
-    oracle values; central differences (h = 1e-6, relative perturbations of
-    the values) on 32 seeded directions match the analytic directional
-    derivative to 1e-5."""
+    oracle values; central differences (h = 1e-6, relative perturbations
+    vals (.) (1 +- h d) along 32 seeded unit directions d ~ N(0, 1) / ||.||)
+    match the analytic directional derivative to 1e-5."""
     rec = _golden("oracle_adjoint_G4_256x256_amg.json")
     s = I.preset(4)
     assert s.n == rec["n"] and s.nnz == rec["nnz"]
@@ -186,15 +186,31 @@ def test_config4_adjoint_full_size(gpu):
     close(x, rec["x_index"], rec["x_sample"], rec["x_max_abs"], rec["x_norm2"], 1e-9)
     close(b.grad, rec["lambda_index"], rec["lambda_sample"], rec["lambda_max_abs"], rec["lambda_norm2"], 1e-8)
     close(vals.grad, rec["grad_index"], rec["grad_sample"], rec["grad_max_abs"], rec["grad_norm2"], 1e-8)
+    # L(+) - L(-) = (x+ - x-) . (x+ + x-).  Along a unit direction the values
+    # move by ~1e-9 relative, so L changes by ~1e-12 of itself: two separate
+    # solves to 1e-13 would differ by their solve errors more than by that.
+    # Instead x- is solved to 1e-13 and the difference from its own system,
+    # A+ (x+ - x-) = -(A+ - A-) x-, whose right-hand side is a product with
+    # 2 h vals (.) d (no cancellation): x+ = x- + (x+ - x-) then solves
+    # A+ x+ = A- x-, i.e. both points see the same right-hand side b - r(x-),
+    # which moves L's derivative by a relative kappa * 1e-13 only.
+    import scipy.sparse as sp
+    fds = gpu.Solver(max_it=6000, batched=1, use_graph=1).setup_system(s, "amg")
     rng = np.random.default_rng(0)
     h = 1e-6
     gv = vals.grad.detach()
     for _ in range(32):
         d = rng.standard_normal(s.nnz)
         d /= np.linalg.norm(d)
-        dv = torch.from_numpy(s.val * d).cuda()
-        lp = gpu.mgd_solve(vals.detach() + h * dv, b.detach(), slv, 1e-13)
-        lm = gpu.mgd_solve(vals.detach() - h * dv, b.detach(), slv, 1e-13)
-        fd = ((lp * lp).sum() - (lm * lm).sum()).item() / (2 * h)
+        dvn = s.val * d
+        dv = torch.from_numpy(dvn).cuda()
+        fds.update_values(vals.detach() - h * dv)
+        xm, _, _, rcm = fds.solve(b.detach(), tol=1e-13)
+        xmn = xm.cpu().numpy()
+        rhs = -(sp.csr_matrix((2 * h * dvn, s.col, s.rowptr), shape=(s.n, s.n)) @ xmn)
+        fds.update_values(vals.detach() + h * dv)
+        dl, _, _, rcd = fds.solve(torch.from_numpy(rhs), tol=1e-10)
+        dln = dl.cpu().numpy()
+        fd = float(np.dot(dln, 2 * xmn + dln)) / (2 * h)
         an = (gv * dv).sum().item()
         assert fd == pytest.approx(an, rel=1e-5)
