@@ -331,7 +331,7 @@ def run_ours(args):
     # device for the transposed solve, the gradient comes to the host
     d_x = torch.empty(sysm.n, dtype=torch.float64, device=dev) if args.adjoint else None
     h_g = torch.empty(sysm.nnz, dtype=torch.float64).pin_memory() if args.adjoint else None
-    e2e_ms = []
+    e2e_ms, e2e_parts = [], []
     for k in range(0 if args.no_e2e else max(2, args.steps // 2) + 1):
         sync()
         t_a = time.perf_counter()
@@ -339,8 +339,13 @@ def run_ours(args):
         d_ci.copy_(h_ci, non_blocking=True)
         d_va.copy_(h_va, non_blocking=True)
         slv.setup(sysm.G, sysm.N, d_rp, d_ci, d_va, args.kind)
+        t_s = time.perf_counter()
         h_x.zero_()
         slv.solve_host_ptr(h_b.data_ptr(), h_x.data_ptr(), tol=args.tol)
+        if k > 0:
+            st_e = slv.stats()
+            e2e_parts.append(((t_s - t_a) * 1e3, st_e["setup_ms"], (time.perf_counter() - t_s) * 1e3,
+                              st_e["solve_ms"]))
         if args.adjoint:
             d_x.copy_(h_x, non_blocking=True)
             lam_e, _, _ = slv.solve_transpose(2.0 * d_x, tol=args.tol)
@@ -468,7 +473,12 @@ def run_ours(args):
         "e2e": {"value": round(statistics.median(e2e_ms) / 1e3, 6) if e2e_ms else None, "unit": "s",
                 "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "path": "mgd_setup on device copies of pinned host CSR arrays + mgd_solve_host (host b, host x)"},
+                "path": "mgd_setup on device copies of pinned host CSR arrays + mgd_solve_host (host b, host x)",
+                "parts_ms_median": ({"copies_and_setup": round(statistics.median(p[0] for p in e2e_parts), 3),
+                                     "setup_inside": round(statistics.median(p[1] for p in e2e_parts), 3),
+                                     "solve_host_call": round(statistics.median(p[2] for p in e2e_parts), 3),
+                                     "solve_inside": round(statistics.median(p[3] for p in e2e_parts), 3)}
+                                    if e2e_parts else None)},
         "gpu_launches": launches,
         "clocks": clk,
         "stats": dict({k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()},

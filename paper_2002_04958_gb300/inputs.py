@@ -281,7 +281,7 @@ PRESET_NAMES = {
     0: "G1_3T_32x32_monolithicAMG",
     1: "G1_3T_1024x1024_inclusion_Schur1",
     2: "G20_256x256_blockdiag_fp32vcycle",
-    3: "G20_96x96x96_Schur2_fp32vcycle",
+    3: "G20_96x96x96_Schur2",
     4: "G4_256x256_adjoint",
     5: "G1_3T_1024x1024_inclusion_diffuseE_Schur1",
     6: "G20_256x256_diffuseE_Schur2_cycles311",
