@@ -137,6 +137,15 @@ int mgd_create(mgd_ctx **out, const mgd_opts *o, void *stream);
 int mgd_setup(mgd_ctx *c, int G, int N, int n, int nnz, const int *d_rowptr, const int *d_colidx,
               const double *d_vals, int kind);
 
+/* As mgd_setup with the CSR arrays in host memory: h_rowptr[n+1],
+ * h_colidx[nnz], h_vals[nnz] are copied to the device (in 32 MiB chunks over
+ * four copy streams, so several copy engines run at once; page-locked host
+ * memory gives the full host-to-device bandwidth, pageable memory is staged by
+ * the driver), then set up exactly as mgd_setup does.  The host arrays are only
+ * read, and may be reused once the call returns.  Same errors as mgd_setup. */
+int mgd_setup_host(mgd_ctx *c, int G, int N, int n, int nnz, const int *h_rowptr, const int *h_colidx,
+                   const double *h_vals, int kind);
+
 /* Same sparsity pattern, new values d_vals[nnz]: re-runs the whole numeric
  * setup (the coarse patterns may change with the values). */
 int mgd_update_values(mgd_ctx *c, const double *d_vals);

@@ -202,7 +202,7 @@ struct Hier {
 // threads add concurrently, so the hierarchy phases can sum past wall time)
 enum SetupPhase {
   SP_STRENGTH = 0, SP_PMIS, SP_INTERP, SP_TRANSPOSE, SP_AP, SP_RAP, SP_FINALIZE, SP_COARSE,
-  SP_VALIDATE, SP_BLOCKS, SP_HIERARCHIES, SP_PCTL, SP_PROGRAM, SP_KRYLOV, SP_COLOUR, SP_COUNT = 16
+  SP_VALIDATE, SP_BLOCKS, SP_HIERARCHIES, SP_PCTL, SP_PROGRAM, SP_KRYLOV, SP_COLOUR, SP_H2D, SP_COUNT = 16
 };
 struct PhaseClock {
   std::mutex mu;
@@ -1169,6 +1169,7 @@ struct mgd_ctx {
   bool graph_ok = false;
   bool capturing = false;            // run_program is being recorded into c->graph
   cudaStream_t s_body = nullptr;     // stream that records conditional-node bodies
+  cudaStream_t s_copy[4] = {nullptr, nullptr, nullptr, nullptr};  // host-to-device copies of mgd_setup_host
   long long graph_kernels = 0;
   long long napply = 0, napplyT = 0; // preconditioner applies since setup (forward, transposed)
   int arn_nb = 0;                    // blocks of the cooperative Arnoldi grid (0: streaming kernels)
@@ -2864,6 +2865,65 @@ int mgd_setup(mgd_ctx* c, int G, int N, int n, int nnz, const int* d_rowptr, con
   });
 }
 
+// Host arrays to the device in 32 MiB chunks spread over the context's copy
+// streams (several copy engines at once), joined back into the context
+// stream; the destination is stream-ordered memory of the context stream.
+static void h2d_spread(mgd_ctx* c, void* dst, const void* src, size_t bytes, int& next) {
+  const size_t chunk = (size_t)32 << 20;
+  for (size_t o = 0; o < bytes; o += chunk) {
+    cudaStream_t cs = c->s_copy[next++ % 4];
+    MGD_CUDA(cudaMemcpyAsync((char*)dst + o, (const char*)src + o, std::min(chunk, bytes - o),
+                             cudaMemcpyHostToDevice, cs));
+  }
+}
+
+int mgd_setup_host(mgd_ctx* c, int G, int N, int n, int nnz, const int* h_rowptr, const int* h_colidx,
+                   const double* h_vals, int kind) {
+  return guarded(c, [&]() -> int {
+    if (G < 1 || N < 1 || n != (G + 2) * N || nnz < n || !h_rowptr || !h_colidx || !h_vals || kind < 0 ||
+        kind > MGD_BLT || G + 1 > kMaxTerms - 1)
+      throw Error{MGD_EINVAL, "invalid sizes or kind"};
+    for (auto& cs : c->s_copy)
+      if (!cs) MGD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    // staging copies (stream-ordered on the context stream, released after
+    // the setup, which keeps its own copy of the operator)
+    Scratch sc(c->s);
+    int* rp = sc.alloc<int>((size_t)n + 1);
+    int* ci = sc.alloc<int>(nnz);
+    double* v = sc.alloc<double>(nnz);
+    auto th = std::chrono::steady_clock::now();
+    cudaEvent_t ready = nullptr, done[4] = {nullptr, nullptr, nullptr, nullptr};
+    MGD_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    for (auto& e : done) MGD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    MGD_CUDA(cudaEventRecord(ready, c->s));
+    for (auto cs : c->s_copy) MGD_CUDA(cudaStreamWaitEvent(cs, ready, 0));
+    int next = 0;
+    h2d_spread(c, v, h_vals, sizeof(double) * (size_t)nnz, next);
+    h2d_spread(c, ci, h_colidx, sizeof(int) * (size_t)nnz, next);
+    h2d_spread(c, rp, h_rowptr, sizeof(int) * ((size_t)n + 1), next);
+    for (int k = 0; k < 4; ++k) {
+      MGD_CUDA(cudaEventRecord(done[k], c->s_copy[k]));
+      MGD_CUDA(cudaStreamWaitEvent(c->s, done[k], 0));
+    }
+    cudaEventDestroy(ready);
+    for (auto e : done) cudaEventDestroy(e);
+    MGD_CUDA(cudaStreamSynchronize(c->s));
+    const double h2d_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th).count();
+    free_setup(c);
+    c->G = G;
+    c->N = N;
+    c->n = n;
+    c->nnz = nnz;
+    c->kind = kind;
+    do_setup(c, rp, ci, v);
+    {
+      std::lock_guard<std::mutex> lk(c->phases.mu);
+      c->phases.ms[SP_H2D] = h2d_ms;  // after do_setup, which resets the phase clock
+    }
+    return MGD_OK;
+  });
+}
+
 int mgd_update_values(mgd_ctx* c, const double* d_vals) {
   return guarded(c, [&]() -> int {
     if (!c->ready) throw Error{MGD_ESTATE, "no setup"};
@@ -3199,6 +3259,8 @@ void mgd_destroy(mgd_ctx* c) {
   if (!c) return;
   free_setup(c);
   if (c->s_body) cudaStreamDestroy(c->s_body);
+  for (auto cs : c->s_copy)
+    if (cs) cudaStreamDestroy(cs);
   if (c->hpin) cudaFreeHost(c->hpin);
   c->pool.destroy();
   delete c;

@@ -1065,6 +1065,7 @@ void launch_spgemm_ub(int n, const int* xrp, const int* xci, const int* yrp, int
 constexpr int kThrSlots = 32;
 constexpr int kThrRows = 128;
 constexpr int kThrMaxProducts = 1024;
+constexpr int kThrBatch = 8;  // entries of a row of Y loaded ahead of the merge
 
 __global__ void __launch_bounds__(kThrRows) k_spgemm_thread(int n, const int* xrp, const int* xci, const double* xv,
                                                             const int* yrp, const int* yci, const double* yv,
@@ -1080,13 +1081,35 @@ __global__ void __launch_bounds__(kThrRows) k_spgemm_thread(int n, const int* xr
   bool over = L > kThrMaxProducts;
   int u = 0;  // columns so far, ascending in s_c[0 .. u)
   const int xe = over ? xrp[i] : xrp[i + 1];
-  for (int p = xrp[i]; p < xe && !over; ++p) {
-    const int k = xci[p];
+  // the row of Y for the next entry of X is located one entry ahead, and the
+  // entries of a row of Y are loaded kThrBatch at a time before they are
+  // merged, so the global loads overlap instead of waiting one by one; the
+  // products are still merged in expansion order
+  int p = xrp[i];
+  int nk = p < xe ? xci[p] : 0;
+  int nyb = p < xe ? yrp[nk] : 0, nye = p < xe ? yrp[nk + 1] : 0;
+  for (; p < xe && !over; ++p) {
     const double x = xv[p];
-    const int ye = yrp[k + 1];
-    for (int q = yrp[k]; q < ye; ++q) {
-      const int c = yci[q];
-      const double pr = __dmul_rn(x, yv[q]);
+    const int yb = nyb, ye = nye;
+    if (p + 1 < xe) {
+      nk = xci[p + 1];
+      nyb = yrp[nk];
+      nye = yrp[nk + 1];
+    }
+    for (int q0 = yb; q0 < ye && !over; q0 += kThrBatch) {
+      int bc[kThrBatch];
+      double bv[kThrBatch];
+#pragma unroll
+      for (int j = 0; j < kThrBatch; ++j)
+        if (q0 + j < ye) {
+          bc[j] = yci[q0 + j];
+          bv[j] = yv[q0 + j];
+        }
+#pragma unroll
+      for (int j = 0; j < kThrBatch; ++j) {
+      if (q0 + j >= ye || over) break;
+      const int c = bc[j];
+      const double pr = __dmul_rn(x, bv[j]);
       int lo = 0, hi = u;  // first entry with column >= c
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
@@ -1108,6 +1131,7 @@ __global__ void __launch_bounds__(kThrRows) k_spgemm_thread(int n, const int* xr
       s_c[lo][t] = c;
       s_v[lo][t] = pr;
       ++u;
+      }
     }
   }
   if (over) {

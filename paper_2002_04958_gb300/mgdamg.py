@@ -26,7 +26,7 @@ ENTRY_POINTS = ["mgd_opts_default", "mgd_create", "mgd_setup", "mgd_update_value
                 "mgd_op_info", "mgd_level_info", "mgd_level_export", "mgd_block_vector", "mgd_coupling_dropped",
                 "mgd_profile_enable", "mgd_profile_read", "mgd_kernel_launches", "mgd_last_error", "mgd_destroy", "mgd_plan_info",
                 "mgd_setup_phases", "mgd_op_cycles", "mgd_level_keys", "mgd_precond_bench",
-                "mgd_relres_noalloc", "mgd_profile_read_fp64", "mgd_fp64_issue_rate"]
+                "mgd_relres_noalloc", "mgd_profile_read_fp64", "mgd_fp64_issue_rate", "mgd_setup_host"]
 
 
 class MgdOpts(C.Structure):
@@ -92,6 +92,7 @@ def lib():
             "mgd_fp64_issue_rate": (I, [P, pD]),
             "mgd_kernel_launches": (C.c_longlong, []),
             "mgd_relres_noalloc": (I, [I, P, P, P, P, P, P, P]),
+            "mgd_setup_host": (I, [P, I, I, I, I, P, P, P, I]),
             "mgd_plan_info": (I, [P, I, I, pI, pI, pI, pI, pI, pI, pI, pI]),
             "mgd_setup_phases": (I, [P, P, I]),
             "mgd_last_error": (C.c_char_p, [P]),
@@ -207,7 +208,25 @@ class Solver:
             raise MgdError(rc, "mgd_create failed")
         self.h = h
         self.n = 0
+        self.nnz = 0
+        self.device = torch.device("cuda", torch.cuda.current_device())
         self._keep = []
+
+    def _vec(self, a, length, name, dtype=None):
+        """a as a contiguous CUDA tensor on the context's device with `length`
+        entries (float64 unless dtype is given): the library reads and writes
+        these buffers through raw pointers, so a short or misplaced one is
+        refused here instead of being read out of bounds."""
+        t = self.torch
+        a = a if isinstance(a, t.Tensor) else t.as_tensor(a)
+        a = a.to(device=self.device, dtype=dtype or t.float64).contiguous()
+        if a.dim() != 1 or a.numel() != length:
+            raise ValueError(f"{name}: expected {length} entries, got shape {tuple(a.shape)}")
+        return a
+
+    def _need_setup(self):
+        if self.n <= 0:
+            raise MgdError(9, "call setup first")
 
     def _order(self):
         self.stream.wait_stream(self.torch.cuda.current_stream())
@@ -220,14 +239,41 @@ class Solver:
     def setup(self, G, N, rowptr, col, val, kind):
         t = self.torch
         kind = KINDS[kind] if isinstance(kind, str) else kind
-        rowptr = rowptr.to(device="cuda", dtype=t.int32).contiguous()
-        col = col.to(device="cuda", dtype=t.int32).contiguous()
-        val = val.to(device="cuda", dtype=t.float64).contiguous()
+        rowptr = rowptr.to(device=self.device, dtype=t.int32).contiguous()
+        col = col.to(device=self.device, dtype=t.int32).contiguous()
+        val = self._vec(val, col.numel(), "val")
         n = rowptr.numel() - 1
         self._order()
         self._check(lib().mgd_setup(self.h, G, N, n, col.numel(), _ptr(rowptr), _ptr(col), _ptr(val), kind))
         self.G, self.N, self.n, self.nnz, self.kind = G, N, n, col.numel(), kind
         self.rowptr, self.col = rowptr, col
+        return self
+
+    def setup_host(self, G, N, rowptr, col, val, kind):
+        """Setup from host arrays (numpy or CPU torch tensors: int32 rowptr/col,
+        float64 val); the library copies them to the device."""
+        t = self.torch
+        kind = KINDS[kind] if isinstance(kind, str) else kind
+
+        def host(a, dt, tdt):
+            if isinstance(a, t.Tensor):
+                if a.is_cuda or a.dtype != tdt or not a.is_contiguous():
+                    raise ValueError("setup_host wants contiguous CPU tensors of dtype %s" % tdt)
+                return a, a.data_ptr()
+            a = np.ascontiguousarray(a, dt)
+            return a, a.ctypes.data
+        rp, prp = host(rowptr, np.int32, t.int32)
+        ci, pci = host(col, np.int32, t.int32)
+        va, pva = host(val, np.float64, t.float64)
+        n = int(rp.shape[0]) - 1
+        nnz = int(ci.shape[0])
+        if int(va.shape[0]) != nnz:
+            raise ValueError("setup_host: col and val lengths differ")
+        self._order()
+        self._check(lib().mgd_setup_host(self.h, G, N, n, nnz, C.c_void_p(prp), C.c_void_p(pci), C.c_void_p(pva),
+                                         kind))
+        self.G, self.N, self.n, self.nnz, self.kind = G, N, n, nnz, kind
+        self.rowptr, self.col = None, None
         return self
 
     def setup_system(self, sysm, kind):
@@ -236,14 +282,16 @@ class Solver:
                           t.from_numpy(sysm.val), kind)
 
     def update_values(self, val):
-        val = val.to(device="cuda", dtype=self.torch.float64).contiguous()
+        self._need_setup()
+        val = self._vec(val, self.nnz, "val")
         self._order()
         self._check(lib().mgd_update_values(self.h, _ptr(val)))
 
     def solve(self, b, tol=1e-8, x0=None, allow_noconv=False):
         t = self.torch
-        b = b.to(device="cuda", dtype=t.float64).contiguous()
-        x = t.zeros_like(b) if x0 is None else x0.to(device="cuda", dtype=t.float64).clone()
+        self._need_setup()
+        b = self._vec(b, self.n, "b")
+        x = t.zeros_like(b) if x0 is None else self._vec(x0, self.n, "x0").clone()
         it, rr = C.c_int(), C.c_double()
         self._order()
         rc = self._check(lib().mgd_solve(self.h, _ptr(b), tol, _ptr(x), C.byref(it), C.byref(rr)),
@@ -252,8 +300,11 @@ class Solver:
 
     def solve_host(self, b, tol=1e-8, x0=None):
         """Host buffers in and out (numpy float64); copies inside the library."""
-        b = np.ascontiguousarray(b, np.float64)
-        x = np.zeros_like(b) if x0 is None else np.array(x0, np.float64)
+        self._need_setup()
+        b = np.ascontiguousarray(b, np.float64).reshape(-1)
+        x = np.zeros_like(b) if x0 is None else np.array(x0, np.float64).reshape(-1)
+        if b.size != self.n or x.size != self.n:
+            raise ValueError(f"solve_host: b and x0 need {self.n} entries")
         it, rr = C.c_int(), C.c_double()
         self._order()
         self._check(lib().mgd_solve_host(self.h, b.ctypes.data_as(C.c_void_p), tol, x.ctypes.data_as(C.c_void_p),
@@ -261,6 +312,10 @@ class Solver:
         return x, it.value, rr.value
 
     def solve_host_ptr(self, b_ptr, x_ptr, tol=1e-8):
+        """Raw host addresses of n float64 values each (b in; x: initial guess
+        in, solution out), e.g. the data_ptr() of page-locked CPU tensors; the
+        caller vouches for their size."""
+        self._need_setup()
         it, rr = C.c_int(), C.c_double()
         self._order()
         self._check(lib().mgd_solve_host(self.h, C.c_void_p(b_ptr), tol, C.c_void_p(x_ptr), C.byref(it),
@@ -269,7 +324,8 @@ class Solver:
 
     def solve_transpose(self, g, tol=1e-8):
         t = self.torch
-        g = g.to(device="cuda", dtype=t.float64).contiguous()
+        self._need_setup()
+        g = self._vec(g, self.n, "g")
         lam = t.zeros_like(g)
         it, rr = C.c_int(), C.c_double()
         self._order()
@@ -277,13 +333,17 @@ class Solver:
         return lam, it.value, rr.value
 
     def grad_values(self, x, lam):
-        g = self.torch.empty(self.nnz, dtype=self.torch.float64, device="cuda")
+        self._need_setup()
+        x = self._vec(x, self.n, "x")
+        lam = self._vec(lam, self.n, "lam")
+        g = self.torch.empty(self.nnz, dtype=self.torch.float64, device=self.device)
         self._order()
         self._check(lib().mgd_grad_values(self.h, _ptr(x), _ptr(lam), _ptr(g)))
         return g
 
     def precond_apply(self, v):
-        v = v.to(device="cuda", dtype=self.torch.float64).contiguous()
+        self._need_setup()
+        v = self._vec(v, self.n, "v")
         z = self.torch.empty_like(v)
         self._order()
         self._check(lib().mgd_precond_apply(self.h, _ptr(v), _ptr(z)))
@@ -291,7 +351,8 @@ class Solver:
 
     def precond_bench(self, v, count=100):
         """(ms per apply, algorithmic bytes per apply) of `count` preconditioner applies back to back."""
-        v = v.to(device="cuda", dtype=self.torch.float64).contiguous()
+        self._need_setup()
+        v = self._vec(v, self.n, "v")
         z = self.torch.empty_like(v)
         ms, by = C.c_double(), C.c_double()
         self._order()
@@ -365,7 +426,7 @@ class Solver:
 
     SETUP_PHASES = ["strength", "pmis", "interp", "transpose", "AP", "RAP", "finalize", "coarse_inverse",
                     "validate", "blocks", "hierarchies_wall", "pctl", "program_autotune", "krylov_graph",
-                    "gs_colouring"]
+                    "gs_colouring", "h2d_copies"]
 
     def setup_phases(self):
         ms = np.zeros(16)

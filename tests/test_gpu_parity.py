@@ -261,6 +261,30 @@ def test_edge_cases(gpu):
         assert e.value.code == 1 and "row pointer" in str(e.value), k
 
 
+@pytest.mark.parametrize("kind", ["amg", "schur2"])
+def test_setup_from_host_buffers(gpu, kind):
+    # mgd_setup_host (chunked copies over several streams) sets up exactly what
+    # mgd_setup does from device arrays: same hierarchy, same solution bits;
+    # pageable numpy arrays and page-locked tensors both work
+    s = _system(CASES[3])
+    dev = gpu.Solver().setup_system(s, kind)
+    xd, itd, _, _ = dev.solve(torch.from_numpy(s.b))
+    for pinned in (False, True):
+        if pinned:
+            rp, ci, va = (torch.from_numpy(a).pin_memory() for a in (s.rowptr, s.col, s.val))
+        else:
+            rp, ci, va = s.rowptr, s.col, s.val
+        hs = gpu.Solver().setup_host(s.G, s.N, rp, ci, va, kind)
+        xh, ith, _, _ = hs.solve(torch.from_numpy(s.b))
+        assert ith == itd and torch.equal(xh, xd)
+        for k in range(dev.stats()["n_ops"]):
+            a, b = dev.level(k, 0), hs.level(k, 0)
+            assert np.array_equal(a["v"], b["v"]) and np.array_equal(a["ci"], b["ci"])
+    with pytest.raises(gpu.MgdError) as e:
+        gpu.Solver().setup_host(s.G, s.N + 1, s.rowptr, s.col, s.val, kind)
+    assert e.value.code == 1
+
+
 def test_solve_host_buffers(gpu, orc):
     s = _system(CASES[0])
     slv = gpu.Solver().setup_system(s, "schur2")

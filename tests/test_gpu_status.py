@@ -129,3 +129,20 @@ def test_iteration_cap_keeps_last_iterate(gpu, orc):
     xo, ito, rro, st, _ = orc.fgmres(Ao, s.b, orc.Block(Ao, s.G, s.N, "amg"), tol=1e-14, maxit=4)
     assert st == 1 and ito == 4
     assert np.abs(x.cpu().numpy() - xo).max() <= 1e-10 * np.abs(xo).max()
+
+
+def test_binding_refuses_wrong_lengths(gpu):
+    # the library reads these buffers through raw pointers: the binding
+    # refuses a short vector before the call
+    s = I.make_system(1, (9, 7))
+    slv = gpu.Solver().setup_system(s, "amg")
+    short = torch.zeros(s.n - 1, dtype=torch.float64)
+    for call in (lambda: slv.solve(short), lambda: slv.precond_apply(short),
+                 lambda: slv.update_values(torch.zeros(s.nnz - 1, dtype=torch.float64)),
+                 lambda: slv.grad_values(short, short), lambda: slv.solve_host(short.numpy())):
+        with pytest.raises(ValueError):
+            call()
+    with pytest.raises(gpu.MgdError):
+        gpu.Solver().solve(torch.zeros(4, dtype=torch.float64))
+    x, it, rr, rc = slv.solve(torch.from_numpy(s.b))   # the context is unharmed
+    assert rc == 0 and rr <= 1e-8
