@@ -2710,7 +2710,8 @@ static int fgmres(mgd_ctx* c, const double* b, double* x, double tol, bool trans
         launch_mgs(
             n, c->V, n, nv, c->w, c->hbuf, c->hbuf + 64, c->partial, c->partial + kDotBlocks, s,
             [&] { sid = c->prof.begin(s, 5); }, [&] { c->prof.end(sid, 5, 32.0 * n * nv, s); });
-        launch_scale_by_norm(n, c->w, c->hbuf + 64, c->V + (size_t)(j + 1) * n, s);
+        // the last step (index nv-1) ran backwards when nv-1 is odd: run the opposite way
+        launch_scale_by_norm(n, c->w, c->hbuf + 64, c->V + (size_t)(j + 1) * n, s, ((nv - 1) & 1) ? 0 : 1);
       }
       c->prof.end(aid, 3, 8.0 * n * (4.0 * nv + 2.0 + 2.0), s);
       MGD_CUDA(cudaMemcpyAsync(hp, c->hbuf, 65 * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -465,7 +465,9 @@ constexpr int kDotBlocks = 608;  // 4 x 152 SMs
 void launch_mgs(int n, const double* V, long long ldv, int nv, double* w, double* h, double* nrm2, double* pa,
                 double* pb, cudaStream_t s, const std::function<void()>& steps_begin = {},
                 const std::function<void()>& steps_end = {});
-void launch_scale_by_norm(int n, const double* w, const double* nrm2, double* v, cudaStream_t s);
+// rev: traverse the vectors backwards (the streaming Arnoldi alternates
+// directions between passes; 1 after a launch_mgs whose last step ran forwards)
+void launch_scale_by_norm(int n, const double* w, const double* nrm2, double* v, cudaStream_t s, int rev = 0);
 // the same modified Gram-Schmidt pass plus the scaling, as one cooperative
 // grid of nb blocks with w in shared memory (nb from arnoldi_coop_blocks; part:
 // (nv + 1) * nb doubles)

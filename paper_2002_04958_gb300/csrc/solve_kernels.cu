@@ -386,7 +386,7 @@ constexpr int kMgsU = 2;
 
 __global__ void __launch_bounds__(kThreads) k_dot_partial2(int n2, const double2* __restrict__ a,
                                                            const double2* __restrict__ b,
-                                                           double* __restrict__ partial) {
+                                                           double* __restrict__ partial, int rev) {
   MGD_PDL_ENTRY();
   const long long stride = (long long)gridDim.x * blockDim.x;
   double s0 = 0.0, s1 = 0.0;
@@ -396,8 +396,9 @@ __global__ void __launch_bounds__(kThreads) k_dot_partial2(int n2, const double2
     for (int u = 0; u < kMgsU; ++u) {
       const long long k = i + u * stride;
       if (k < n2) {
-        x[u] = a[k];
-        y[u] = b[k];
+        const long long e = rev ? n2 - 1 - k : k;
+        x[u] = a[e];
+        y[u] = b[e];
       } else {
         x[u] = make_double2(0.0, 0.0);
         y[u] = x[u];
@@ -425,7 +426,8 @@ __global__ void __launch_bounds__(kThreads) k_dot_partial2(int n2, const double2
 __global__ void __launch_bounds__(kThreads) k_mgs_step2(int n2, const double2* __restrict__ vi,
                                                         const double2* __restrict__ vnext, double2* __restrict__ w,
                                                         const double* __restrict__ pin, int nb,
-                                                        double* __restrict__ pout, double* __restrict__ hout) {
+                                                        double* __restrict__ pout, double* __restrict__ hout,
+                                                        int rev) {
   MGD_PDL_ENTRY();
   const double h = block_sum_partials(pin, nb);
   if (blockIdx.x == 0 && threadIdx.x == 0) *hout = h;
@@ -437,9 +439,10 @@ __global__ void __launch_bounds__(kThreads) k_mgs_step2(int n2, const double2* _
     for (int u = 0; u < kMgsU; ++u) {
       const long long k = i + u * stride;
       if (k < n2) {
-        ww[u] = w[k];
-        a[u] = __ldcs(vi + k);
-        c[u] = vnext ? vnext[k] : make_double2(0.0, 0.0);
+        const long long e = rev ? n2 - 1 - k : k;
+        ww[u] = w[e];
+        a[u] = __ldcs(vi + e);
+        c[u] = vnext ? vnext[e] : make_double2(0.0, 0.0);
       }
     }
 #pragma unroll
@@ -449,7 +452,7 @@ __global__ void __launch_bounds__(kThreads) k_mgs_step2(int n2, const double2* _
         double2 r;
         r.x = ww[u].x - h * a[u].x;
         r.y = ww[u].y - h * a[u].y;
-        w[k] = r;
+        w[rev ? n2 - 1 - k : k] = r;
         if (vnext) {
           s0 += c[u].x * r.x;
           s1 += c[u].y * r.y;
@@ -491,8 +494,11 @@ void launch_mgs(int n, const double* V, long long ldv, int nv, double* w, double
   // 16-byte vectors when every basis vector and w start on a 16-byte boundary
   const bool vec = (n % 2 == 0) && (ldv % 2 == 0) && aligned16(V) && aligned16(w);
   const int n2 = n / 2;
+  // consecutive passes over the vectors alternate their direction, so each
+  // pass starts on the lines the previous one touched last (still in L2):
+  // the first dot product runs backwards, step i forwards for even i
   if (vec)
-    launch_k(k_dot_partial2, dim3(nb), dim3(kThreads), 0, s, n2, (const double2*)V, (const double2*)w, pa);
+    launch_k(k_dot_partial2, dim3(nb), dim3(kThreads), 0, s, n2, (const double2*)V, (const double2*)w, pa, 1);
   else
     launch_k(k_dot_partial, dim3(nb), dim3(kThreads), 0, s, n, V, w, pa);
   MGD_LAUNCH_CHECK();
@@ -503,7 +509,7 @@ void launch_mgs(int n, const double* V, long long ldv, int nv, double* w, double
     const double* vnext = i + 1 < nv ? V + (long long)(i + 1) * ldv : nullptr;
     if (vec)
       launch_k(k_mgs_step2, dim3(nb), dim3(kThreads), 0, s, n2, (const double2*)(V + (long long)i * ldv),
-               (const double2*)vnext, (double2*)w, pin, nb, pout, h + i);
+               (const double2*)vnext, (double2*)w, pin, nb, pout, h + i, i & 1);
     else
       launch_k(k_mgs_step, dim3(nb), dim3(kThreads), 0, s, n, V + (long long)i * ldv, vnext, w, pin, nb, pout,
                h + i);
@@ -632,7 +638,7 @@ void launch_arnoldi_coop(int nb, int n, const double* V, long long ldv, int nv, 
 // the same on 16-byte vectors, kMgsU pairs per thread and trip (n even, both vectors 16-byte aligned)
 __global__ void __launch_bounds__(kThreads) k_scale_by_norm2(int n2, const double2* __restrict__ w,
                                                              const double* __restrict__ nrm2,
-                                                             double2* __restrict__ v) {
+                                                             double2* __restrict__ v, int rev) {
   MGD_PDL_ENTRY();
   __shared__ double s_inv;
   if (threadIdx.x == 0) {
@@ -646,18 +652,18 @@ __global__ void __launch_bounds__(kThreads) k_scale_by_norm2(int n2, const doubl
     double2 a[kMgsU];
 #pragma unroll
     for (int u = 0; u < kMgsU; ++u)
-      if (i + u * stride < n2) a[u] = w[i + u * stride];
+      if (i + u * stride < n2) a[u] = w[rev ? n2 - 1 - (i + u * stride) : i + u * stride];
 #pragma unroll
     for (int u = 0; u < kMgsU; ++u)
-      if (i + u * stride < n2) v[i + u * stride] = make_double2(a[u].x * r, a[u].y * r);
+      if (i + u * stride < n2) v[rev ? n2 - 1 - (i + u * stride) : i + u * stride] = make_double2(a[u].x * r, a[u].y * r);
   }
 }
 
-void launch_scale_by_norm(int n, const double* w, const double* nrm2, double* v, cudaStream_t s) {
+void launch_scale_by_norm(int n, const double* w, const double* nrm2, double* v, cudaStream_t s, int rev) {
   if (n % 2 == 0 && aligned16(w) && aligned16(v)) {
     const int n2 = n / 2;
     const int nb = std::min(4 * kDotBlocks, std::max(1, cdiv(n2, kThreads * kMgsU)));
-    launch_k(k_scale_by_norm2, dim3(nb), dim3(kThreads), 0, s, n2, (const double2*)w, nrm2, (double2*)v);
+    launch_k(k_scale_by_norm2, dim3(nb), dim3(kThreads), 0, s, n2, (const double2*)w, nrm2, (double2*)v, rev);
   } else {
     launch_k(k_scale_by_norm, dim3(cdiv(n, kThreads)), dim3(kThreads), 0, s, n, w, nrm2, v);
   }
