@@ -273,7 +273,7 @@ static Csr spgemm(Arena& a, const Csr& X, const Csr& Y, cudaStream_t s, Scratch*
   double* tv = sc.alloc<double>(total);
   int* cnt = sc.alloc<int>(n);
   int* work = sc.alloc<int>(2 * (size_t)n + 2);
-  launch_spgemm_expand(n, X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off, tc, tv, cnt, work, s);
+  launch_spgemm_expand(n, X.rp, X.ci, X.v, Y.rp, Y.ci, Y.v, off, tc, tv, cnt, work, s, total);
   Csr C;
   C.n = n;
   C.m = Y.m;

@@ -375,9 +375,10 @@ void launch_transpose_fill(int n, const int* rp, const int* ci, const double* v,
                            int* tci, double* tv, cudaStream_t s);
 void launch_sort_rows(int n, const int* rp, int* ci, double* v, cudaStream_t s);
 void launch_spgemm_ub(int n, const int* xrp, const int* xci, const int* yrp, int* ub, cudaStream_t s);
+// total_products: the expansion's product count (sets the per-row list size)
 void launch_spgemm_expand(int n, const int* xrp, const int* xci, const double* xv, const int* yrp,
-                          const int* yci, const double* yv, const long long* off, int* tc, double* tv,
-                          int* cnt, int* work, cudaStream_t s);  // work: 2n + 2 ints
+                          const int* yci, const double* yv, const long long* off, int* tc, double* tv, int* cnt,
+                          int* work, cudaStream_t s, long long total_products);  // work: 2n + 2 ints
 void launch_spgemm_compact(int n, const long long* off, const int* tc, const double* tv, const int* crp,
                            int* cci, double* cv, cudaStream_t s);
 void launch_l1_dinv(int n, const int* rp, const double* v, double* dinv, cudaStream_t s);

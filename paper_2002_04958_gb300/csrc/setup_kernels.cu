@@ -1067,12 +1067,17 @@ constexpr int kThrRows = 128;
 constexpr int kThrMaxProducts = 1024;
 constexpr int kThrBatch = 8;  // entries of a row of Y loaded ahead of the merge
 
+// SLOTS: the column-list capacity per row.  Shared memory (12 SLOTS bytes per
+// thread) bounds the resident blocks, so a product whose rows are short runs
+// with fewer slots and more warps per SM; a row that needs more columns is
+// listed for the warp kernel, which gives the same sums.
+template <int SLOTS>
 __global__ void __launch_bounds__(kThrRows) k_spgemm_thread(int n, const int* xrp, const int* xci, const double* xv,
                                                             const int* yrp, const int* yci, const double* yv,
                                                             const long long* off, int* tc, double* tv, int* cnt,
                                                             int* wrows, int* nw) {
-  __shared__ int s_c[kThrSlots][kThrRows];
-  __shared__ double s_v[kThrSlots][kThrRows];
+  __shared__ int s_c[SLOTS][kThrRows];
+  __shared__ double s_v[SLOTS][kThrRows];
   const int t = threadIdx.x;
   const int i = blockIdx.x * kThrRows + t;
   if (i >= n) return;
@@ -1120,7 +1125,7 @@ __global__ void __launch_bounds__(kThrRows) k_spgemm_thread(int n, const int* xr
         s_v[lo][t] = __dadd_rn(s_v[lo][t], pr);
         continue;
       }
-      if (u == kThrSlots) {
+      if (u == SLOTS) {
         over = true;
         break;
       }
@@ -1383,7 +1388,7 @@ __global__ void __launch_bounds__(kLongThreads) k_spgemm_long(const int* xrp, co
 
 void launch_spgemm_expand(int n, const int* xrp, const int* xci, const double* xv, const int* yrp,
                           const int* yci, const double* yv, const long long* off, int* tc, double* tv, int* cnt,
-                          int* work, cudaStream_t s) {
+                          int* work, cudaStream_t s, long long mean_products_hint) {
   // work: 2n + 2 ints (list of long rows, their count, list of the warp
   // kernel's rows, their count)
   int* nlong = work + n;
@@ -1392,7 +1397,19 @@ void launch_spgemm_expand(int n, const int* xrp, const int* xci, const double* x
   MGD_CUDA(cudaMemsetAsync(nlong, 0, sizeof(int), s));
   MGD_CUDA(cudaMemsetAsync(nw, 0, sizeof(int), s));
   if (n <= 0) return;
-  k_spgemm_thread<<<cdiv(n, kThrRows), kThrRows, 0, s>>>(n, xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt, wrows, nw);
+  // list size from the mean number of products per row (the upper bound of
+  // its columns): the finest level's A P (about 17 products, at most ~19
+  // columns on the 3-D workloads) takes 16 slots, its R (A P) 24
+  const long long tot = mean_products_hint;
+  if (tot > 0 && tot <= 24LL * n)
+    k_spgemm_thread<16><<<cdiv(n, kThrRows), kThrRows, 0, s>>>(n, xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt, wrows,
+                                                               nw);
+  else if (tot > 0 && tot <= 96LL * n)
+    k_spgemm_thread<24><<<cdiv(n, kThrRows), kThrRows, 0, s>>>(n, xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt, wrows,
+                                                               nw);
+  else
+    k_spgemm_thread<kThrSlots><<<cdiv(n, kThrRows), kThrRows, 0, s>>>(n, xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt,
+                                                                      wrows, nw);
   MGD_LAUNCH_CHECK();
   // the listed rows, a grid-stride loop over the list (its length stays on the device)
   k_spgemm_warp<<<152 * 8, 32 * kSpgWarps, 0, s>>>(xrp, xci, xv, yrp, yci, yv, off, tc, tv, cnt, wrows, nw, work,
