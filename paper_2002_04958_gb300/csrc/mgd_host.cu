@@ -2892,22 +2892,32 @@ int mgd_setup_host(mgd_ctx* c, int G, int N, int n, int nnz, const int* h_rowptr
     int* rp = sc.alloc<int>((size_t)n + 1);
     int* ci = sc.alloc<int>(nnz);
     double* v = sc.alloc<double>(nnz);
+    struct CopyDrain {  // before the staging is freed on any exit path, the copies have ended
+      mgd_ctx* c;
+      ~CopyDrain() {
+        for (auto cs : c->s_copy)
+          if (cs) cudaStreamSynchronize(cs);
+      }
+    } drain{c};
     auto th = std::chrono::steady_clock::now();
-    cudaEvent_t ready = nullptr, done[4] = {nullptr, nullptr, nullptr, nullptr};
-    MGD_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-    for (auto& e : done) MGD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    MGD_CUDA(cudaEventRecord(ready, c->s));
-    for (auto cs : c->s_copy) MGD_CUDA(cudaStreamWaitEvent(cs, ready, 0));
+    struct Events {  // released on every exit path
+      cudaEvent_t e[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+      ~Events() {
+        for (auto x : e)
+          if (x) cudaEventDestroy(x);
+      }
+    } ev;
+    for (auto& e : ev.e) MGD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    MGD_CUDA(cudaEventRecord(ev.e[4], c->s));
+    for (auto cs : c->s_copy) MGD_CUDA(cudaStreamWaitEvent(cs, ev.e[4], 0));
     int next = 0;
     h2d_spread(c, v, h_vals, sizeof(double) * (size_t)nnz, next);
     h2d_spread(c, ci, h_colidx, sizeof(int) * (size_t)nnz, next);
     h2d_spread(c, rp, h_rowptr, sizeof(int) * ((size_t)n + 1), next);
     for (int k = 0; k < 4; ++k) {
-      MGD_CUDA(cudaEventRecord(done[k], c->s_copy[k]));
-      MGD_CUDA(cudaStreamWaitEvent(c->s, done[k], 0));
+      MGD_CUDA(cudaEventRecord(ev.e[k], c->s_copy[k]));
+      MGD_CUDA(cudaStreamWaitEvent(c->s, ev.e[k], 0));
     }
-    cudaEventDestroy(ready);
-    for (auto e : done) cudaEventDestroy(e);
     MGD_CUDA(cudaStreamSynchronize(c->s));
     const double h2d_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th).count();
     free_setup(c);
