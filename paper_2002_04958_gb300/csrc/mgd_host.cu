@@ -306,7 +306,10 @@ static Csr transpose(Arena& a, const Csr& X, cudaStream_t s, Scratch* keep = nul
   return T;
 }
 
-static Sell build_sell(Arena& a, const Csr& A, bool mixed, cudaStream_t s, const int* selfmap = nullptr) {
+// SELL-32 copy of A in the V-cycle's precision only (FP32 values when mixed,
+// else FP64); with dinv given, also A D^-1 in the same layout (vpre).
+static Sell build_sell(Arena& a, const Csr& A, bool mixed, cudaStream_t s, const int* selfmap = nullptr,
+                       const double* dinv = nullptr) {
   Scratch sc(s);
   Sell S;
   S.n = A.n;
@@ -317,11 +320,14 @@ static Sell build_sell(Arena& a, const Csr& A, bool mixed, cudaStream_t s, const
   exclusive_scan(w, S.sptr, S.nslices, s);
   S.nstored = read_int(S.sptr + S.nslices, s);
   S.ci = a.alloc<int>(S.nstored);
-  S.v = a.alloc<double>(S.nstored);
-  launch_sell_fill(A.n, A.rp, A.ci, A.v, S.sptr, S.ci, S.v, s, selfmap);
   if (mixed) {
     S.v32 = a.alloc<float>(S.nstored);
-    launch_cast_f64_f32((int)S.nstored, S.v, S.v32, s);
+    if (dinv) S.vpre32 = a.alloc<float>(S.nstored);
+    launch_sell_fill(A.n, A.rp, A.ci, A.v, dinv, S.sptr, S.ci, S.v32, S.vpre32, s, selfmap);
+  } else {
+    S.v = a.alloc<double>(S.nstored);
+    if (dinv) S.vpre = a.alloc<double>(S.nstored);
+    launch_sell_fill(A.n, A.rp, A.ci, A.v, dinv, S.sptr, S.ci, S.v, S.vpre, s, selfmap);
   }
   return S;
 }
@@ -580,41 +586,36 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
       launch_perm_rows_fill(n, lv.perm, lv.A.rp, lv.A.ci, lv.A.v, Ap.rp, Ap.ci, Ap.v, s);
       lv.gsell = build_sell(ar, Ap, sc.mixed, s, lv.perm);
     }
-    lv.sell = build_sell(ar, lv.A, sc.mixed, s);
-    const bool jac = lv.nk == 0;  // A D^-1 feeds only the l1-Jacobi pre-smoothing
-    if (jac) {
-      lv.vpre = ar.alloc<double>(lv.A.nnz);
-      launch_colscale(lv.A.nnz, lv.A.ci, lv.A.v, lv.dinv, lv.vpre, s);
-      lv.sell.vpre = ar.alloc<double>(lv.sell.nstored);
-      launch_colscale(lv.sell.nstored, lv.sell.ci, lv.sell.v, lv.dinv, lv.sell.vpre, s);
-    }
+    // A D^-1 feeds only the l1-Jacobi pre-smoothing.  The FP32 form keeps the
+    // FP64 CSR values (Galerkin products, coarsest inverse) and builds every
+    // kernel array in FP32 straight from them: each FP32 value is the FP64
+    // value (or the FP64 product a_ij d_j) rounded once.
+    const bool jac = lv.nk == 0;
+    const double* pre = jac ? lv.dinv : nullptr;
+    lv.sell = build_sell(ar, lv.A, sc.mixed, s, nullptr, pre);
     if (sc.mixed) {
-      if (jac) {
-        lv.vpre32 = cast32(ar, lv.vpre, lv.A.nnz, s);
-        lv.sell.vpre32 = cast32(ar, lv.sell.vpre, (int)lv.sell.nstored, s);
-      }
-      lv.v32 = cast32(ar, lv.A.v, lv.A.nnz, s);
+      lv.v32 = ar.alloc<float>(lv.A.nnz);
+      if (jac) lv.vpre32 = ar.alloc<float>(lv.A.nnz);
+      launch_colscale_f32(lv.A.nnz, lv.A.ci, lv.A.v, pre, lv.v32, lv.vpre32, s);
       lv.dinv32 = cast32(ar, lv.dinv, n, s);
       if (l < h.nlev() - 1) {
         lv.pv32 = cast32(ar, lv.P.v, lv.P.nnz, s);
         lv.rv32 = cast32(ar, lv.R.v, lv.R.nnz, s);
       }
+    } else if (jac) {
+      lv.vpre = ar.alloc<double>(lv.A.nnz);
+      launch_colscale(lv.A.nnz, lv.A.ci, lv.A.v, lv.dinv, lv.vpre, s);
     }
     if (sc.keepT) {
       lv.AT = transpose(ar, lv.A, s);
-      lv.sellT = build_sell(ar, lv.AT, sc.mixed, s);
-      if (jac) {
+      lv.sellT = build_sell(ar, lv.AT, sc.mixed, s, nullptr, pre);
+      if (sc.mixed) {
+        lv.atv32 = ar.alloc<float>(lv.AT.nnz);
+        if (jac) lv.atvpre32 = ar.alloc<float>(lv.AT.nnz);
+        launch_colscale_f32(lv.AT.nnz, lv.AT.ci, lv.AT.v, pre, lv.atv32, lv.atvpre32, s);
+      } else if (jac) {
         lv.atvpre = ar.alloc<double>(lv.AT.nnz);
         launch_colscale(lv.AT.nnz, lv.AT.ci, lv.AT.v, lv.dinv, lv.atvpre, s);
-        lv.sellT.vpre = ar.alloc<double>(lv.sellT.nstored);
-        launch_colscale(lv.sellT.nstored, lv.sellT.ci, lv.sellT.v, lv.dinv, lv.sellT.vpre, s);
-      }
-      if (sc.mixed) {
-        lv.atv32 = cast32(ar, lv.AT.v, lv.AT.nnz, s);
-        if (jac) {
-          lv.atvpre32 = cast32(ar, lv.atvpre, lv.AT.nnz, s);
-          lv.sellT.vpre32 = cast32(ar, lv.sellT.vpre, (int)lv.sellT.nstored, s);
-        }
       }
     }
     size_t es = sc.mixed ? sizeof(float) : sizeof(double);

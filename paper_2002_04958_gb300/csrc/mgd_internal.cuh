@@ -390,9 +390,15 @@ void launch_pctl_ac_fill(int N, int nc, int G, const int* const* brp, const int*
                          const double* const* bv, const double* const* p, const double* const* dtab,
                          const int* acrp, int* acci, double* acv, cudaStream_t s);
 void launch_sell_widths(int n, const int* rp, int* w, cudaStream_t s);
-void launch_sell_fill(int n, const int* rp, const int* ci, const double* v, const int* sptr, int* sci, double* sv,
-                      cudaStream_t s, const int* selfmap = nullptr);
+// SELL-32 copy of a CSR matrix; with d given, svpre gets A D^-1 in the same pass
+void launch_sell_fill(int n, const int* rp, const int* ci, const double* v, const double* d, const int* sptr,
+                      int* sci, double* sv, double* svpre, cudaStream_t s, const int* selfmap = nullptr);
+void launch_sell_fill(int n, const int* rp, const int* ci, const double* v, const double* d, const int* sptr,
+                      int* sci, float* sv, float* svpre, cudaStream_t s, const int* selfmap = nullptr);
 void launch_colscale(long long nnz, const int* ci, const double* v, const double* d, double* out, cudaStream_t s);
+// FP32 values (vout) and FP32 A D^-1 (out, when d is given) of FP64 CSR values, one pass
+void launch_colscale_f32(long long nnz, const int* ci, const double* v, const double* d, float* vout, float* out,
+                         cudaStream_t s);
 void launch_grad_vals(int n, const int* rp, const int* ci, const double* x, const double* lam, double* g,
                       cudaStream_t s);
 void launch_offsets64(const int* cnt, long long* off, int n, cudaStream_t s);

@@ -1759,11 +1759,12 @@ void launch_sell_widths(int n, const int* rp, int* w, cudaStream_t s) {
   MGD_LAUNCH_CHECK();
 }
 
-// padding: column = the row itself, value 0
 // padding entries: value 0 at the row's own column (self[r] when given: the
-// original index of a row of a row-permuted copy)
-__global__ void k_sell_fill(int n, const int* rp, const int* ci, const double* v, const int* sptr, int* sci,
-                            double* sv, const int* selfmap) {
+// original index of a row of a row-permuted copy).  With d given, svpre gets
+// the column-scaled values a_ij d_j (A D^-1, rounded once in FP64, then to T).
+template <typename T>
+__global__ void k_sell_fill(int n, const int* rp, const int* ci, const double* v, const double* d,
+                            const int* sptr, int* sci, T* sv, T* svpre, const int* selfmap) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int nsl = (n + 31) / 32;
   if (r >= nsl * 32) return;
@@ -1776,31 +1777,60 @@ __global__ void k_sell_fill(int n, const int* rp, const int* ci, const double* v
   for (int j = 0; j < width; ++j) {
     int idx = base + j * 32 + lane;
     if (j < len) {
-      sci[idx] = ci[b + j];
-      sv[idx] = v[b + j];
+      int c = ci[b + j];
+      double a = v[b + j];
+      sci[idx] = c;
+      sv[idx] = (T)a;
+      if (svpre) svpre[idx] = (T)__dmul_rn(a, d[c]);
     } else {
       sci[idx] = self;
-      sv[idx] = 0.0;
+      sv[idx] = T(0);
+      if (svpre) svpre[idx] = T(0);
     }
   }
 }
 
-void launch_sell_fill(int n, const int* rp, const int* ci, const double* v, const int* sptr, int* sci, double* sv,
-                      cudaStream_t s, const int* selfmap) {
+template <typename T>
+static void sell_fill(int n, const int* rp, const int* ci, const double* v, const double* d, const int* sptr,
+                      int* sci, T* sv, T* svpre, cudaStream_t s, const int* selfmap) {
   int nsl = (n + 31) / 32;
-  k_sell_fill<<<cdiv(nsl * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, sptr, sci, sv, selfmap);
+  k_sell_fill<T><<<cdiv(nsl * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, d, sptr, sci, sv, d ? svpre : nullptr,
+                                                               selfmap);
   MGD_LAUNCH_CHECK();
 }
 
+void launch_sell_fill(int n, const int* rp, const int* ci, const double* v, const double* d, const int* sptr,
+                      int* sci, double* sv, double* svpre, cudaStream_t s, const int* selfmap) {
+  sell_fill<double>(n, rp, ci, v, d, sptr, sci, sv, svpre, s, selfmap);
+}
+
+void launch_sell_fill(int n, const int* rp, const int* ci, const double* v, const double* d, const int* sptr,
+                      int* sci, float* sv, float* svpre, cudaStream_t s, const int* selfmap) {
+  sell_fill<float>(n, rp, ci, v, d, sptr, sci, sv, svpre, s, selfmap);
+}
+
 // ------------------------------------------------------------------ column scaling A D^-1
-__global__ void k_colscale(long long nnz, const int* ci, const double* v, const double* d, double* out) {
+// out = A D^-1 values (the FP64 product, rounded to T); vout, when given, the
+// values themselves rounded to T (the FP32 copy of a level, in the same pass)
+template <typename T>
+__global__ void k_colscale(long long nnz, const int* ci, const double* v, const double* d, T* vout, T* out) {
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < nnz) out[p] = __dmul_rn(v[p], d[ci[p]]);
+  if (p >= nnz) return;
+  double a = v[p];
+  if (vout) vout[p] = (T)a;
+  if (out) out[p] = (T)__dmul_rn(a, d[ci[p]]);
 }
 
 void launch_colscale(long long nnz, const int* ci, const double* v, const double* d, double* out, cudaStream_t s) {
   if (nnz <= 0) return;
-  k_colscale<<<cdiv(nnz, kThreads), kThreads, 0, s>>>(nnz, ci, v, d, out);
+  k_colscale<double><<<cdiv(nnz, kThreads), kThreads, 0, s>>>(nnz, ci, v, d, nullptr, out);
+  MGD_LAUNCH_CHECK();
+}
+
+void launch_colscale_f32(long long nnz, const int* ci, const double* v, const double* d, float* vout, float* out,
+                         cudaStream_t s) {
+  if (nnz <= 0) return;
+  k_colscale<float><<<cdiv(nnz, kThreads), kThreads, 0, s>>>(nnz, ci, v, d, vout, d ? out : nullptr);
   MGD_LAUNCH_CHECK();
 }
 

@@ -217,3 +217,29 @@ def test_config4_adjoint_full_size(gpu):
         fd = float(np.dot(dln, 2 * xmn + dln)) / (2 * h)
         an = (gv * dv).sum().item()
         assert fd == pytest.approx(an, rel=1e-5)
+
+
+@pytest.mark.parametrize("name", ["G1_1024x1024_schur1_exti_option3", "G1_1024x1024_schur1_exti_option4_k3",
+                                  "G1_1024x1024_diffuseE_schur1_exti", "G20_256x256_amg_cf_gauss_seidel"])
+def test_options_at_full_size(gpu, name):
+    """The options beside the default path at their workloads' full sizes, in
+    the bench's launch form (batched launches, graph replay, autotuned
+    layouts): option #3 and option #4 inverses, E diffusing (Eq. 2.1 as
+    printed), the C/F Gauss-Seidel smoother.  FP64 iterations and every
+    inverse's V-cycle count equal the stored oracle solve's; the stored
+    entries within 1e-10 of max|x|."""
+    rec = _golden("oracle_options_fullsize.json")[name]
+    s = I.preset(rec["preset"])
+    assert s.n == rec["n"] and s.nnz == rec["nnz"]
+    slv = gpu.Solver(batched=1, use_graph=1, autotune=1, **rec["options"]).setup_system(s, rec["precond"])
+    x, it, rr, rc = slv.solve(torch.from_numpy(s.b), tol=1e-8)
+    assert rc == 0 and it == rec["iterations"], (it, rec["iterations"])
+    assert rr == pytest.approx(rec["relres"], rel=1e-4)
+    xg = x.cpu().numpy()
+    idx = np.asarray(rec["sample_index"])
+    assert np.max(np.abs(xg[idx] - np.asarray(rec["sample_x"]))) <= 1e-10 * rec["x_max_abs"]
+    assert abs(np.linalg.norm(xg) - rec["x_norm2"]) <= 1e-10 * rec["x_norm2"]
+    for k in range(slv.stats()["n_ops"]):
+        info = slv.op_info(k)
+        key = f"{info['kind']},{info['comp']}"
+        assert slv.op_cycles(k) == rec["cycles"].get(key, 0), (key, slv.op_cycles(k), rec["cycles"].get(key))
