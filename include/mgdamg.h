@@ -249,7 +249,9 @@ int mgd_setup_phases(mgd_ctx *c, double *h_ms, int n);
  * launched together); for batch `batch` and level `level`, the number of
  * subsystems descending through that level, the largest row count, and the
  * autotuned layouts of the operator / restriction / prolongation kernels
- * (0 = SELL-32, 1..6 = CSR with 1, 2, 4, 8, 16, 32 threads per row); *tail =
+ * (0 = SELL-32, 1..6 = CSR with 1, 2, 4, 8, 16, 32 threads per row, 7 / 8 =
+ * SELL-32 with a thread on 2 / 4 slices, 9 / 10 = CSR with a thread on one
+ * row of each of 2 / 4 adjacent 32-row groups); *tail =
  * first level handled by the fused coarse-level kernel (depth if none). */
 int mgd_plan_info(mgd_ctx *c, int batch, int level, int *nbatches, int *depth, int *nsub, int *maxrows, int *fmtA,
                   int *fmtR, int *fmtP, int *tail);

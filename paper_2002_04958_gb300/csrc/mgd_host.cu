@@ -1029,7 +1029,7 @@ static void autotune(VBatch<T>& vb, bool trans, cudaStream_t s) {
     return ms;
   };
   const int candA[] = {FMT_SELL, FMT_SELL2, FMT_SELL4, FMT_CSR1, FMT_CSR2, FMT_CSR4, FMT_CSR8};
-  const int candRP[] = {FMT_CSR1, FMT_CSR2, FMT_CSR4, FMT_CSR8};
+  const int candRP[] = {FMT_CSR1, FMT_CSR1X2, FMT_CSR1X4, FMT_CSR2, FMT_CSR4, FMT_CSR8};
   for (int l = 0; l < vb.depth; ++l) {
     auto& lp = plan[l];
     if (!lp.ndown) continue;

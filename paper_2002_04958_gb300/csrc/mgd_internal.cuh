@@ -166,8 +166,10 @@ struct Csr {  // device CSR, FP64 values
 
 // sparse-kernel formats chosen per level by the autotuner
 enum Fmt { FMT_SELL = 0, FMT_CSR1 = 1, FMT_CSR2 = 2, FMT_CSR4 = 3, FMT_CSR8 = 4, FMT_CSR16 = 5, FMT_CSR32 = 6,
-           FMT_SELL2 = 7, FMT_SELL4 = 8 };  // SELL-32 with each thread on the same lane of 2 / 4 adjacent
+           FMT_SELL2 = 7, FMT_SELL4 = 8,     // SELL-32 with each thread on the same lane of 2 / 4 adjacent
                                              // slices (l1-Jacobi smoothing phases only)
+           FMT_CSR1X2 = 9, FMT_CSR1X4 = 10 };  // CSR, one thread per row, each thread on the same lane of
+                                               // 2 / 4 adjacent 32-row groups (restriction, prolongation only)
 constexpr int kNumFmt = 7;
 
 struct Sell {  // sliced ELL, slice height 32, column-major inside a slice

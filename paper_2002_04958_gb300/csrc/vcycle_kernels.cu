@@ -178,6 +178,97 @@ __global__ void __launch_bounds__(kVThreads) k_prolong(const LDesc<T>* __restric
   if (valid && lane == 0) d->xt[row] += s;
 }
 
+// Multi-row forms of RESTRICT and PROLONG (FMT_CSR1X2, FMT_CSR1X4): one thread
+// per row as in FMT_CSR1, each thread on the same lane of K adjacent 32-row
+// groups.  A transfer row has few entries (one for a C point of P), so one row
+// per thread leaves a warp one or two dependent loads in flight; here every
+// gather of the K rows is issued before any sum is stored.  Each row sum takes
+// its entries in CSR order, as in FMT_CSR1.
+template <int K>
+struct MrPre {
+  static constexpr int pre = K >= 4 ? 2 : 3;  // entries per row loaded before the wait
+};
+
+template <typename T, int K, class XF>
+__device__ __forceinline__ void mr_sums(const RowPre<T, MrPre<K>::pre> (&R)[K], int w, int lane, int n,
+                                        const int* __restrict__ ci, const T* __restrict__ v, const XF& xf,
+                                        T (&s)[K]) {
+  constexpr int PRE = MrPre<K>::pre;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    s[q] = T(0);
+    if ((w * K + q) * 32 + lane < n) {
+      const int first = R[q].p - PRE;
+#pragma unroll
+      for (int k = 0; k < PRE; ++k)
+        if (first + k < R[q].e) s[q] += R[q].a[k] * xf(R[q].c[k]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q)
+    if ((w * K + q) * 32 + lane < n)
+      for (int p = R[q].p; p < R[q].e; ++p) s[q] += __ldg(v + p) * xf(__ldg(ci + p));
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kVThreads) k_restrict_mr(const LDesc<T>* __restrict__ descs) {
+  MGD_PDL_TRIGGER();
+  const LDesc<T>* d = descs + blockIdx.y;
+  constexpr int PRE = MrPre<K>::pre;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int w = g >> 5, lane = g & 31;
+  int n = d->nc;
+  if (w * 32 * K >= n) return;  // the whole warp is past the last row
+  RowPre<T, PRE> R[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    int r = (w * K + q) * 32 + lane;
+    row_load<T, FMT_CSR1, PRE>(R[q], r, 0, r < n, d->rrp, d->rci, d->rv, nullptr, nullptr, nullptr);
+  }
+  MGD_PDL_WAIT();
+  MGD_SKIP_INACTIVE(d);
+  T s[K];
+  mr_sums<T, K>(R, w, lane, n, d->rci, d->rv, XPlain<T>{d->r}, s);
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    int r = (w * K + q) * 32 + lane;
+    if (r < n) d->bc[r] = s[q];
+  }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kVThreads) k_prolong_mr(const LDesc<T>* __restrict__ descs) {
+  MGD_PDL_TRIGGER();
+  const LDesc<T>* d = descs + blockIdx.y;
+  constexpr int PRE = MrPre<K>::pre;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int w = g >> 5, lane = g & 31;
+  int n = d->n;
+  if (w * 32 * K >= n) return;
+  RowPre<T, PRE> R[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    int r = (w * K + q) * 32 + lane;
+    row_load<T, FMT_CSR1, PRE>(R[q], r, 0, r < n, d->prp, d->pci, d->pv, nullptr, nullptr, nullptr);
+  }
+  MGD_PDL_WAIT();
+  MGD_SKIP_INACTIVE(d);
+  T* xt = d->xt;
+  T xo[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    int r = (w * K + q) * 32 + lane;
+    xo[q] = r < n ? xt[r] : T(0);
+  }
+  T s[K];
+  mr_sums<T, K>(R, w, lane, n, d->pci, d->pv, XPlain<T>{d->xc}, s);
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    int r = (w * K + q) * 32 + lane;
+    if (r < n) xt[r] = xo[q] + s[q];
+  }
+}
+
 // stalled coarsest level, first l1-Jacobi sweep from zero: xt = D^-1 b
 template <typename T>
 __global__ void k_jac1(const LDesc<T>* __restrict__ descs) {
@@ -248,8 +339,26 @@ void launch_phase(int phase, int fmtA, int fmtRP, const LDesc<T>* d_descs, int n
       else
         MGD_DISPATCH_FMT(k_post, fmtA, maxrows, ndesc, s, d_descs);
       break;
-    case PH_RESTRICT: MGD_DISPATCH_FMT(k_restrict, rp, maxrows, ndesc, s, d_descs); break;
-    case PH_PROLONG: MGD_DISPATCH_FMT(k_prolong, rp, maxrows, ndesc, s, d_descs); break;
+    case PH_RESTRICT:
+      if (rp == FMT_CSR1X2)
+        launch_k(k_restrict_mr<T, 2>, dim3(cdiv((long long)cdiv(maxrows, 64) * 32, kVThreads), ndesc),
+                 dim3(kVThreads), 0, s, d_descs);
+      else if (rp == FMT_CSR1X4)
+        launch_k(k_restrict_mr<T, 4>, dim3(cdiv((long long)cdiv(maxrows, 128) * 32, kVThreads), ndesc),
+                 dim3(kVThreads), 0, s, d_descs);
+      else
+        MGD_DISPATCH_FMT(k_restrict, rp, maxrows, ndesc, s, d_descs);
+      break;
+    case PH_PROLONG:
+      if (rp == FMT_CSR1X2)
+        launch_k(k_prolong_mr<T, 2>, dim3(cdiv((long long)cdiv(maxrows, 64) * 32, kVThreads), ndesc),
+                 dim3(kVThreads), 0, s, d_descs);
+      else if (rp == FMT_CSR1X4)
+        launch_k(k_prolong_mr<T, 4>, dim3(cdiv((long long)cdiv(maxrows, 128) * 32, kVThreads), ndesc),
+                 dim3(kVThreads), 0, s, d_descs);
+      else
+        MGD_DISPATCH_FMT(k_prolong, rp, maxrows, ndesc, s, d_descs);
+      break;
     case PH_JAC1: launch_k(k_jac1<T>, dim3(dim3(cdiv(maxrows, kVThreads), ndesc)), dim3(kVThreads), 0, s, d_descs); break;
     case PH_COARSE:
       // one 1024-thread CTA per subsystem: a warp per row of the dense inverse

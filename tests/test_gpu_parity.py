@@ -325,6 +325,25 @@ def test_adjoint_gradient(gpu, orc, smoother):
         assert fd == pytest.approx(an, rel=1e-5)
 
 
+@pytest.mark.parametrize("kind", ["amg", "bd"])
+@pytest.mark.parametrize("batched", [0, 1])
+def test_fp32_vcycle_transposed_solve(gpu, orc, kind, batched):
+    # A^T lam = g with the transposed FP32 V-cycles (the FP32 copies of A^T and
+    # of A^T D^-1): iterations within one of the FP64 oracle's transposed
+    # solve, the true transposed residual below the tolerance
+    s = I.make_system(4, (23, 19), multigroup=True)
+    slv = gpu.Solver(keep_transpose=1, precision=1, batched=batched, use_graph=batched).setup_system(s, kind)
+    g = np.random.default_rng(3).standard_normal(s.n)
+    lam, it, rr = slv.solve_transpose(torch.from_numpy(g), tol=1e-8)
+    Ao = orc.csr_of_system(s)
+    lo, ito, *_ = orc.fgmres(Ao, g, orc.Block(Ao, s.G, s.N, kind), tol=1e-8, transpose=True)
+    assert abs(it - ito) <= 1, (it, ito)
+    lg = lam.cpu().numpy()
+    assert np.linalg.norm(g - s.scipy().T @ lg) <= 1.0000001e-8 * np.linalg.norm(g)
+    # both residuals are below 1e-8 ||g|| and cond(A) is about 4.5e3 here
+    assert np.linalg.norm(lg - lo) <= 2e-4 * np.linalg.norm(lo)
+
+
 @pytest.mark.parametrize("kind", ["amg", "schur1", "bd"])
 @pytest.mark.parametrize("case", [CASES[0], CASES[3], CASES[4]], ids=["G1", "G20", "G2_3d"])
 def test_resident_arnoldi_matches_streaming(gpu, orc, kind, case):
@@ -391,6 +410,73 @@ def test_tune_cache_file(gpu, tmp_path):
     path.write_text("not a cache line\n" + "\n".join(lines) + "\n")
     second = run()
     assert second == first
+
+
+_LAYOUT_SCRIPT = """
+import hashlib, json, sys
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2002_04958_gb300 import inputs, mgdamg
+out = {}
+for name, G, dims, kind, prec in [("G20_schur2", 20, (37, 29), "schur2", 0), ("G20_bd", 20, (37, 29), "bd", 0),
+                                  ("G2_3d_amg", 2, (13, 11, 9), "amg", 0), ("G20_schur2_fp32", 20, (37, 29), "schur2", 1),
+                                  ("G4_bd_fp32", 4, (41, 23), "bd", 1)]:
+    s = inputs.make_system(G, dims, multigroup=True)
+    trans = kind in ("amg", "bd")  # the transposed solve takes AMG or BD
+    slv = mgdamg.Solver(autotune=1, batched=1, use_graph=1, keep_transpose=int(trans),
+                        precision=prec).setup_system(s, kind)
+    b = torch.from_numpy(s.b)
+    x, it, rr, rc = slv.solve(b)
+    lam, itT, _ = slv.solve_transpose(b) if trans else (x, 0, 0.0)   # raises unless it converged
+    rcT = 0
+    out[name] = dict(plan=slv.plan(), it=it, itT=itT, rc=[rc, rcT],
+                     x=hashlib.sha256(x.cpu().numpy().tobytes()).hexdigest(),
+                     lam=hashlib.sha256(lam.cpu().numpy().tobytes()).hexdigest())
+print(json.dumps(out))
+"""
+
+
+def test_transfer_layouts_bit_identical(gpu, tmp_path):
+    # the multi-row restriction / prolongation layouts (9, 10) sum each row as
+    # the one-thread-per-row layout (1) does: with every level's transfer
+    # layouts forced through the tune cache, forward and transposed solves are
+    # bitwise identical across the three
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    path = tmp_path / "tune.txt"
+    env = dict(os.environ, MGD_TUNE_CACHE=str(path))
+
+    def run():
+        p = subprocess.run([sys.executable, "-c", _LAYOUT_SCRIPT, root], env=env, capture_output=True, text=True,
+                           timeout=900)
+        assert p.returncode == 0, p.stderr[-2000:]
+        return json.loads(p.stdout.strip().splitlines()[-1])
+
+    run()   # writes the autotuned entries
+    lines = path.read_text().splitlines()
+    res = {}
+    for f in (1, 9, 10):
+        forced = []
+        for ln in lines:
+            fs = ln.split("|")
+            depth = len(fs[1].split())
+            fs[2] = fs[3] = " ".join([str(f)] * depth)
+            forced.append("|".join(fs))
+        path.write_text("\n".join(forced) + "\n")
+        res[f] = run()
+        for name, r in res[f].items():
+            assert r["rc"] == [0, 0], (f, name)
+            for batch in r["plan"]:
+                for lv in batch["levels"][:-1]:
+                    if lv["nsub"]:
+                        assert lv["fmtR"] == f and lv["fmtP"] == f, (f, name, lv)
+    for f in (9, 10):
+        for name in res[1]:
+            for k in ("it", "itT", "x", "lam"):
+                assert res[f][name][k] == res[1][name][k], (f, name, k)
 
 
 def test_fp64_accounting_and_issue_rate(gpu):
