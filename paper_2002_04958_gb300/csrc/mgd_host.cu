@@ -1107,6 +1107,7 @@ struct Step {
   void* descs2 = nullptr;
   int nd2 = 0;
   int len = 0;            // vector length of produce/consume
+  int nterms = 0;         // PRODUCE: coupling terms over all descriptors
   std::vector<int> ops;   // INVERT
   int batch = -1;         // index into batches when batched
   double bytes = 0;
@@ -1235,7 +1236,10 @@ static void push_produce(mgd_ctx* c, std::vector<Step>& steps, std::vector<Produ
   st.nd = (int)v.size();
   st.len = len;
   st.descs = upload_vec(c, v);
-  for (auto& d : v) st.bytes += (double)len * (sizeof(T) + (d.a.slot || d.a.abs ? 8 : 0) + 16.0 * d.nt);
+  for (auto& d : v) {
+    st.bytes += (double)len * (sizeof(T) + (d.a.slot || d.a.abs ? 8 : 0) + 16.0 * d.nt);
+    st.nterms += d.nt;
+  }
   steps.push_back(st);
 }
 template <typename T>
@@ -1816,7 +1820,8 @@ static void build_program(mgd_ctx* c) {
   std::vector<Step> fused;
   for (size_t i = 0; i < S.size(); ++i) {
     if (i + 1 < S.size() && S[i].type == Step::CONSUME && S[i + 1].type == Step::PRODUCE && S[i].batch == -1 &&
-        S[i + 1].batch == -1 && S[i].len == S[i + 1].len) {
+        S[i + 1].batch == -1 && S[i].len == S[i + 1].len && S[i].nd <= kCpMaxCons && S[i + 1].nd <= kCpMaxProd &&
+        S[i + 1].nterms <= kCpMaxTerms) {
       Step f = S[i];
       f.type = Step::CONSPROD;
       f.descs2 = S[i + 1].descs;

@@ -263,6 +263,9 @@ struct IOSlots {
 };
 
 constexpr int kMaxTerms = 32;
+// a CONSUME and the PRODUCE after it fuse into one kernel when their
+// descriptors fit its shared-memory tables
+constexpr int kCpMaxCons = 64, kCpMaxProd = 64, kCpMaxTerms = 512;
 template <typename T>
 struct ProduceDesc {  // dst = (T)(a + sum_t s_t * d_t (.) w_t)
   T* dst;

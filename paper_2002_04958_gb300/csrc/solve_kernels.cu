@@ -54,35 +54,140 @@ __global__ void k_consume(const ConsumeDesc<T>* __restrict__ ds, int N, const IO
 }
 
 // A CONSUME step followed by a PRODUCE step, fused: per element, every
-// consume descriptor, then every produce descriptor.  Both are elementwise,
-// so a produce term that reads a vector the consume just wrote reads it back
-// at the same index in the same thread (the data pointers are not restrict:
-// the compiler keeps the store before the load).
+// consume descriptor, then every produce descriptor, each computed as in
+// k_consume / k_produce.  The block first resolves the descriptors' vectors
+// into shared memory.  The descriptors of one step are independent (those
+// kernels run them as parallel blocks), so a thread issues the loads of
+// kCpGroup descriptors (or of kCpGroup terms of one descriptor) before it uses
+// them or stores a result: one descriptor at a time would leave a single
+// dependent load per thread in flight.  A produce term that reads a vector
+// the consume just wrote reads it back at the same index in the same thread,
+// after the store (the data pointers are not restrict: the compiler keeps the
+// order).  The host fuses only steps within the shared-memory tables' sizes.
+constexpr int kCpGroup = 4;
+
 template <typename T>
-__global__ void k_consume_produce(const ConsumeDesc<T>* __restrict__ cd, int ncd, const ProduceDesc<T>* __restrict__ pd,
-                                  int npd, int N, const IOSlots* __restrict__ io) {
+__global__ void __launch_bounds__(kThreads) k_consume_produce(const ConsumeDesc<T>* __restrict__ cd, int ncd,
+                                                              const ProduceDesc<T>* __restrict__ pd, int npd, int N,
+                                                              const IOSlots* __restrict__ io) {
+  __shared__ const T* s_cx[kCpMaxCons];
+  __shared__ const double* s_cb[kCpMaxCons];
+  __shared__ double* s_cdst[kCpMaxCons];
+  __shared__ double s_cs[kCpMaxCons];
+  __shared__ T* s_pdst[kCpMaxProd];
+  __shared__ const double* s_pa[kCpMaxProd];
+  __shared__ int s_pt[kCpMaxProd + 1];  // terms of produce j: [s_pt[j], s_pt[j+1])
+  __shared__ const double* s_tw[kCpMaxTerms];
+  __shared__ const double* s_td[kCpMaxTerms];
+  __shared__ double s_ts[kCpMaxTerms];
   MGD_PDL_ENTRY();
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  for (int j = 0; j < ncd; ++j) {
+  const int t = threadIdx.x;
+  for (int j = t; j < ncd; j += blockDim.x) {
     const ConsumeDesc<T>* d = cd + j;
-    double* dst = resolve(d->dst, io);
-    const double* base = resolve(d->base, io);
-    double val = d->s * (double)d->x[k];
-    dst[k] = base ? base[k] + val : val;
+    s_cx[j] = d->x;
+    s_cb[j] = resolve(d->base, io);
+    s_cdst[j] = resolve(d->dst, io);
+    s_cs[j] = d->s;
   }
-  for (int j = 0; j < npd; ++j) {
+  for (int j = t; j < npd; j += blockDim.x) {
     const ProduceDesc<T>* d = pd + j;
-    const double* a = resolve(d->a, io);
-    double acc = a ? a[k] : 0.0;
-    int nt = d->nt;
-    for (int t = 0; t < nt; ++t) {
-      const double* w = resolve(d->w[t], io);
-      double term = w[k];
-      if (d->d[t]) term *= d->d[t][k];
-      acc += d->s[t] * term;
+    int o = 0;
+    for (int q = 0; q < j; ++q) o += pd[q].nt;
+    s_pdst[j] = d->dst;
+    s_pa[j] = resolve(d->a, io);
+    s_pt[j] = o;
+    for (int u = 0; u < d->nt; ++u) {
+      s_tw[o + u] = resolve(d->w[u], io);
+      s_td[o + u] = d->d[u];
+      s_ts[o + u] = d->s[u];
     }
-    d->dst[k] = (T)acc;
+    if (j == npd - 1) s_pt[npd] = o + d->nt;
+  }
+  __syncthreads();
+  const int k = blockIdx.x * blockDim.x + t;
+  if (k >= N) return;
+  for (int j0 = 0; j0 < ncd; j0 += kCpGroup) {
+    double xv[kCpGroup], bv[kCpGroup];
+#pragma unroll
+    for (int u = 0; u < kCpGroup; ++u) {
+      xv[u] = 0.0;
+      bv[u] = 0.0;
+      if (j0 + u < ncd) {
+        xv[u] = (double)s_cx[j0 + u][k];
+        const double* b = s_cb[j0 + u];
+        if (b) bv[u] = b[k];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kCpGroup; ++u)
+      if (j0 + u < ncd) {
+        const int j = j0 + u;
+        double val = s_cs[j] * xv[u];
+        s_cdst[j][k] = s_cb[j] ? bv[u] + val : val;
+      }
+  }
+  for (int j = 0; j < npd;) {
+    if (s_pt[j + 1] - s_pt[j] <= 1) {
+      // up to kCpGroup consecutive descriptors with at most one term each
+      int m = 1;
+      while (m < kCpGroup && j + m < npd && s_pt[j + m + 1] - s_pt[j + m] <= 1) ++m;
+      double av[kCpGroup], wv[kCpGroup], dv[kCpGroup];
+#pragma unroll
+      for (int u = 0; u < kCpGroup; ++u) {
+        av[u] = 0.0;
+        wv[u] = 0.0;
+        dv[u] = 1.0;
+        if (u < m) {
+          const double* a = s_pa[j + u];
+          if (a) av[u] = a[k];
+          const int o = s_pt[j + u];
+          if (s_pt[j + u + 1] > o) {
+            wv[u] = s_tw[o][k];
+            const double* dd = s_td[o];
+            if (dd) dv[u] = dd[k];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kCpGroup; ++u)
+        if (u < m) {
+          double acc = av[u];
+          const int o = s_pt[j + u];
+          if (s_pt[j + u + 1] > o) {
+            double term = wv[u];
+            if (s_td[o]) term *= dv[u];
+            acc += s_ts[o] * term;
+          }
+          s_pdst[j + u][k] = (T)acc;
+        }
+      j += m;
+    } else {
+      const int o0 = s_pt[j], o1 = s_pt[j + 1];
+      const double* a = s_pa[j];
+      double acc = a ? a[k] : 0.0;
+      for (int o = o0; o < o1; o += kCpGroup) {
+        double wv[kCpGroup], dv[kCpGroup];
+#pragma unroll
+        for (int q = 0; q < kCpGroup; ++q) {
+          wv[q] = 0.0;
+          dv[q] = 1.0;
+          if (o + q < o1) {
+            wv[q] = s_tw[o + q][k];
+            const double* dd = s_td[o + q];
+            if (dd) dv[q] = dd[k];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kCpGroup; ++q)
+          if (o + q < o1) {
+            double term = wv[q];
+            if (s_td[o + q]) term *= dv[q];
+            acc += s_ts[o + q] * term;
+          }
+      }
+      s_pdst[j][k] = (T)acc;
+      ++j;
+    }
   }
 }
 
