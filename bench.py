@@ -569,16 +569,26 @@ def _traffic_from_profiles(name, workload):
     return d.get("traffic_bytes_per_launch")
 
 
-TRAFFIC_SOURCES = {"level0": ("vcycle_kernels.cu", "row_dot.cuh"), "mgs": ("solve_kernels.cu",)}
+# source of each kernel class: (file, first marker, end marker); with markers,
+# only the text from the first marker up to the end marker is hashed (the
+# kernels of the class and their launcher), else the whole file
+TRAFFIC_SOURCES = {
+    "level0": (("vcycle_kernels.cu", None, None), ("row_dot.cuh", None, None)),
+    "mgs": (("solve_kernels.cu", "constexpr int kMgsU", "// v = w / ||w||: one reciprocal per block"),),
+}
 
 
 def kernel_source_sha256(name="level0"):
-    """Hash of the source files of a kernel class (the code its traffic was measured on)."""
+    """Hash of the source of a kernel class (the code its traffic was measured on)."""
     import hashlib
     h = hashlib.sha256()
-    for fn in TRAFFIC_SOURCES[name]:
+    for fn, first, end in TRAFFIC_SOURCES[name]:
         with open(os.path.join(ROOT, "paper_2002_04958_gb300", "csrc", fn), "rb") as f:
-            h.update(f.read())
+            text = f.read()
+        if first is not None:
+            i = text.index(first.encode())
+            text = text[i:text.index(end.encode(), i)]
+        h.update(text)
     return h.hexdigest()
 
 
