@@ -292,6 +292,17 @@ int mgd_profile_read_fp64(mgd_ctx *c, int cls, double *fp64_ops);
  * context; allocates ~2.5 MB stream-ordered and frees it.  MGD_EINVAL for a
  * null output, MGD_ECUDA when a CUDA call fails. */
 int mgd_fp64_issue_rate(void *stream, double *lane_ops_per_s);
+/* Self-check of the binary32 <-> binary64 conversions that the block updates
+ * of the FP32-V-cycle form (precision = 1) do on the integer pipe (IEEE
+ * 754-2008 formats, round to nearest even) against the hardware conversions,
+ * on `stream` (the current device; a CUDA stream handle or NULL): every
+ * binary32 pattern widened and narrowed back, and for every finite binary32
+ * value the binary64 tie halfway to the next binary32 and that tie's two
+ * binary64 neighbours narrowed.  Writes the number of differing results to
+ * *mismatches (NaN results compare as equal when both are NaN).  Needs no
+ * context; about 0.1 s; allocates 8 bytes stream-ordered and frees it.
+ * MGD_EINVAL for a null output, MGD_ECUDA when a CUDA call fails. */
+int mgd_check_conversions(void *stream, long long *mismatches);
 
 /* Largest n accepted by mgd_relres_noalloc (its fixed work array holds n
  * doubles plus 1216 partial sums: about 4 MiB per GPU, kept until exit). */

@@ -1215,6 +1215,7 @@ static void add_consume(std::vector<ConsumeDesc<T>>& v, PRef dst, PRef base, dou
   d.dst = dst;
   d.base = base;
   d.s = s;
+  d.unit = s == 1.0 ? 1 : (s == -1.0 ? 2 : 0);
   d.x = (const T*)x;
   (void)dvec;
   v.push_back(d);
@@ -3232,6 +3233,17 @@ int mgd_fp64_issue_rate(void* stream, double* lane_ops_per_s) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   try {
     *lane_ops_per_s = measure_fp64_rate(s);
+  } catch (const Error&) {
+    cudaGetLastError();
+    return MGD_ECUDA;
+  }
+  return MGD_OK;
+}
+
+int mgd_check_conversions(void* stream, long long* mismatches) {
+  if (!mismatches) return MGD_EINVAL;
+  try {
+    *mismatches = check_conversions(static_cast<cudaStream_t>(stream));
   } catch (const Error&) {
     cudaGetLastError();
     return MGD_ECUDA;

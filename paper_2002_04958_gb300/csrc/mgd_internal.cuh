@@ -280,6 +280,7 @@ struct ConsumeDesc {  // dst = base + s * (double)x
   PRef dst;
   PRef base;          // null: 0
   double s;
+  int unit;           // 1: s = +1, 2: s = -1 (applied without a multiply), 0: other
   const T* x;
 };
 template <typename T>
@@ -325,6 +326,7 @@ void exclusive_scan(const int* in, int* out, int n, cudaStream_t s);  // out[0..
 int read_int(const int* d, cudaStream_t s);
 // FP64 multiply-add lane operations per second of the whole device (measured)
 double measure_fp64_rate(cudaStream_t s);
+long long check_conversions(cudaStream_t s);  // mismatches of the integer-pipe format conversions
 
 void launch_validate(int n, int nnz, int N, int nc, const int* rp, const int* ci, const double* v, int* flags,
                      cudaStream_t s);

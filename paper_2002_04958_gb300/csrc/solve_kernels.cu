@@ -14,6 +14,64 @@ namespace mgd {
 
 namespace cg = cooperative_groups;
 
+// ---------------------------------------------------------------- binary32 <-> binary64
+// The block updates of the FP32-V-cycle form convert every V-cycle input and
+// output between the IEEE-754 binary32 and binary64 formats.  On this part
+// the conversion instruction issues on the FP64 pipe, which already bounds
+// these updates, so the common cases are done on the integer pipe from the
+// formats' definitions (IEEE 754-2008, 3.4 and 5.4.2; round to nearest, ties
+// to even): a normal binary32 widens exactly by rebiasing its exponent (127 ->
+// 1023) and shifting its 23-bit significand up by 29; a binary64 whose value
+// lies in the binary32 normal range keeps its top 23 significand bits and is
+// rounded on the remaining 29 (a carry out of the significand moves to the
+// next binade, and out of the largest one to infinity).  Zeros are built
+// directly; subnormal, infinite and NaN operands, and binary64 values outside
+// the binary32 normal range, take the hardware conversion.
+// mgd_check_conversions compares both with the hardware conversion.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if ((u & 0x7fffffffu) == 0) return __longlong_as_double((long long)sign);
+  if (e == 0 || e == 255) return (double)f;
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+__device__ __forceinline__ float f64_to_f32(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  if ((b << 1) == 0) return __uint_as_float(sign);
+  const int fe = (int)((b >> 52) & 0x7ffu) - 896;  // binary32 exponent field if normal
+  if (fe < 1 || fe > 254) return (float)d;
+  const unsigned keep = (unsigned)((b >> 29) & 0x7fffffu);
+  const unsigned rem = (unsigned)(b & 0x1fffffffu);
+  unsigned r = ((unsigned)fe << 23) | keep;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u))) ++r;
+  return __uint_as_float(sign | r);
+}
+
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f32_to_f64(x); }
+template <typename T>
+__device__ __forceinline__ T from_f64(double x);
+template <>
+__device__ __forceinline__ double from_f64<double>(double x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ float from_f64<float>(double x) {
+  return f64_to_f32(x);
+}
+
+// s x for a consume coefficient: +1 and -1 (every coefficient of the block
+// preconditioners, flagged on the host) without a multiply; the same bits
+__device__ __forceinline__ double unit_times(int unit, double s, double x) {
+  if (unit == 1) return x;
+  if (unit == 2) return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+  return s * x;
+}
+
 // ---------------------------------------------------------------- block-level updates
 __device__ __forceinline__ double* resolve(const PRef& r, const IOSlots* io) {
   if (r.slot == 0) return r.abs;
@@ -37,7 +95,7 @@ __global__ void k_produce(const ProduceDesc<T>* __restrict__ ds, int N, const IO
     if (d->d[t]) term *= d->d[t][k];
     acc += d->s[t] * term;
   }
-  d->dst[k] = (T)acc;
+  d->dst[k] = from_f64<T>(acc);
 }
 
 // dst = base + s * x
@@ -49,7 +107,7 @@ __global__ void k_consume(const ConsumeDesc<T>* __restrict__ ds, int N, const IO
   if (k >= N) return;
   double* dst = resolve(d->dst, io);
   const double* base = resolve(d->base, io);
-  double val = d->s * (double)d->x[k];
+  double val = unit_times(d->unit, d->s, to_f64(d->x[k]));
   dst[k] = base ? base[k] + val : val;
 }
 
@@ -74,6 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_consume_produce(const ConsumeDesc<
   __shared__ const double* s_cb[kCpMaxCons];
   __shared__ double* s_cdst[kCpMaxCons];
   __shared__ double s_cs[kCpMaxCons];
+  __shared__ int s_cu[kCpMaxCons];
   __shared__ T* s_pdst[kCpMaxProd];
   __shared__ const double* s_pa[kCpMaxProd];
   __shared__ int s_pt[kCpMaxProd + 1];  // terms of produce j: [s_pt[j], s_pt[j+1])
@@ -88,6 +147,7 @@ __global__ void __launch_bounds__(kThreads) k_consume_produce(const ConsumeDesc<
     s_cb[j] = resolve(d->base, io);
     s_cdst[j] = resolve(d->dst, io);
     s_cs[j] = d->s;
+    s_cu[j] = d->unit;
   }
   for (int j = t; j < npd; j += blockDim.x) {
     const ProduceDesc<T>* d = pd + j;
@@ -113,7 +173,7 @@ __global__ void __launch_bounds__(kThreads) k_consume_produce(const ConsumeDesc<
       xv[u] = 0.0;
       bv[u] = 0.0;
       if (j0 + u < ncd) {
-        xv[u] = (double)s_cx[j0 + u][k];
+        xv[u] = to_f64(s_cx[j0 + u][k]);
         const double* b = s_cb[j0 + u];
         if (b) bv[u] = b[k];
       }
@@ -122,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) k_consume_produce(const ConsumeDesc<
     for (int u = 0; u < kCpGroup; ++u)
       if (j0 + u < ncd) {
         const int j = j0 + u;
-        double val = s_cs[j] * xv[u];
+        double val = unit_times(s_cu[j], s_cs[j], xv[u]);
         s_cdst[j][k] = s_cb[j] ? bv[u] + val : val;
       }
   }
@@ -158,7 +218,7 @@ __global__ void __launch_bounds__(kThreads) k_consume_produce(const ConsumeDesc<
             if (s_td[o]) term *= dv[u];
             acc += s_ts[o] * term;
           }
-          s_pdst[j + u][k] = (T)acc;
+          s_pdst[j + u][k] = from_f64<T>(acc);
         }
       j += m;
     } else {
@@ -185,7 +245,7 @@ __global__ void __launch_bounds__(kThreads) k_consume_produce(const ConsumeDesc<
             acc += s_ts[o + q] * term;
           }
       }
-      s_pdst[j][k] = (T)acc;
+      s_pdst[j][k] = from_f64<T>(acc);
       ++j;
     }
   }
@@ -242,6 +302,63 @@ double measure_fp64_rate(cudaStream_t s) {
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess || ms <= 0.f) throw Error{MGD_ECUDA, "FP64 rate measurement failed"};
   return (double)blocks * threads * iters * 4.0 / (ms * 1e-3);
+}
+
+// Self-check of f32_to_f64 / f64_to_f32 against the hardware conversions:
+// every binary32 pattern widened; and narrowed, for every binary32 value f, f
+// itself, the midpoint between f and the next binary32 above it (a tie) and
+// the binary64 neighbours of that midpoint.  NaN results compare as equal
+// when both are NaN.
+__device__ __forceinline__ bool same_f64(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b) || (isnan(a) && isnan(b));
+}
+__device__ __forceinline__ bool same_f32(float a, float b) {
+  return __float_as_uint(a) == __float_as_uint(b) || (isnan(a) && isnan(b));
+}
+
+__global__ void k_check_conversions(unsigned long long* mismatches) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  unsigned long long bad = 0;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < (1ull << 32); i += stride) {
+    const unsigned u = (unsigned)i;
+    const float f = __uint_as_float(u);
+    const double w = (double)f;
+    if (!same_f64(f32_to_f64(f), w)) ++bad;
+    if (!same_f32(f64_to_f32(w), (float)w)) ++bad;
+    if ((u & 0x7f800000u) != 0x7f800000u && (u & 0x7fffffffu) != 0x7f7fffffu) {
+      // the next binary32 away from zero is finite: the midpoint is exact in binary64
+      const double up = (double)__uint_as_float(u + 1u);
+      const double mid = 0.5 * (w + up);
+      const long long mb = __double_as_longlong(mid);
+      const double lo = __longlong_as_double(mb - 1), hi = __longlong_as_double(mb + 1);
+      if (!same_f32(f64_to_f32(mid), (float)mid)) ++bad;
+      if (!same_f32(f64_to_f32(lo), (float)lo)) ++bad;
+      if (!same_f32(f64_to_f32(hi), (float)hi)) ++bad;
+    }
+  }
+  if (bad) atomicAdd(mismatches, bad);
+}
+
+long long check_conversions(cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  MGD_CUDA(cudaGetDevice(&dev));
+  MGD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  unsigned long long* d = nullptr;
+  unsigned long long h = 0;
+  cudaError_t e = cudaMallocAsync(&d, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) {
+    k_check_conversions<<<8 * nsm, 256, 0, s>>>(d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (d) {
+    cudaFreeAsync(d, s);
+    cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) throw Error{MGD_ECUDA, "conversion check failed"};
+  return (long long)h;
 }
 
 template <typename T>

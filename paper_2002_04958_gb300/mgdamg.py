@@ -26,7 +26,8 @@ ENTRY_POINTS = ["mgd_opts_default", "mgd_create", "mgd_setup", "mgd_update_value
                 "mgd_op_info", "mgd_level_info", "mgd_level_export", "mgd_block_vector", "mgd_coupling_dropped",
                 "mgd_profile_enable", "mgd_profile_read", "mgd_kernel_launches", "mgd_last_error", "mgd_destroy", "mgd_plan_info",
                 "mgd_setup_phases", "mgd_op_cycles", "mgd_level_keys", "mgd_precond_bench",
-                "mgd_relres_noalloc", "mgd_profile_read_fp64", "mgd_fp64_issue_rate", "mgd_setup_host"]
+                "mgd_relres_noalloc", "mgd_profile_read_fp64", "mgd_fp64_issue_rate", "mgd_setup_host",
+                "mgd_check_conversions"]
 
 
 class MgdOpts(C.Structure):
@@ -90,6 +91,7 @@ def lib():
             "mgd_profile_read": (I, [P, I, pLL, pD, pD]),
             "mgd_profile_read_fp64": (I, [P, I, pD]),
             "mgd_fp64_issue_rate": (I, [P, pD]),
+            "mgd_check_conversions": (I, [P, pLL]),
             "mgd_kernel_launches": (C.c_longlong, []),
             "mgd_relres_noalloc": (I, [I, P, P, P, P, P, P, P]),
             "mgd_setup_host": (I, [P, I, I, I, I, P, P, P, I]),
@@ -183,6 +185,18 @@ def fp64_issue_rate(stream=None):
     rc = lib().mgd_fp64_issue_rate(C.c_void_p(st.cuda_stream), C.byref(r))
     if rc != 0:
         raise MgdError(rc, "mgd_fp64_issue_rate failed")
+    return r.value
+
+
+def check_conversions(stream=None):
+    """Mismatches of the library's integer-pipe binary32 <-> binary64
+    conversions against the hardware ones (expected 0)."""
+    import torch
+    st = stream or torch.cuda.current_stream()
+    r = C.c_longlong()
+    rc = lib().mgd_check_conversions(C.c_void_p(st.cuda_stream), C.byref(r))
+    if rc != 0:
+        raise MgdError(rc, "mgd_check_conversions failed")
     return r.value
 
 

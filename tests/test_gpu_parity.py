@@ -479,6 +479,12 @@ def test_transfer_layouts_bit_identical(gpu, tmp_path):
                 assert res[f][name][k] == res[1][name][k], (f, name, k)
 
 
+def test_format_conversions_match_hardware(gpu):
+    # the block updates of the FP32-V-cycle form convert on the integer pipe;
+    # every binary32 pattern, every binary32 tie and its binary64 neighbours
+    assert gpu.check_conversions() == 0
+
+
 def test_fp64_accounting_and_issue_rate(gpu):
     # the FP64 roofline inputs: a measured device rate and the algorithmic FP64
     # lane operations of the level-0 l1-Jacobi kernels (none in FP32 V-cycles)
