@@ -28,12 +28,17 @@ namespace cg = cooperative_groups;
 // directly; subnormal, infinite and NaN operands, and binary64 values outside
 // the binary32 normal range, take the hardware conversion.
 // mgd_check_conversions compares both with the hardware conversion.
+// the hardware conversions of the rare operands, out of line so that the
+// common path does not issue them predicated off
+__device__ __noinline__ double f32_to_f64_hw(float f) { return (double)f; }
+__device__ __noinline__ float f64_to_f32_hw(double d) { return (float)d; }
+
 __device__ __forceinline__ double f32_to_f64(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xffu;
   const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
   if ((u & 0x7fffffffu) == 0) return __longlong_as_double((long long)sign);
-  if (e == 0 || e == 255) return (double)f;
+  if (e == 0 || e == 255) return f32_to_f64_hw(f);
   return __longlong_as_double(
       (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
 }
@@ -43,7 +48,7 @@ __device__ __forceinline__ float f64_to_f32(double d) {
   const unsigned sign = (unsigned)(b >> 63) << 31;
   if ((b << 1) == 0) return __uint_as_float(sign);
   const int fe = (int)((b >> 52) & 0x7ffu) - 896;  // binary32 exponent field if normal
-  if (fe < 1 || fe > 254) return (float)d;
+  if (fe < 1 || fe > 254) return f64_to_f32_hw(d);
   const unsigned keep = (unsigned)((b >> 29) & 0x7fffffu);
   const unsigned rem = (unsigned)(b & 0x1fffffffu);
   unsigned r = ((unsigned)fe << 23) | keep;
