@@ -340,8 +340,9 @@ def run_ours(args):
         slv.solve_host_ptr(h_b.data_ptr(), h_x.data_ptr(), tol=args.tol)
         if k > 0:
             st_e = slv.stats()
+            ph = slv.setup_phases()
             e2e_parts.append(((t_s - t_a) * 1e3, st_e["setup_ms"], (time.perf_counter() - t_s) * 1e3,
-                              st_e["solve_ms"], slv.setup_phases()["h2d_copies"]))
+                              st_e["solve_ms"], ph["h2d_copies"], ph["release_previous"]))
         if args.adjoint:
             d_x.copy_(h_x, non_blocking=True)
             lam_e, _, _ = slv.solve_transpose(2.0 * d_x, tol=args.tol)
@@ -474,7 +475,9 @@ def run_ours(args):
                                      "setup_inside": round(statistics.median(p[1] for p in e2e_parts), 3),
                                      "solve_host_call": round(statistics.median(p[2] for p in e2e_parts), 3),
                                      "solve_inside": round(statistics.median(p[3] for p in e2e_parts), 3),
-                                     "h2d_csr_copies": round(statistics.median(p[4] for p in e2e_parts), 3)}
+                                     "h2d_csr_copies": round(statistics.median(p[4] for p in e2e_parts), 3),
+                                     "release_previous_setup": round(statistics.median(p[5] for p in e2e_parts),
+                                                                     3)}
                                     if e2e_parts else None)},
         "gpu_launches": launches,
         "clocks": clk,

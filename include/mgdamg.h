@@ -242,7 +242,9 @@ int mgd_coupling_dropped(mgd_ctx *c, int a, int b);
  * these eight summed over every hierarchy (built concurrently, so they can
  * exceed the wall time) -- then 8 validation, 9 block extraction, 10 all
  * hierarchies (wall), 11 PCTL vectors and coarse operator, 12 launch program,
- * batches and autotuning, 13 Krylov storage and graph capture. */
+ * batches and autotuning, 13 Krylov storage and graph capture, 14 Gauss-Seidel
+ * colouring (summed), 15 host-to-device copies (mgd_setup_host), 16 release of
+ * the previous setup's device memory and graph. */
 int mgd_setup_phases(mgd_ctx *c, double *h_ms, int n);
 
 /* Launch plan of the V-cycle batches: *nbatches batches (independent V-cycles

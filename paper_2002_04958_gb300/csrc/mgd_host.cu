@@ -202,7 +202,8 @@ struct Hier {
 // threads add concurrently, so the hierarchy phases can sum past wall time)
 enum SetupPhase {
   SP_STRENGTH = 0, SP_PMIS, SP_INTERP, SP_TRANSPOSE, SP_AP, SP_RAP, SP_FINALIZE, SP_COARSE,
-  SP_VALIDATE, SP_BLOCKS, SP_HIERARCHIES, SP_PCTL, SP_PROGRAM, SP_KRYLOV, SP_COLOUR, SP_H2D, SP_COUNT = 16
+  SP_VALIDATE, SP_BLOCKS, SP_HIERARCHIES, SP_PCTL, SP_PROGRAM, SP_KRYLOV, SP_COLOUR, SP_H2D, SP_RELEASE,
+  SP_COUNT = 17
 };
 struct PhaseClock {
   std::mutex mu;
@@ -2250,6 +2251,18 @@ static void free_setup(mgd_ctx* c) {
   c->napply = c->napplyT = 0;
 }
 
+// free_setup, timed (ms): do_setup resets the phase clock, so callers record it afterwards
+static double free_setup_timed(mgd_ctx* c) {
+  const auto t = std::chrono::steady_clock::now();
+  free_setup(c);
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+}
+
+static void record_phase(mgd_ctx* c, int ph, double ms) {
+  std::lock_guard<std::mutex> lk(c->phases.mu);
+  c->phases.ms[ph] = ms;
+}
+
 static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) {
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = c->s;
@@ -2862,13 +2875,14 @@ int mgd_setup(mgd_ctx* c, int G, int N, int n, int nnz, const int* d_rowptr, con
     if (G < 1 || N < 1 || n != (G + 2) * N || nnz < n || !d_rowptr || !d_colidx || !d_vals || kind < 0 ||
         kind > MGD_BLT || G + 1 > kMaxTerms - 1)
       throw Error{MGD_EINVAL, "invalid sizes or kind"};
-    free_setup(c);
+    const double rel_ms = free_setup_timed(c);
     c->G = G;
     c->N = N;
     c->n = n;
     c->nnz = nnz;
     c->kind = kind;
     do_setup(c, d_rowptr, d_colidx, d_vals);
+    record_phase(c, SP_RELEASE, rel_ms);
     return MGD_OK;
   });
 }
@@ -2927,17 +2941,15 @@ int mgd_setup_host(mgd_ctx* c, int G, int N, int n, int nnz, const int* h_rowptr
     }
     MGD_CUDA(cudaStreamSynchronize(c->s));
     const double h2d_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th).count();
-    free_setup(c);
+    const double rel_ms = free_setup_timed(c);
     c->G = G;
     c->N = N;
     c->n = n;
     c->nnz = nnz;
     c->kind = kind;
     do_setup(c, rp, ci, v);
-    {
-      std::lock_guard<std::mutex> lk(c->phases.mu);
-      c->phases.ms[SP_H2D] = h2d_ms;  // after do_setup, which resets the phase clock
-    }
+    record_phase(c, SP_H2D, h2d_ms);
+    record_phase(c, SP_RELEASE, rel_ms);
     return MGD_OK;
   });
 }
@@ -2954,8 +2966,9 @@ int mgd_update_values(mgd_ctx* c, const double* d_vals) {
     MGD_CUDA(cudaMemcpyAsync(ci, c->A.ci, sizeof(int) * c->nnz, cudaMemcpyDeviceToDevice, c->s));
     MGD_CUDA(cudaMemcpyAsync(v, d_vals, sizeof(double) * c->nnz, cudaMemcpyDeviceToDevice, c->s));
     MGD_CUDA(cudaStreamSynchronize(c->s));
-    free_setup(c);
+    const double rel_ms = free_setup_timed(c);
     do_setup(c, rp, ci, v);
+    record_phase(c, SP_RELEASE, rel_ms);
     return MGD_OK;
   });
 }

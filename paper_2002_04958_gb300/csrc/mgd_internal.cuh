@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -111,24 +112,61 @@ inline void* pool_alloc(cudaMemPool_t pool, size_t bytes, cudaStream_t s) {
 }
 
 // Allocations owned by a context, freed together at destroy / re-setup.
-// Safe to use from the setup worker threads: each allocates (and zeroes) on
-// its own stream and synchronises it before the memory is used elsewhere.
+// Arrays are carved, 256-byte aligned, from slabs of the context's pool (the
+// first 4 MiB, each next one twice the last, up to 1 GiB; an array above 256
+// MiB gets a block of its own), so a setup makes a few dozen pool allocations
+// instead of thousands and the release frees as many.  A slab is allocated on the arena's own stream, which is otherwise
+// idle, and synchronised there before any array in it is handed out, so every
+// stream may use it; arrays are never freed one by one.  Safe to use from the
+// setup worker threads: each zeroes on its own stream and synchronises it
+// before the memory is used elsewhere.
 struct Arena {
-  std::vector<void*> ptrs;
-  cudaStream_t stream = nullptr;
+  std::vector<void*> ptrs;          // slabs and separate blocks
+  cudaStream_t stream = nullptr;    // the context stream (release)
   cudaMemPool_t pool = nullptr;
+  cudaStream_t astream = nullptr;   // slab allocations
   std::mutex mu;
+  char* cur = nullptr;              // free part of the current slab
+  size_t left = 0;
+  size_t next_slab = kSlabMin;
+  static constexpr size_t kSlabMin = (size_t)4 << 20, kSlabMax = (size_t)1 << 30;
+  static constexpr size_t kAlign = 256;
   template <typename T>
   T* alloc(size_t n, bool zero = false, cudaStream_t zs = nullptr) {
-    size_t bytes = (n ? n : 1) * sizeof(T);
+    const size_t bytes = (n ? n : 1) * sizeof(T);
+    const size_t need = (bytes + kAlign - 1) & ~(kAlign - 1);
     cudaStream_t st = zs ? zs : (tl_stream ? tl_stream : stream);
-    void* p = pool_alloc(pool, bytes, st);
+    void* p;
     {
       std::lock_guard<std::mutex> lk(mu);
-      ptrs.push_back(p);
+      if (need > kSlabMax / 4) {
+        p = block_locked(need);
+      } else {
+        if (need > left) {
+          size_t sz = next_slab;
+          while (sz < need) sz *= 2;
+          cur = static_cast<char*>(block_locked(sz));
+          left = sz;
+          next_slab = std::min(sz * 2, kSlabMax);
+        }
+        p = cur;
+        cur += need;
+        left -= need;
+      }
     }
     if (zero) MGD_CUDA(cudaMemsetAsync(p, 0, bytes, st));
     return (T*)p;
+  }
+  void* block_locked(size_t bytes) {
+    if (!astream) MGD_CUDA(cudaStreamCreateWithFlags(&astream, cudaStreamNonBlocking));
+    void* p = pool_alloc(pool, bytes, astream);
+    const cudaError_t e = cudaStreamSynchronize(astream);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(p, astream);
+      throw Error{8, std::string("device allocation failed: ") + cudaGetErrorString(e)};
+    }
+    ptrs.push_back(p);
+    return p;
   }
   void release() {
     std::lock_guard<std::mutex> lk(mu);
@@ -136,6 +174,12 @@ struct Arena {
     for (void* p : ptrs) cudaFreeAsync(p, stream);
     if (stream) cudaStreamSynchronize(stream);
     ptrs.clear();
+    cur = nullptr;
+    left = 0;
+    next_slab = kSlabMin;
+  }
+  ~Arena() {
+    if (astream) cudaStreamDestroy(astream);
   }
 };
 

@@ -440,11 +440,11 @@ class Solver:
 
     SETUP_PHASES = ["strength", "pmis", "interp", "transpose", "AP", "RAP", "finalize", "coarse_inverse",
                     "validate", "blocks", "hierarchies_wall", "pctl", "program_autotune", "krylov_graph",
-                    "gs_colouring", "h2d_copies"]
+                    "gs_colouring", "h2d_copies", "release_previous"]
 
     def setup_phases(self):
-        ms = np.zeros(16)
-        self._check(lib().mgd_setup_phases(self.h, ms.ctypes.data_as(C.c_void_p), 16))
+        ms = np.zeros(len(self.SETUP_PHASES))
+        self._check(lib().mgd_setup_phases(self.h, ms.ctypes.data_as(C.c_void_p), len(self.SETUP_PHASES)))
         return {k: round(float(v), 3) for k, v in zip(self.SETUP_PHASES, ms)}
 
     def plan(self):
