@@ -30,6 +30,7 @@ long long g_kernel_launches = 0;
 thread_local cudaMemPool_t tl_pool = nullptr;
 thread_local bool tl_pdl = false;
 thread_local cudaStream_t tl_stream = nullptr;
+thread_local ScratchRegion* tl_region = nullptr;
 
 enum OpKind { OP_A = 0, OP_CE = 1, OP_CG = 2, OP_SG = 3, OP_SI = 4, OP_AC = 5, OP_MONO = 6 };
 
@@ -1326,11 +1327,14 @@ static void finalize_ops_parallel(mgd_ctx* c, size_t first, size_t last) {
   std::mutex emu;
   auto worker = [&]() {
     cudaStream_t st = nullptr;
+    ScratchRegion* region = nullptr;
     try {
       MGD_CUDA(cudaSetDevice(c->device));
       MGD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
       tl_pool = c->ar.pool;
       tl_stream = st;
+      region = new ScratchRegion(st, c->ar.pool);
+      tl_region = region;
       for (size_t k = next++; k < last; k = next++) finalize_op<T>(c, c->ops[k], st);
     } catch (const Error& e) {
       std::lock_guard<std::mutex> lk(emu);
@@ -1339,6 +1343,9 @@ static void finalize_ops_parallel(mgd_ctx* c, size_t first, size_t last) {
       std::lock_guard<std::mutex> lk(emu);
       errs.push_back(Error{MGD_ECUDA, e.what()});
     }
+    tl_region = nullptr;
+    if (st) cudaStreamSynchronize(st);
+    delete region;  // its chunks are freed on st, after everything issued there
     if (st) {
       cudaStreamSynchronize(st);
       cudaStreamDestroy(st);

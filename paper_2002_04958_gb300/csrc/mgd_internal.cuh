@@ -183,20 +183,89 @@ struct Arena {
   }
 };
 
-// Scratch allocations for one setup step (stream-ordered, freed at scope exit)
+// Scratch memory of one setup worker thread, for the work it issues on its
+// own stream: chunks of the context's pool (64 MiB first, doubling), handed out
+// as a stack of 256-byte aligned blocks.  A freed block is marked dead and the
+// stack top rewinds over dead blocks, so memory comes back in the order the
+// scopes close; a block reused this way is only ever touched by later work on
+// the same stream, which the stream orders after the work that used it
+// before.  This replaces one pool allocation and one pool free per scratch
+// array, which the concurrent setup threads otherwise serialise on.
+struct ScratchRegion {
+  struct Chunk {
+    char* base;
+    size_t size;
+  };
+  struct Blk {
+    int chunk;
+    size_t off, bytes;
+    bool live;
+  };
+  cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+  std::vector<Chunk> chunks;
+  std::vector<Blk> stack;
+  static constexpr size_t kChunkMin = (size_t)64 << 20;
+  ScratchRegion(cudaStream_t s, cudaMemPool_t p) : stream(s), pool(p) {}
+  void* alloc(size_t bytes) {
+    const size_t need = (bytes + 255) & ~(size_t)255;
+    int c = stack.empty() ? 0 : stack.back().chunk;
+    size_t off = stack.empty() ? 0 : stack.back().off + stack.back().bytes;
+    if (!chunks.empty() && off + need > chunks[c].size) {
+      ++c;
+      off = 0;
+    }
+    if (c >= (int)chunks.size() || chunks[c].size < need) {
+      size_t sz = std::max(kChunkMin, chunks.empty() ? need : 2 * chunks.back().size);
+      while (sz < need) sz *= 2;
+      if (c < (int)chunks.size()) {  // too small for this block: replaced (stream-ordered free)
+        cudaFreeAsync(chunks[c].base, stream);
+        chunks[c] = Chunk{static_cast<char*>(pool_alloc(pool, sz, stream)), sz};
+      } else {
+        chunks.push_back(Chunk{static_cast<char*>(pool_alloc(pool, sz, stream)), sz});
+      }
+    }
+    stack.push_back(Blk{c, off, need, true});
+    return chunks[c].base + off;
+  }
+  void free(void* p) {
+    for (size_t k = stack.size(); k-- > 0;)
+      if (chunks[stack[k].chunk].base + stack[k].off == p && stack[k].live) {
+        stack[k].live = false;
+        break;
+      }
+    while (!stack.empty() && !stack.back().live) stack.pop_back();
+  }
+  ~ScratchRegion() {
+    for (auto& ch : chunks) cudaFreeAsync(ch.base, stream);
+  }
+};
+
+// the scratch region of the calling setup worker thread (nullptr elsewhere)
+extern thread_local ScratchRegion* tl_region;
+
+// Scratch allocations for one setup step (stream-ordered, freed at scope
+// exit): from the calling worker's region when they are for its stream, else
+// from the pool
 struct Scratch {
   std::vector<void*> ptrs;
   cudaStream_t stream;
   cudaMemPool_t pool;
-  explicit Scratch(cudaStream_t s, cudaMemPool_t p = nullptr) : stream(s), pool(p ? p : tl_pool) {}
+  ScratchRegion* region;
+  explicit Scratch(cudaStream_t s, cudaMemPool_t p = nullptr)
+      : stream(s), pool(p ? p : tl_pool), region(tl_region && tl_region->stream == s ? tl_region : nullptr) {}
   template <typename T>
   T* alloc(size_t n) {
-    void* p = pool_alloc(pool, (n ? n : 1) * sizeof(T), stream);
+    const size_t bytes = (n ? n : 1) * sizeof(T);
+    void* p = region ? region->alloc(bytes) : pool_alloc(pool, bytes, stream);
     ptrs.push_back(p);
     return (T*)p;
   }
   ~Scratch() {
-    for (void* p : ptrs) cudaFreeAsync(p, stream);
+    for (size_t k = ptrs.size(); k-- > 0;) {
+      if (region) region->free(ptrs[k]);
+      else cudaFreeAsync(ptrs[k], stream);
+    }
   }
 };
 
