@@ -294,15 +294,15 @@ static Csr transpose(Arena& a, const Csr& X, cudaStream_t s, Scratch* keep = nul
   T.n = X.m;
   T.m = X.n;
   T.nnz = X.nnz;
-  int* cnt = sc.alloc<int>(X.m);
-  MGD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * std::max(X.m, 1), s));
+  const int m1 = std::max(X.m, 1);
+  int* cnt = sc.alloc<int>(2 * (size_t)m1);  // column counts, then the fill cursors
+  int* cur = cnt + m1;
+  MGD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)m1, s));
   launch_transpose_count(X.nnz, X.ci, cnt, s);
   T.rp = keep ? keep->alloc<int>(T.n + 1) : a.alloc<int>(T.n + 1);
   exclusive_scan(cnt, T.rp, T.n, s);
   T.ci = keep ? keep->alloc<int>(T.nnz) : a.alloc<int>(T.nnz);
   T.v = keep ? keep->alloc<double>(T.nnz) : a.alloc<double>(T.nnz);
-  int* cur = sc.alloc<int>(X.m);
-  MGD_CUDA(cudaMemsetAsync(cur, 0, sizeof(int) * std::max(X.m, 1), s));
   launch_transpose_fill(X.n, X.rp, X.ci, X.v, T.rp, cur, T.ci, T.v, s);
   launch_sort_rows(T.n, T.rp, T.ci, T.v, s);
   return T;
@@ -420,14 +420,13 @@ static bool coarsen_pass(SetupCtx& sc, const Csr& A, int lid, Scratch* keep, Pas
   PhaseTimer pt_str(sc.clk, SP_STRENGTH);
   uint8_t* S = tmp.alloc<uint8_t>(A.nnz);
   launch_strength(n, A.rp, A.ci, A.v, o.theta_str, S, s);
-  int* cnt = tmp.alloc<int>(n);
-  MGD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * n, s));
+  int* cnt = tmp.alloc<int>(2 * (size_t)n);  // strong counts, then the fill cursors
+  int* cur = cnt + n;
+  MGD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)n, s));
   launch_count_st(n, A.rp, A.ci, S, cnt, s);
   int* strp = tmp.alloc<int>(n + 1);
   exclusive_scan(cnt, strp, n, s);
   int* stci = tmp.alloc<int>(A.nnz);  // at most every entry is strong: no read-back of the count
-  int* cur = tmp.alloc<int>(n);
-  MGD_CUDA(cudaMemsetAsync(cur, 0, sizeof(int) * n, s));
   launch_fill_st(n, A.rp, A.ci, S, strp, cur, stci, s);
   pt_str.stop();
   PhaseTimer pt_pmis(sc.clk, SP_PMIS);
@@ -620,16 +619,17 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
         launch_colscale(lv.AT.nnz, lv.AT.ci, lv.AT.v, lv.dinv, lv.atvpre, s);
       }
     }
-    size_t es = sc.mixed ? sizeof(float) : sizeof(double);
-    lv.b = ar.alloc<char>(es * n);
-    lv.xt = ar.alloc<char>(es * n);
+    // the level's vectors b, xt, (x,) r in one zeroed block, each 256-byte aligned;
     // Gauss-Seidel levels smooth in place: the level's output is xt itself
-    lv.x = lv.nk > 0 ? lv.xt : ar.alloc<char>(es * n);
-    lv.r = ar.alloc<char>(es * n);
-    MGD_CUDA(cudaMemsetAsync(lv.b, 0, es * n, s));
-    MGD_CUDA(cudaMemsetAsync(lv.x, 0, es * n, s));
-    MGD_CUDA(cudaMemsetAsync(lv.xt, 0, es * n, s));
-    MGD_CUDA(cudaMemsetAsync(lv.r, 0, es * n, s));
+    size_t es = sc.mixed ? sizeof(float) : sizeof(double);
+    const size_t vb = (es * n + 255) & ~(size_t)255;
+    const int nvec = lv.nk > 0 ? 3 : 4;
+    char* vecs = ar.alloc<char>(vb * nvec);
+    MGD_CUDA(cudaMemsetAsync(vecs, 0, vb * nvec, s));
+    lv.b = vecs;
+    lv.xt = vecs + vb;
+    lv.x = lv.nk > 0 ? lv.xt : vecs + 2 * vb;
+    lv.r = vecs + (nvec - 1) * vb;
   }
   MGD_CUDA(cudaStreamSynchronize(s));
   pt_fin.stop();

@@ -12,8 +12,10 @@
 namespace mgd {
 
 // ------------------------------------------------------------------ scan
-template <typename I>
-__global__ void k_scan_block_i(const I* in, I* out, I* bsum, int n) {
+// per block of kThreads * 4 outputs: exclusive sums of in[0..n_in) followed
+// by zeros (n outputs), and the block's total in bsum
+template <typename IN, typename I>
+__global__ void k_scan_block_i(const IN* in, int n_in, I* out, I* bsum, int n) {
   __shared__ I sh[kThreads];
   int base = blockIdx.x * kThreads * 4;
   I v[4];
@@ -21,7 +23,7 @@ __global__ void k_scan_block_i(const I* in, I* out, I* bsum, int n) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     int i = base + threadIdx.x * 4 + k;
-    v[k] = i < n ? in[i] : 0;
+    v[k] = i < n_in ? (I)in[i] : (I)0;
     tsum += v[k];
   }
   sh[threadIdx.x] = tsum;
@@ -47,20 +49,6 @@ __global__ void k_scan_add(I* out, const I* boff, int n, I* total_out, const I* 
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] += boff[i / (kThreads * 4)];
   if (i == 0 && total_out) *total_out = *btotal;
-}
-
-// exclusive scan of I-typed values (recursive over block sums)
-template <typename I>
-static void scan_rec(const I* in, I* out, int n, cudaStream_t s, Scratch& sc) {
-  int nb = cdiv(n, kThreads * 4);
-  I* bsum = sc.alloc<I>(nb + 1);
-  I* boff = sc.alloc<I>(nb + 1);
-  k_scan_block_i<I><<<nb, kThreads, 0, s>>>(in, out, bsum, n);
-  MGD_LAUNCH_CHECK();
-  if (nb > 1) scan_rec<I>(bsum, boff, nb, s, sc);
-  else MGD_CUDA(cudaMemsetAsync(boff, 0, sizeof(I), s));
-  k_scan_add<I><<<cdiv(n, kThreads), kThreads, 0, s>>>(out, boff, n, nullptr, nullptr);
-  MGD_LAUNCH_CHECK();
 }
 
 // one block: exclusive sums of in[0..n_in) followed by zeros, n outputs,
@@ -100,6 +88,26 @@ __global__ void __launch_bounds__(kOneThreads) k_scan_one(const IN* in, int n_in
   }
 }
 
+// out[0..n_out): exclusive sums of in[0..n_in) followed by zeros: blocks of
+// kThreads * 4, their totals scanned by one block (or again by this, for
+// more than kOneMax blocks), then added back; the input is read in place
+template <typename IN, typename I>
+static void scan_big(const IN* in, int n_in, I* out, int n_out, cudaStream_t s, Scratch& sc) {
+  const int nb = cdiv(n_out, kThreads * 4);
+  I* bsum = sc.alloc<I>(nb);
+  I* boff = sc.alloc<I>(nb);
+  k_scan_block_i<IN, I><<<nb, kThreads, 0, s>>>(in, n_in, out, bsum, n_out);
+  MGD_LAUNCH_CHECK();
+  if (nb <= kOneMax) {
+    k_scan_one<I, I><<<1, kOneThreads, 0, s>>>(bsum, nb, boff, nb);
+    MGD_LAUNCH_CHECK();
+  } else {
+    scan_big<I, I>(bsum, nb, boff, nb, s, sc);
+  }
+  k_scan_add<I><<<cdiv(n_out, kThreads), kThreads, 0, s>>>(out, boff, n_out, nullptr, nullptr);
+  MGD_LAUNCH_CHECK();
+}
+
 // out[0..n]: exclusive prefix sums of in[0..n), out[n] = total
 void exclusive_scan(const int* in, int* out, int n, cudaStream_t s) {
   if (n + 1 <= kOneMax) {
@@ -108,16 +116,7 @@ void exclusive_scan(const int* in, int* out, int n, cudaStream_t s) {
     return;
   }
   Scratch sc(s);
-  int* ext = sc.alloc<int>(n + 1);
-  MGD_CUDA(cudaMemcpyAsync(ext, in, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
-  MGD_CUDA(cudaMemsetAsync(ext + n, 0, sizeof(int), s));
-  scan_rec<int>(ext, out, n + 1, s, sc);
-}
-
-__global__ void k_widen(const int* in, long long* out, int n) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = in[i];
-  if (i == n) out[n] = 0;
+  scan_big<int, int>(in, n, out, n + 1, s, sc);
 }
 
 void launch_offsets64(const int* cnt, long long* off, int n, cudaStream_t s) {
@@ -127,10 +126,7 @@ void launch_offsets64(const int* cnt, long long* off, int n, cudaStream_t s) {
     return;
   }
   Scratch sc(s);
-  long long* ext = sc.alloc<long long>(n + 1);
-  k_widen<<<cdiv(n + 1, kThreads), kThreads, 0, s>>>(cnt, ext, n);
-  MGD_LAUNCH_CHECK();
-  scan_rec<long long>(ext, off, n + 1, s, sc);
+  scan_big<int, long long>(cnt, n, off, n + 1, s, sc);
 }
 
 int read_int(const int* d, cudaStream_t s) {
