@@ -582,8 +582,10 @@ __device__ __forceinline__ bool beats(const double* w, int i, int j) {
 
 // round part 1: undecided local maxima over S_i and S^T_i become C (newc)
 __global__ void k_pmis_select(int n, const int* rp, const int* ci, const uint8_t* S, const int* strp,
-                              const int* stci, const double* w, const signed char* CF, uint8_t* newc) {
+                              const int* stci, const double* w, const signed char* CF, uint8_t* newc,
+                              int* undecided) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *undecided = 0;  // counted by k_pmis_fmark, the next launch on the stream
   if (i >= n) return;
   uint8_t res = 0;
   if (CF[i] == 0) {
@@ -597,19 +599,22 @@ __global__ void k_pmis_select(int n, const int* rp, const int* ci, const uint8_t
   newc[i] = res;
 }
 
-__global__ void k_pmis_apply(int n, const uint8_t* newc, signed char* CF) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && newc[i]) CF[i] = 1;
-}
-
-// round part 2: undecided points that strongly depend on a C point become F
-__global__ void k_pmis_fmark(int n, const int* rp, const int* ci, const uint8_t* S, signed char* CF,
-                             int* undecided) {
+// round part 2: the points selected in part 1 become C; undecided points that
+// strongly depend on a C point (an old one, or one selected in part 1) become
+// F.  A neighbour's CF may change during this launch only from 0 to 1 (when
+// it was selected, which newc shows as well) or from 0 to -1 (when it was not),
+// so the test CF == 1 || newc reads the same either way.
+__global__ void k_pmis_fmark(int n, const int* rp, const int* ci, const uint8_t* S, const uint8_t* newc,
+                             signed char* CF, int* undecided) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (newc[i]) {
+    CF[i] = 1;
+    return;
+  }
   if (CF[i] != 0) return;
   for (int p = rp[i]; p < rp[i + 1]; ++p)
-    if (S[p] && CF[ci[p]] == 1) {
+    if (S[p] && (CF[ci[p]] == 1 || newc[ci[p]])) {
       CF[i] = -1;
       return;
     }
@@ -619,12 +624,9 @@ __global__ void k_pmis_fmark(int n, const int* rp, const int* ci, const uint8_t*
 void launch_pmis_round(int n, const int* rp, const int* ci, const uint8_t* S, const int* strp, const int* stci,
                        const double* w, signed char* CF, uint8_t* newc, int* undecided, cudaStream_t s) {
   int nb = cdiv(n, kThreads);
-  k_pmis_select<<<nb, kThreads, 0, s>>>(n, rp, ci, S, strp, stci, w, CF, newc);
+  k_pmis_select<<<nb, kThreads, 0, s>>>(n, rp, ci, S, strp, stci, w, CF, newc, undecided);
   MGD_LAUNCH_CHECK();
-  k_pmis_apply<<<nb, kThreads, 0, s>>>(n, newc, CF);
-  MGD_LAUNCH_CHECK();
-  MGD_CUDA(cudaMemsetAsync(undecided, 0, sizeof(int), s));
-  k_pmis_fmark<<<nb, kThreads, 0, s>>>(n, rp, ci, S, CF, undecided);
+  k_pmis_fmark<<<nb, kThreads, 0, s>>>(n, rp, ci, S, newc, CF, undecided);
   MGD_LAUNCH_CHECK();
 }
 
