@@ -115,11 +115,12 @@ inline void* pool_alloc(cudaMemPool_t pool, size_t bytes, cudaStream_t s) {
 // Arrays are carved, 256-byte aligned, from slabs of the context's pool (the
 // first 4 MiB, each next one twice the last, up to 1 GiB; an array above 256
 // MiB gets a block of its own), so a setup makes a few dozen pool allocations
-// instead of thousands and the release frees as many.  A slab is allocated on the arena's own stream, which is otherwise
-// idle, and synchronised there before any array in it is handed out, so every
-// stream may use it; arrays are never freed one by one.  Safe to use from the
-// setup worker threads: each zeroes on its own stream and synchronises it
-// before the memory is used elsewhere.
+// instead of thousands and the release frees as many.  A slab is allocated on
+// the arena's own stream, which is otherwise idle, and synchronised there
+// before any array in it is handed out, so every stream may use it; arrays
+// are never freed one by one.  Safe to use from the setup worker threads:
+// each zeroes on its own stream and synchronises it before the memory is used
+// elsewhere.
 struct Arena {
   std::vector<void*> ptrs;          // slabs and separate blocks
   cudaStream_t stream = nullptr;    // the context stream (release)
@@ -283,7 +284,6 @@ enum Fmt { FMT_SELL = 0, FMT_CSR1 = 1, FMT_CSR2 = 2, FMT_CSR4 = 3, FMT_CSR8 = 4,
                                              // slices (l1-Jacobi smoothing phases only)
            FMT_CSR1X2 = 9, FMT_CSR1X4 = 10 };  // CSR, one thread per row, each thread on the same lane of
                                                // 2 / 4 adjacent 32-row groups (restriction, prolongation only)
-constexpr int kNumFmt = 7;
 
 struct Sell {  // sliced ELL, slice height 32, column-major inside a slice
   int n = 0, nslices = 0;
