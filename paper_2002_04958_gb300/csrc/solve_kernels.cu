@@ -28,6 +28,7 @@ namespace cg = cooperative_groups;
 // directly; subnormal, infinite and NaN operands, and binary64 values outside
 // the binary32 normal range, take the hardware conversion.
 // mgd_check_conversions compares both with the hardware conversion.
+
 // the hardware conversions of the rare operands, out of line so that the
 // common path does not issue them predicated off
 __device__ __noinline__ double f32_to_f64_hw(float f) { return (double)f; }
