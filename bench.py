@@ -582,15 +582,19 @@ TRAFFIC_SOURCES = {
 
 
 def kernel_source_sha256(name="level0"):
-    """Hash of the source of a kernel class (the code its traffic was measured on)."""
+    """Hash of the source of a kernel class (the code its traffic was measured
+    on); None when a marker of the class's source region is missing."""
     import hashlib
     h = hashlib.sha256()
     for fn, first, end in TRAFFIC_SOURCES[name]:
         with open(os.path.join(ROOT, "paper_2002_04958_gb300", "csrc", fn), "rb") as f:
             text = f.read()
         if first is not None:
-            i = text.index(first.encode())
-            text = text[i:text.index(end.encode(), i)]
+            i = text.find(first.encode())
+            j = text.find(end.encode(), i) if i >= 0 else -1
+            if j < 0:
+                return None
+            text = text[i:j]
         h.update(text)
     return h.hexdigest()
 

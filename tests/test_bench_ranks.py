@@ -85,3 +85,21 @@ def test_reference_arm_line_on_the_small_workload():
                               agg=0, precision=0, batched=1, graph=1)
     assert d["config"] == json.loads(json.dumps(bench._config(args, inputs.preset(0), 1)))
     assert d["metric"] == bench.METRIC
+
+
+def test_roofline_traffic_entries_match_the_kernel_sources():
+    # the stored DRAM traffic of each roofline class applies to the kernel
+    # source it was captured on: every class's source region is found, and
+    # an entry whose hash differs is reported as null by the bench (not used)
+    import json
+    import bench
+    with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+        table = json.load(f)
+    for name in bench.TRAFFIC_SOURCES:
+        h = bench.kernel_source_sha256(name)
+        assert h is not None, name
+        entry = table.get(name)
+        if entry and entry.get("kernel_source_sha256") == h:
+            assert bench._traffic_from_profiles(name, entry["workload"]) == entry["traffic_bytes_per_launch"]
+        else:
+            assert bench._traffic_from_profiles(name, (entry or {}).get("workload", "")) is None
