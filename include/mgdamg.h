@@ -141,8 +141,10 @@ int mgd_setup(mgd_ctx *c, int G, int N, int n, int nnz, const int *d_rowptr, con
  * h_colidx[nnz], h_vals[nnz] are copied to the device (in 32 MiB chunks over
  * four copy streams, so several copy engines run at once; page-locked host
  * memory gives the full host-to-device bandwidth, pageable memory is staged by
- * the driver), then set up exactly as mgd_setup does.  The host arrays are only
- * read, and may be reused once the call returns.  Same errors as mgd_setup. */
+ * the driver) straight into the device memory the setup keeps as its copy of
+ * the operator, after the previous setup has been released, then set up
+ * exactly as mgd_setup does.  The host arrays are only read, and may be reused
+ * once the call returns.  Same errors as mgd_setup. */
 int mgd_setup_host(mgd_ctx *c, int G, int N, int n, int nnz, const int *h_rowptr, const int *h_colidx,
                    const double *h_vals, int kind);
 

@@ -568,7 +568,8 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
     Level& lv = h.L[l];
     int n = lv.A.n;
     lv.dinv = ar.alloc<double>(n);
-    launch_l1_dinv(n, lv.A.rp, lv.A.v, lv.dinv, s);
+    if (sc.mixed) lv.dinv32 = ar.alloc<float>(n);
+    launch_l1_dinv(n, lv.A.rp, lv.A.v, lv.dinv, s, lv.dinv32);
     if (lv.nk > 0) {
       lv.gdinv = ar.alloc<double>(n);
       launch_diag_inv(n, lv.A.rp, lv.A.ci, lv.A.v, lv.gdinv, s);
@@ -598,7 +599,6 @@ static void build_hierarchy(SetupCtx& sc, Hier& h, const Csr& A0) {
       lv.v32 = ar.alloc<float>(lv.A.nnz);
       if (jac) lv.vpre32 = ar.alloc<float>(lv.A.nnz);
       launch_colscale_f32(lv.A.nnz, lv.A.ci, lv.A.v, pre, lv.v32, lv.vpre32, s);
-      lv.dinv32 = cast32(ar, lv.dinv, n, s);
       if (l < h.nlev() - 1) {
         lv.pv32 = cast32(ar, lv.P.v, lv.P.nnz, s);
         lv.rv32 = cast32(ar, lv.R.v, lv.R.nnz, s);
@@ -2270,7 +2270,9 @@ static void record_phase(mgd_ctx* c, int ph, double ms) {
   c->phases.ms[ph] = ms;
 }
 
-static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) {
+// owned: rp, ci, v are arrays of the context's arena (mgd_setup_host copied
+// the host arrays there), kept as the monolithic operator without a copy
+static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v, bool owned = false) {
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = c->s;
   int G = c->G, N = c->N, n = c->n, nnz = c->nnz, nc = G + 2;
@@ -2301,7 +2303,7 @@ static void do_setup(mgd_ctx* c, const int* rp, const int* ci, const double* v) 
   in.rp = const_cast<int*>(rp);
   in.ci = const_cast<int*>(ci);
   in.v = const_cast<double*>(v);
-  c->A = csr_copy(c->ar, in, s);
+  c->A = owned ? in : csr_copy(c->ar, in, s);
   c->Asell = build_sell(c->ar, c->A, false, s);
   if (o.keep_transpose) {
     c->AT = transpose(c->ar, c->A, s);
@@ -2914,13 +2916,14 @@ int mgd_setup_host(mgd_ctx* c, int G, int N, int n, int nnz, const int* h_rowptr
       throw Error{MGD_EINVAL, "invalid sizes or kind"};
     for (auto& cs : c->s_copy)
       if (!cs) MGD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    // staging copies (stream-ordered on the context stream, released after
-    // the setup, which keeps its own copy of the operator)
-    Scratch sc(c->s);
-    int* rp = sc.alloc<int>((size_t)n + 1);
-    int* ci = sc.alloc<int>(nnz);
-    double* v = sc.alloc<double>(nnz);
-    struct CopyDrain {  // before the staging is freed on any exit path, the copies have ended
+    // the previous setup goes first; the host arrays are copied straight into
+    // the new setup's arena, where they stay as the monolithic operator
+    const double rel_ms = free_setup_timed(c);
+    c->ar.stream = c->s;
+    int* rp = c->ar.alloc<int>((size_t)n + 1);
+    int* ci = c->ar.alloc<int>(nnz);
+    double* v = c->ar.alloc<double>(nnz);
+    struct CopyDrain {  // on any exit path the copies have ended before the arena can be released
       mgd_ctx* c;
       ~CopyDrain() {
         for (auto cs : c->s_copy)
@@ -2948,13 +2951,12 @@ int mgd_setup_host(mgd_ctx* c, int G, int N, int n, int nnz, const int* h_rowptr
     }
     MGD_CUDA(cudaStreamSynchronize(c->s));
     const double h2d_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th).count();
-    const double rel_ms = free_setup_timed(c);
     c->G = G;
     c->N = N;
     c->n = n;
     c->nnz = nnz;
     c->kind = kind;
-    do_setup(c, rp, ci, v);
+    do_setup(c, rp, ci, v, true);
     record_phase(c, SP_H2D, h2d_ms);
     record_phase(c, SP_RELEASE, rel_ms);
     return MGD_OK;

@@ -501,7 +501,7 @@ void launch_spgemm_expand(int n, const int* xrp, const int* xci, const double* x
                           int* work, cudaStream_t s, long long total_products);  // work: 2n + 2 ints
 void launch_spgemm_compact(int n, const long long* off, const int* tc, const double* tv, const int* crp,
                            int* cci, double* cv, cudaStream_t s);
-void launch_l1_dinv(int n, const int* rp, const double* v, double* dinv, cudaStream_t s);
+void launch_l1_dinv(int n, const int* rp, const double* v, double* dinv, cudaStream_t s, float* dinv32 = nullptr);
 void launch_diag_inv(int n, const int* rp, const int* ci, const double* v, double* dinv, cudaStream_t s);
 void launch_densify(int n, const int* rp, const int* ci, const double* v, double* a, cudaStream_t s);
 void launch_dense_inverse(int n, double* a, int* piv, double* inv, double* invT, int* status, cudaStream_t s);

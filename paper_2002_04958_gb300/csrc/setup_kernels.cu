@@ -576,8 +576,11 @@ void launch_perm_rows_fill(int n, const int* perm, const int* rp, const int* ci,
   MGD_LAUNCH_CHECK();
 }
 
+// PMIS weights are count + u with u in [0, 1): finite and not negative, so
+// their bit patterns order as the values do and compare on the integer pipe
 __device__ __forceinline__ bool beats(const double* w, int i, int j) {
-  return w[i] > w[j] || (w[i] == w[j] && i > j);
+  const long long wi = __double_as_longlong(w[i]), wj = __double_as_longlong(w[j]);
+  return wi > wj || (wi == wj && i > j);
 }
 
 // round part 1: undecided local maxima over S_i and S^T_i become C (newc)
@@ -650,7 +653,22 @@ void launch_interp_count(int n, const int* rp, const int* ci, const uint8_t* S, 
   MGD_LAUNCH_CHECK();
 }
 
-__device__ __forceinline__ bool opp_sign(double akm, double akk) { return akk > 0.0 ? (akm < 0.0) : (akm > 0.0); }
+// Comparisons of binary64 values with zero on the integer pipe (an FP64
+// compare issues on the FP64 pipe, slow on this part), exact for every input
+// including +-0, +-inf and NaN: x > 0 iff the sign is clear and the magnitude
+// bits lie in (0, inf]; x < 0 iff the sign is set and likewise; x == 0 iff
+// every bit but the sign is clear.
+__device__ __forceinline__ bool pos_f64(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool neg_f64(double x) {
+  const long long m = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+  return __double_as_longlong(x) < 0 && m > 0 && m <= 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool zero_f64(double x) { return (__double_as_longlong(x) << 1) == 0; }
+
+__device__ __forceinline__ bool opp_sign(double akm, double akk) { return pos_f64(akk) ? neg_f64(akm) : pos_f64(akm); }
 
 // One thread per row.  Numerators start from a_ij (j in C_i, row order); strong
 // F neighbours k distribute a_ik abar_kj / sum_{m in C_i} abar_km, or are lumped
@@ -786,7 +804,7 @@ __global__ void k_exti_diag(int n, const int* rp, const int* ci, const double* v
     if (S[p] && CF[k] == 1) continue;
     if (S[p] && CF[k] == -1) {
       double denom = den[p];
-      if (denom == 0.0) {
+      if (zero_f64(denom)) {
         diag = __dadd_rn(diag, aik);
       } else {
         int q = find_col(rp, ci, k, i);
@@ -822,13 +840,13 @@ __global__ void k_exti_value(int nnzp, const int* prowof, const int* prp, const 
     int k = ci[p];
     if (k == i || !(S[p] && CF[k] == -1)) continue;
     double denom = den[p];
-    if (denom == 0.0) continue;
+    if (zero_f64(denom)) continue;
     int q = find_col(rp, ci, k, l);
     if (q >= 0 && opp_sign(v[q], dg[k])) num = __dadd_rn(num, __ddiv_rn(__dmul_rn(v[p], v[q]), denom));
   }
   double diag = diagv[i];
   pci[e] = cidx[l];
-  pv[e] = (diag != 0.0) ? __ddiv_rn(-num, diag) : 0.0;
+  pv[e] = !zero_f64(diag) ? __ddiv_rn(-num, diag) : 0.0;
 }
 
 // Classical modified interpolation values in passes that keep the operand
@@ -878,7 +896,7 @@ __global__ void k_cl_diag(int n, const int* rp, const int* ci, const double* v, 
     if (k == i) continue;
     if (S[p] && CF[k] == 1) continue;
     if (S[p] && CF[k] == -1) {
-      if (den[p] == 0.0) diag = __dadd_rn(diag, v[p]);
+      if (zero_f64(den[p])) diag = __dadd_rn(diag, v[p]);
     } else {
       diag = __dadd_rn(diag, v[p]);  // weak neighbours: lumped
     }
@@ -901,12 +919,12 @@ __global__ void k_cl_value(int nnzp, const int* prowof, const int* rp, const int
     int k = ci[p];
     if (k == i || !(S[p] && CF[k] == -1)) continue;
     double denom = den[p];
-    if (denom == 0.0) continue;
+    if (zero_f64(denom)) continue;
     int q = find_col(rp, ci, k, m);
     if (q >= 0 && opp_sign(v[q], dg[k])) num = __dadd_rn(num, __ddiv_rn(__dmul_rn(v[p], v[q]), denom));
   }
   double diag = diagv[i];
-  pv[e] = (diag != 0.0) ? __ddiv_rn(-num, diag) : 0.0;
+  pv[e] = !zero_f64(diag) ? __ddiv_rn(-num, diag) : 0.0;
 }
 
 __global__ void k_cl_columns(int nnzp, const int* prowof, const signed char* CF, const int* cidx, int* pci) {
@@ -1444,16 +1462,19 @@ void launch_spgemm_compact(int n, const long long* off, const int* tc, const dou
 }
 
 // ------------------------------------------------------------------ smoother diagonals, coarsest inverse
-__global__ void k_l1_dinv(int n, const int* rp, const double* v, double* dinv) {
+// dinv = 1 / sum_j |a_ij|; dinv32, when given, the same rounded to FP32
+__global__ void k_l1_dinv(int n, const int* rp, const double* v, double* dinv, float* dinv32) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double s = 0.0;
   for (int p = rp[i]; p < rp[i + 1]; ++p) s = __dadd_rn(s, fabs(v[p]));
-  dinv[i] = __ddiv_rn(1.0, s);
+  const double d = __ddiv_rn(1.0, s);
+  dinv[i] = d;
+  if (dinv32) dinv32[i] = (float)d;
 }
 
-void launch_l1_dinv(int n, const int* rp, const double* v, double* dinv, cudaStream_t s) {
-  k_l1_dinv<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, v, dinv);
+void launch_l1_dinv(int n, const int* rp, const double* v, double* dinv, cudaStream_t s, float* dinv32) {
+  k_l1_dinv<<<cdiv(n, kThreads), kThreads, 0, s>>>(n, rp, v, dinv, dinv32);
   MGD_LAUNCH_CHECK();
 }
 
